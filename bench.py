@@ -1,0 +1,299 @@
+"""Throughput benchmark of the data-annealed SMC sampler on GB300.
+
+A step is one SMC iteration through the C ABI: smc_anneal_next, smc_resample
+and smc_step (S leapfrog steps, each a forward + adjoint pass of all J
+particle networks over the annealed subset D_k, then the reweight,
+normalisation and ESS).  Workload: the MNIST-shaped stand-in (60000 synthetic
+28x28 10-class images), MLP 784-100-10 ReLU, J = 256 particles, mini-batch
+1000, Linear data annealing taken at its full-subset phase (|D_k| = 60000),
+HMC with S = 3, h = 0.002, BF16 tcgen05 contractions with FP32 accumulation.
+
+Metric: particle-sample gradient evaluations per second = J * |D_k| * (gradient
+evaluations) / time.  `value` is device-timed with inputs resident in HBM;
+`e2e` streams the annealed subset from pinned host memory through
+smc_upload_rows every step and reads the step statistics back.
+
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload instead (the reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle*sample grad-evals/s"
+UNIT = "grad-evals/s"
+N_TRAIN, DIN, H, NCLS = 60000, 784, 100, 10
+J_DEFAULT, MB, K_SCHED, K_START, STEP_H, S_LF = 256, 1000, 200, 100, 0.002, 3
+
+
+def workload_config(args):
+    return {
+        "workload": (f"MLP {DIN}-{H}-{NCLS} ReLU, J={args.J} particles, synthetic {args.n}x{DIN} 10-class images, "
+                     f"Linear DA (C=kappa={MB}, K={K_SCHED}) at its full-subset phase |D_k|={args.n}, "
+                     f"HMC S={S_LF}, h={STEP_H}"),
+        "particles": args.J, "rows": args.n, "model": f"mlp-{DIN}-{H}-{NCLS}-relu",
+        "schedule": "linear", "leapfrog_steps": S_LF,
+        "l2": "no flush: per-step working set (activations 2x3 GB) far above the 129 MB L2",
+    }
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, idx):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(idx), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_data(n, seed=0):
+    import synthetic
+    return synthetic.template_images(n, seed=seed)
+
+
+def cpu_baseline(seconds=12.0, J_s=2, M_s=2000):
+    """The FP64 oracle's gradient evaluation on a bounded sample of the
+    workload: J_s particles x M_s rows of the same model and data."""
+    import synthetic
+    from oracle import nn
+    spec = nn.Spec([("dense", DIN, H), ("dense", H, NCLS)], (DIN,), nn.RELU)
+    X, y = synthetic.template_images(M_s, seed=3)
+    X = X.astype(np.float64)
+    th = synthetic.particles(J_s, spec.n_params, 3, std=0.05).astype(np.float64)
+    coef = np.full(M_s, N_TRAIN / M_s)
+    n_eval = 0
+    t0 = time.perf_counter()
+    while True:
+        for j in range(J_s):
+            nn.loglik_grad(spec, th[j], X, y, coef)
+        n_eval += J_s
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": n_eval * M_s / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n_eval} FP64 oracle gradient evaluations of single particles over {M_s} rows "
+                      f"({el:.1f} s, numpy BLAS default threads)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synthetic
+    from oracle import nn, rng, smc as osmc
+    J_s, M_s = 2, 2000
+    spec = nn.Spec([("dense", DIN, H), ("dense", H, NCLS)], (DIN,), nn.RELU)
+    X, y = synthetic.template_images(M_s, seed=3)
+    orc = osmc.Sampler(spec, X, y, J_s, rng.fisher_yates_permutation(M_s, 1))
+    orc.set_schedule("fb", M_s, M_s, K_SCHED, synthetic.particles(J_s, spec.n_params, 1, std=0.05))
+    z = synthetic.normals((J_s, spec.n_params), 2)
+    for _ in range(args.warmup):
+        orc.step(STEP_H, S_LF, z)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orc.step(STEP_H, S_LF, z)
+    el = time.perf_counter() - t0
+    value = J_s * M_s * S_LF * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"each step: one FP64 oracle SMC move (S={S_LF}) of {J_s} particles over "
+                                       f"{M_s} rows (bounded sample of the workload)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--J", type=int, default=J_DEFAULT)
+    ap.add_argument("--n", type=int, default=N_TRAIN)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-roofline", action="store_true")
+    args = ap.parse_args()
+    args.steps = max(1, args.steps)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2601_21983_gb300 import smc as S
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    S.load()
+    stream = torch.cuda.current_stream()
+
+    X, y = make_data(args.n, seed=rank)
+    Xd = torch.from_numpy(X).cuda()
+    yd = torch.from_numpy(y).cuda()
+    model = S.make_model([("dense", DIN, H), ("dense", H, NCLS)], (DIN,), S.ACT_RELU)
+    cfg = S.make_config(args.J, 1234 + rank, S.PREC_BF16, stream=stream)
+    ctx = S.smc_init(model, Xd, y_class=yd, cfg=cfg)
+    sched = S.make_schedule("linear", MB, MB, K_SCHED, k_start=K_START)
+    S.smc_set_schedule(ctx, sched)
+    evals = [0]
+
+    def one_step(upload=None):
+        if upload is not None:
+            S.smc_upload_rows(ctx, 0, upload[0], upload[1])
+        info = S.smc_anneal_next(ctx)
+        S.smc_resample(ctx)
+        st = S.smc_step(ctx, STEP_H, S_LF)
+        evals[0] += st["grad_evals"] * st["rows"] * args.J
+        return st
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local) if rank == 0 else None
+    n0, _, _ = S.smc_get_counters(ctx)
+    evals[0] = 0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    n1, _, _ = S.smc_get_counters(ctx)
+    clk = clocks.stop() if clocks else None
+    my_evals = evals[0]
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    e = torch.tensor([float(my_evals)], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    ms_max, total_evals = t.item(), e.item()
+    value = total_evals / (ms_max / 1e3)
+
+    # ---- end to end: subset streamed from pinned host memory every step
+    e2e = None
+    if not args.no_e2e:
+        perm = S.smc_get_permutation(ctx, args.n)
+        hx = torch.from_numpy(np.ascontiguousarray(X[perm])).pin_memory()
+        hy = torch.from_numpy(np.ascontiguousarray(y[perm])).pin_memory()
+        hxn, hyn = hx.numpy(), hy.numpy()
+        one_step((hxn, hyn))
+        torch.cuda.synchronize()
+        evals[0] = 0
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            one_step((hxn, hyn))
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        e2e = {"value": evals[0] / el, "unit": UNIT, "h2d_bytes_per_step": int(hxn.nbytes + hyn.nbytes),
+               "d2h_bytes_per_step": 16 * 8 + 2 * 4}
+
+    # ---- per-kernel-family times for the roofline (separate pass, events per launch)
+    roof = None
+    fam = None
+    if not args.no_roofline:
+        S.smc_destroy(ctx)
+        cfg_t = S.make_config(args.J, 1234 + rank, S.PREC_BF16, stream=stream, timing=1)
+        ctx = S.smc_init(model, Xd, y_class=yd, cfg=cfg_t)
+        S.smc_set_schedule(ctx, sched)
+        one_step()
+        S.smc_reset_counters(ctx)
+        nsteps = 2
+        for _ in range(nsteps):
+            one_step()
+        _, times, calls = S.smc_get_counters(ctx)
+        fam = {k: {"ms": times[k], "calls": calls[k]} for k in times if calls[k]}
+        hbm, tf_burst, tf_sus, src = peaks()
+        M = args.n
+        flops = {"fwd_gemm": 2.0 * M * args.J * H * DIN, "wgrad_gemm": 2.0 * M * args.J * H * (DIN + 1)}
+        dom = max(("fwd_gemm", "wgrad_gemm"), key=lambda k: times[k])
+        avg_ms = times[dom] / max(1, calls[dom])
+        achieved = flops[dom] / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": tf_sus, "unit": "TFLOP/s",
+                "frac": achieved / tf_sus, "peak_kind": f"{src} bf16_tflops_sustained", "traffic": None,
+                "flops_per_launch": flops[dom], "avg_launch_ms": avg_ms}
+    S.smc_destroy(ctx)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                "config": workload_config(args), "e2e": e2e, "gpu_launches": n1 - n0,
+                "clocks": clk, "roofline": roof, "families_ms": fam}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

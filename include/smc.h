@@ -1,0 +1,293 @@
+/*
+ * smc.h - C ABI of libsmc, a GB300 (sm_103a) implementation of the data-annealed
+ * Sequential Monte Carlo sampler for neural-network posteriors described in
+ * "Investigating Batch Inference in a Sequential Monte Carlo Framework for
+ * Neural Networks" (Millard, Murphy, Green, Maskell).
+ *
+ * The sampler keeps J particles theta_j (one weight vector of a network each)
+ * with log-weights log w_j and targets, at iteration k,
+ *     log pi_k(theta) = -|theta|^2 / (2 sigma^2) + sum_{i in D_k} c_i log p(y_i | theta)
+ * where D_k is the data-annealed subset (Sec. 3: whole mini-batches appended to
+ * a cumulatively growing subset), c_i = N / M_k for the fixed schedules
+ * (Sec. 3, eq. approx-grad) and c_i in {1, beta_k} for smooth data annealing
+ * (Sec. 3.1, eq. sda_initial_target and the annealed target after it).
+ *
+ * Conventions shared by every call
+ *  - Status: every call returns smc_status.  A CUDA error or a device-side
+ *    timeout makes the context sticky-failed: later calls return SMC_ESTATE
+ *    until smc_destroy.  Nothing aborts, traps or exits the process.
+ *  - Ownership: the context owns all device state.  Inputs are copied during
+ *    the call; output buffers are caller-owned.  Pointer arguments are host
+ *    pointers unless the argument or a flag says "device".
+ *  - Streams: all work is enqueued on the stream given in smc_config (0 = the
+ *    legacy default stream).  Calls that return statistics synchronise that
+ *    stream before returning.
+ *  - Threads: one context must not be used by two threads at once.
+ *  - Parameter order: a particle's parameter vector ("canonical order") lists
+ *    the parametric layers in order, each as W (row-major: dense [n_out][n_in],
+ *    conv [c_out][c_in][k][k]) followed by b [n_out]; D is its length.  Arrays
+ *    of particles are [J][D] row-major.
+ */
+#ifndef SMC_H
+#define SMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SMC_ABI_VERSION 1
+
+typedef struct smc_ctx smc_ctx;
+
+typedef enum {
+    SMC_OK = 0,
+    SMC_EINVAL = 1,        /* bad argument or inconsistent model/config */
+    SMC_ENOMEM = 2,        /* device or pinned-host allocation failed */
+    SMC_ECUDA = 3,         /* a CUDA runtime/driver call failed */
+    SMC_ESTATE = 4,        /* call out of order, or context already failed */
+    SMC_ENUMERIC = 5,      /* every particle's log-weight is -inf or NaN */
+    SMC_ETIMEOUT = 6,      /* a bounded device-side wait gave up */
+    SMC_EUNSUPPORTED = 7   /* valid request this build does not implement */
+} smc_status;
+
+enum { SMC_LAYER_DENSE = 0, SMC_LAYER_CONV = 1, SMC_LAYER_MAXPOOL2 = 2 };
+enum { SMC_ACT_TANH = 0, SMC_ACT_RELU = 1, SMC_ACT_IDENTITY = 2 };
+enum { SMC_LIK_CATEGORICAL = 0, SMC_LIK_GAUSSIAN = 1 };
+enum { SMC_PREC_FP32 = 0, SMC_PREC_BF16 = 1 };
+enum { SMC_RESAMPLE_SYSTEMATIC = 0, SMC_RESAMPLE_MULTINOMIAL = 1 };
+enum {
+    SMC_SCHED_CONSTANT = 0, SMC_SCHED_FB = 1, SMC_SCHED_CTR = 2,
+    SMC_SCHED_LINEAR = 3, SMC_SCHED_AUTOMATED = 4, SMC_SCHED_SDA = 5
+};
+enum { SMC_PROPOSAL_PLAIN = 0, SMC_PROPOSAL_LEARNED = 1 };
+
+/* One layer.  DENSE: n_in -> n_out.  CONV: valid ksize x ksize cross-correlation,
+ * stride 1, n_in = c_in channels -> n_out = c_out channels.  MAXPOOL2: 2x2 max
+ * pool with stride 2 (n_in, n_out, ksize ignored).  An activation follows every
+ * parametric layer except the last; the last layer's outputs are the logits
+ * (categorical likelihood) or the mean (Gaussian likelihood, n_out = 1). */
+typedef struct { int32_t kind, n_in, n_out, ksize; } smc_layer;
+
+typedef struct {
+    int32_t version;           /* SMC_ABI_VERSION */
+    int32_t n_layers;
+    const smc_layer* layers;   /* host array of n_layers, copied */
+    int32_t in_c, in_h, in_w;  /* input shape (c, h, w); a feature vector is (d, 1, 1) */
+    int32_t activation;        /* SMC_ACT_* */
+    int32_t likelihood;        /* SMC_LIK_* */
+    double prior_sigma;        /* q_0 = N(0, prior_sigma^2 I)  (eq. init_weight's q_0) */
+    double noise_sigma;        /* Gaussian likelihood only */
+} smc_model;
+
+/* Training set: x [n][in_c*in_h*in_w] float32 in (c, h, w) order; y_class
+ * int32 [n] (categorical) or y_value float32 [n] (Gaussian).  on_device != 0
+ * means the pointers are device pointers.  The data are copied at smc_init. */
+typedef struct {
+    const float* x;
+    const int32_t* y_class;
+    const float* y_value;
+    int64_t n;
+    int32_t on_device;
+} smc_data;
+
+typedef struct {
+    int32_t version;           /* SMC_ABI_VERSION */
+    int32_t n_particles;       /* J >= 1 (<= 4096) */
+    uint64_t seed;             /* keys the mini-batch order, prior draws, momenta, uniforms */
+    int32_t precision;         /* SMC_PREC_FP32: all arithmetic FP32 (SIMT kernels).
+                                  SMC_PREC_BF16: network contractions in BF16 on tcgen05
+                                  tensor cores with FP32 accumulation (dense models only). */
+    int32_t resampler;         /* SMC_RESAMPLE_* */
+    int32_t scaled;            /* 1: c_i = N/M_k on the log-likelihood and gradient
+                                     (eq. approx-grad); 0: c_i = 1 */
+    int64_t chunk_rows;        /* rows per forward/backward chunk (0 = automatic) */
+    void* stream;              /* cudaStream_t */
+    int32_t timing;            /* 1: record per-kernel-family CUDA-event times */
+} smc_config;
+
+typedef struct {
+    int32_t kind;              /* SMC_SCHED_* (Sec. 3.1) */
+    int64_t C;                 /* initial subset size */
+    int64_t kappa;             /* mini-batch increment */
+    int32_t K;                 /* number of iterations (for the 0.9K switch) */
+    int32_t k_start;           /* iteration to start at (0 normally) */
+    double beta0;              /* SDA: initial temperature (0.1) */
+    double beta_reinit;        /* SDA: temperature after an append (0.1) */
+    double delta_s;            /* SDA: entropy increment Delta S (1) */
+} smc_schedule;
+
+typedef struct {
+    double h;                  /* leapfrog step size */
+    int32_t S;                 /* leapfrog steps (S = 1: Langevin dynamics) */
+    int32_t proposal;          /* SMC_PROPOSAL_* */
+} smc_step_params;
+
+typedef struct {
+    double ess;                /* J_eff after the call (eq. jeff) */
+    double mean_logpi;         /* mean of log pi_k(theta_j) over particles */
+    double beta;               /* temperature of the tempered block (1 for fixed schedules) */
+    int64_t rows;              /* |D_k| */
+    int32_t k;                 /* iteration index */
+    int32_t n_nonfinite;       /* particles whose log pi was not finite (log w set to -inf) */
+    int32_t grad_evals;        /* gradient evaluations over D_k made by the call */
+    int32_t pad_;
+} smc_step_stats;
+
+typedef struct {
+    int32_t appended;          /* 1 if rows were added to the subset */
+    int32_t k;                 /* new iteration index */
+    int64_t rows;              /* |D_{k}| after the call */
+    int64_t rows_full;         /* SDA: fully included rows (= rows for fixed schedules) */
+    double beta;               /* SDA temperature after the call */
+} smc_anneal_info;
+
+/* ---------------------------------------------------------------- lifecycle */
+
+/* Create a sampler.  Validates the model, copies the training set to the GPU in
+ * the order of one Fisher-Yates permutation drawn from `seed` (Sec. 3:
+ * mini-batches drawn without replacement; D_k is the first |D_k| rows of that
+ * order), and draws theta_0 ~ q_0 = N(0, prior_sigma^2 I) (eq. init_weight) with
+ * Philox4x32-10.  Errors: SMC_EINVAL (shape/arg), SMC_EUNSUPPORTED (BF16 with a
+ * non-dense model), SMC_ENOMEM, SMC_ECUDA.  *out is NULL on error. */
+smc_status smc_init(const smc_model* model, const smc_data* train,
+                    const smc_config* cfg, smc_ctx** out);
+
+/* Release all device and host resources.  NULL is ignored. */
+void smc_destroy(smc_ctx* ctx);
+
+/* Human-readable name of a status code (static storage). */
+const char* smc_status_string(smc_status s);
+
+/* Last error message recorded by a context (static per context; never NULL). */
+const char* smc_last_error(const smc_ctx* ctx);
+
+/* Parameter count D of one particle. */
+int64_t smc_num_params(const smc_ctx* ctx);
+
+/* --------------------------------------------------------- the SMC iteration */
+
+/* Fix the annealing schedule (Sec. 3.1) and start at iteration k_start: set the
+ * subset D_{k_start}, evaluate log pi_0 and its gradient at the current
+ * particles and set log w_0 = log pi_0(theta) - log q_0(theta), i.e. the
+ * coefficient-weighted log-likelihood (eq. init_weight); then normalise
+ * (eq. normalise) and compute the ESS (eq. jeff).  `stats` may be NULL.
+ * Errors: SMC_EINVAL (C < 1, kappa < 1, K < 1), SMC_ENUMERIC. */
+smc_status smc_set_schedule(smc_ctx* ctx, const smc_schedule* sched, smc_step_stats* stats);
+
+/* One move + reweight under the current target pi_k (Sec. 2.1):
+ * P^0 ~ N(0, M); S leapfrog steps (eqs. mom_first, pos_update, mom_second);
+ * log w += log pi_k(theta_k) - log pi_{k-1}(theta_{k-1}) - P_k' M^-1 P_k / 2
+ *          + P^0' M^-1 P^0 / 2 (eq. weight_update_fp, reversed-momentum L-kernel);
+ * normalise and ESS.  M = I for SMC_PROPOSAL_PLAIN; a per-layer diagonal mass and
+ * step chosen by the learned proposal for SMC_PROPOSAL_LEARNED (not in the paper).
+ * Errors: SMC_EINVAL (h < 0, S < 1), SMC_ENUMERIC, SMC_ETIMEOUT, SMC_ECUDA. */
+smc_status smc_step(smc_ctx* ctx, const smc_step_params* p, smc_step_stats* stats);
+
+/* Advance to the target of iteration k+1 (Sec. 3.1): fixed schedules compute
+ * M_{k+1}; SDA updates beta from the weighted moments of Omega and Omega_hat
+ * (eqs. beta_initial_data_k / beta_annealed_k) or, once beta has reached 1,
+ * appends the next mini-batch and resets beta.  `info` may be NULL. */
+smc_status smc_anneal_next(smc_ctx* ctx, smc_anneal_info* info);
+
+/* Resample when J_eff < J/2 (Sec. 2) or when force != 0, then set every weight
+ * to 1/J.  Systematic or multinomial per smc_config.resampler, computed on an
+ * exact fixed-point cumulative sum of the normalised weights.  did_resample
+ * may be NULL. */
+smc_status smc_resample(smc_ctx* ctx, int32_t force, int32_t* did_resample);
+
+/* Weighted posterior predictive (Sec. 2, E_pi[f] ~ sum_j w~_j f(theta_j)) with
+ * f = softmax of the network's logits: probs_out[n][n_classes] (float32).
+ * x_test [n][input] float32.  on_device: 1 if x_test and probs_out are device
+ * pointers.  Categorical models only (SMC_EUNSUPPORTED otherwise). */
+smc_status smc_posterior_predict(smc_ctx* ctx, const float* x_test, int64_t n,
+                                 int32_t on_device, float* probs_out);
+
+/* Replace training rows [row0, row0 + n) of the annealed order with host data
+ * x [n][input], y [n] (stream-ordered copy through pinned staging).  Lets a
+ * caller keep the training set in host memory and stream the subset each
+ * iteration. */
+smc_status smc_upload_rows(smc_ctx* ctx, int64_t row0, int64_t n,
+                           const float* x, const int32_t* y_class, const float* y_value);
+
+/* ------------------------------------------------ state access (tests, tools) */
+
+/* Copy particles [J][D] (canonical order, float32), log-weights [J] and the
+ * cached log pi of the last evaluated target [J] to host buffers; any may be NULL. */
+smc_status smc_get_state(smc_ctx* ctx, float* theta, double* logw, double* logpi);
+
+/* Overwrite the particles from host [J][D]; invalidates the cached gradient.
+ * logw / logpi (host [J]) may be NULL to leave them unchanged. */
+smc_status smc_set_state(smc_ctx* ctx, const float* theta, const double* logw, const double* logpi);
+
+/* Inject the standard-normal draws z [J][D] (host, canonical order) used for the
+ * momentum of the next smc_step instead of Philox (P^0 = M^{1/2} z). */
+smc_status smc_set_noise(smc_ctx* ctx, const float* z);
+
+/* Inject resampling uniforms for the next smc_resample: 1 value (systematic) or
+ * J values (multinomial), host, each in [0, 1). */
+smc_status smc_set_uniforms(smc_ctx* ctx, const double* u, int32_t n);
+
+/* Evaluate, at the current particles and under the current target, log pi [J],
+ * the gradient of the log-likelihood part sum_i c_i grad log p(y_i|theta)
+ * [J][D] (canonical order, prior excluded) and the unweighted log-likelihood
+ * sums over the fully weighted rows (la) and the tempered block (lb).  Host
+ * outputs, each may be NULL. */
+smc_status smc_eval(smc_ctx* ctx, double* logpi, float* grad_ll, double* la, double* lb);
+
+/* The annealed row order (Sec. 3: mini-batches drawn without replacement):
+ * perm[r] = index of the training row stored at position r, [n] int32 host. */
+smc_status smc_get_permutation(smc_ctx* ctx, int32_t* perm);
+
+/* Normalised weights [J] (host). */
+smc_status smc_get_weights(smc_ctx* ctx, double* wn);
+
+/* Ancestor indices [J] chosen by the last resampling (host). */
+smc_status smc_get_ancestors(smc_ctx* ctx, int32_t* ancestors);
+
+/* Kernel launches made by this context so far, and per-family CUDA-event times
+ * in milliseconds (accumulated while smc_config.timing = 1).  Family order:
+ * 0 first-layer forward GEMM, 1 head/adjoint, 2 first-layer weight-gradient GEMM,
+ * 3 hidden-layer GEMMs, 4 leapfrog, 5 weights/normalise/ESS, 6 resample+gather,
+ * 7 other network kernels (SIMT path), 8 partial reductions.  times may be NULL;
+ * n_fam is the capacity of times. */
+smc_status smc_get_counters(smc_ctx* ctx, int64_t* launches, double* times, int32_t n_fam,
+                            int64_t* calls_per_family);
+smc_status smc_reset_counters(smc_ctx* ctx);
+
+/* ------------------------------------------ stateless kernels (device pointers) */
+
+/* Normalise log-weights [J] (device) into wn [J] (device) and write J_eff to
+ * *ess_dev (device, 1 double): eqs. normalise and jeff in FP64. */
+smc_status smc_k_normalise(const double* logw_dev, int32_t J, double* wn_dev,
+                           double* ess_dev, void* stream);
+
+/* Ancestors [J] (device int32) from normalised weights wn [J] (device, FP64)
+ * and uniforms u (host: 1 value for systematic, J for multinomial). */
+smc_status smc_k_resample(const double* wn_dev, int32_t J, int32_t kind,
+                          const double* u_host, int32_t* ancestors_dev, void* stream);
+
+/* n standard normals of the (seed, stream_id, iteration) Philox4x32-10 +
+ * Box-Muller sequence starting at `offset` (device float32 out). */
+smc_status smc_k_philox_normals(uint64_t seed, uint32_t stream_id, uint32_t iteration,
+                                uint64_t offset, int64_t n, float* out_dev, void* stream);
+
+/* Raw Philox4x32-10 blocks: out_dev [n][4] u32 for counters (q, 0, c2, c3),
+ * q = 0..n-1, under key (k0, k1). */
+smc_status smc_k_philox_u32(uint32_t k0, uint32_t k1, uint32_t c2, uint32_t c3,
+                            int64_t n, uint32_t* out_dev, void* stream);
+
+/* C[m][n] = sum_k A[m][k] B[n][k] on tcgen05 tensor cores: A [M][K] and B [N][K]
+ * BF16 row-major with row pitches lda, ldb (elements, multiples of 8), C FP32
+ * row-major with pitch ldc.  Device pointers.  K-tails and ragged M/N are
+ * handled (TMA zero fill).  accumulate != 0 adds into C. */
+smc_status smc_k_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb,
+                           float* C, int64_t ldc, int64_t M, int64_t N, int64_t K,
+                           int32_t accumulate, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMC_H */

@@ -1,0 +1,782 @@
+// C ABI of libsmc: context lifecycle, annealing schedules, the SMC iteration
+// (move + reweight, anneal, resample), prediction, state access and the
+// stateless kernel entry points.  Host code only orchestrates: every step of
+// the sampler's arithmetic runs in the kernels of k_smc.cu / k_simt.cu / k_tc.cu.
+#include "internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+using namespace smc;
+
+namespace smc {
+
+smc_status fail(smc_ctx* c, smc_status s, const std::string& msg) {
+    if (c) {
+        c->last_error = msg;
+        if (s == SMC_ECUDA || s == SMC_ETIMEOUT) c->failed = true;
+    }
+    return s;
+}
+
+smc_status cuda_check(smc_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return SMC_OK;
+    return fail(c, SMC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void fam_begin(smc_ctx* c, int f) {
+    c->fam_calls[f]++;
+    if (!c->timing) return;
+    if (!c->timers[f].a) {
+        cudaEventCreate(&c->timers[f].a);
+        cudaEventCreate(&c->timers[f].b);
+    }
+    cudaEventRecord(c->timers[f].a, c->stream);
+}
+
+void fam_end(smc_ctx* c, int f) {
+    if (!c->timing) return;
+    cudaEventRecord(c->timers[f].b, c->stream);
+    cudaEventSynchronize(c->timers[f].b);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, c->timers[f].a, c->timers[f].b);
+    c->fam_ms[f] += ms;
+}
+
+}  // namespace smc
+
+namespace {
+
+// ------------------------------------------------------------- host RNG
+// SplitMix64 (Steele, Lea, Flood 2014).
+uint64_t splitmix_next(uint64_t& s) {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+double splitmix_double(uint64_t& s) { return (double)(splitmix_next(s) >> 11) * (1.0 / 9007199254740992.0); }
+
+// Mini-batch order (Sec. 3: batches drawn without replacement): Fisher-Yates
+// from the last position down, j = floor(r (i + 1) / 2^64).
+void fisher_yates(std::vector<int32_t>& a, uint64_t seed) {
+    uint64_t s = seed;
+    for (int64_t i = (int64_t)a.size() - 1; i >= 1; --i) {
+        const uint64_t r = splitmix_next(s);
+        const uint64_t j = (uint64_t)(((unsigned __int128)r * (uint64_t)(i + 1)) >> 64);
+        std::swap(a[i], a[j]);
+    }
+}
+
+// ------------------------------------------------------------- schedules
+// Sec. 3.1: Constant, FB, CTR, Linear, Automated; k < 0.9K evaluated as 10k < 9K.
+int64_t subset_size(int kind, int64_t k, int64_t N, int64_t C, int64_t kappa, int64_t K) {
+    C = std::min(C, N);
+    const bool late = 10 * k >= 9 * K;
+    switch (kind) {
+        case SMC_SCHED_CONSTANT: return C;
+        case SMC_SCHED_FB: return N;
+        case SMC_SCHED_CTR: return late ? N : C;
+        case SMC_SCHED_LINEAR: return late ? N : std::min(N, kappa * k + C);
+        case SMC_SCHED_AUTOMATED: {
+            if (late) return N;
+            const int64_t inc = (10 * (N - C)) / (9 * K);
+            int64_t m = C + inc * k;
+            m = ((2 * m + kappa) / (2 * kappa)) * kappa;   // nearest multiple of kappa, ties upward
+            return std::max(C, std::min(N, m));
+        }
+        default: return N;
+    }
+}
+
+bool ok_ctx(smc_ctx* c) { return c != nullptr && !c->failed; }
+
+smc_status sync_and_check(smc_ctx* c, const char* what) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, what);
+    int err = 0;
+    e = cudaMemcpy(&err, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_check(c, e, what);
+    if (err != 0) return fail(c, SMC_ETIMEOUT, std::string(what) + ": device wait timed out (code " + std::to_string(err) + ")");
+    return SMC_OK;
+}
+
+// Set the target's row regions for the current iteration (fixed schedules) or
+// from the SDA state.
+struct SdaHost { int64_t m_full = 0, block = 0; };
+SdaHost g_unused;
+
+void set_regions_fixed(smc_ctx* c) {
+    const smc_schedule& s = c->sched;
+    const int64_t M = subset_size(s.kind, c->k, c->N, s.C, s.kappa, s.K);
+    c->rows_a = M;
+    c->coef_a = c->scaled ? (double)c->N / (double)M : 1.0;
+    c->rows_b = 0;
+    c->coef_b = 0.0;
+    c->beta = 1.0;
+}
+
+smc_status engine_eval(smc_ctx* c) {
+    smc_status st = (c->precision == SMC_PREC_BF16) ? tc_eval(c) : simt_eval(c);
+    if (st != SMC_OK) return st;
+    c->grad_target_id = c->target_id;
+    return SMC_OK;
+}
+
+smc_status read_stats(smc_ctx* c, smc_step_stats* out, int grad_evals, const char* what) {
+    cudaError_t e = cudaMemcpyAsync(c->stats_host, c->stats_dev, 16 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, what);
+    smc_status st = sync_and_check(c, what);
+    if (st != SMC_OK) return st;
+    c->ess = c->stats_host[0];
+    const int nonfin = (int)c->stats_host[3];
+    if (out) {
+        out->ess = c->stats_host[0];
+        out->mean_logpi = c->stats_host[2];
+        out->beta = c->beta;
+        out->rows = c->rows_a + c->rows_b;
+        out->k = c->k;
+        out->n_nonfinite = nonfin;
+        out->grad_evals = grad_evals;
+    }
+    if (!std::isfinite(c->stats_host[1])) return fail(c, SMC_ENUMERIC, "every log-weight is -inf or NaN");
+    return SMC_OK;
+}
+
+int64_t rup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+void free_all(smc_ctx* c) {
+    if (c->precision == SMC_PREC_BF16) tc_free(c); else simt_free(c);
+    void* ps[] = {c->X, c->Y, c->Yv, c->Xb, c->XTa, c->theta, c->theta_alt, c->mom, c->grad, c->grad_alt,
+                  c->shadow, c->logw, c->wn, c->logpi, c->logpi_alt, c->la, c->lb, c->la_alt, c->lb_alt, c->part,
+                  c->stats_dev, c->anc, c->u_dev, c->err_dev, c->inv_mass, c->z_inject};
+    for (void* p : ps) cudaFree(p);
+    if (c->stats_host) cudaFreeHost(c->stats_host);
+    for (auto& t : c->timers) {
+        if (t.a) cudaEventDestroy(t.a);
+        if (t.b) cudaEventDestroy(t.b);
+    }
+}
+
+template <typename T>
+bool dalloc(T*& p, size_t n) {
+    return cudaMalloc((void**)&p, std::max<size_t>(n, 1) * sizeof(T)) == cudaSuccess;
+}
+
+// canonical [J][D] (host) <-> segment-major (host mirror of the device layout)
+void canon_to_seg(const smc_ctx* c, const float* canon, std::vector<float>& seg) {
+    const int64_t total = c->segs.back().off + (int64_t)c->J * c->segs.back().size;
+    seg.assign(total, 0.0f);
+    for (const Segment& s : c->segs)
+        for (int j = 0; j < c->J; ++j)
+            std::memcpy(&seg[s.off + j * s.size], canon + (int64_t)j * c->D + s.canon, s.size * sizeof(float));
+}
+void seg_to_canon(const smc_ctx* c, const std::vector<float>& seg, float* canon) {
+    for (const Segment& s : c->segs)
+        for (int j = 0; j < c->J; ++j)
+            std::memcpy(canon + (int64_t)j * c->D + s.canon, &seg[s.off + j * s.size], s.size * sizeof(float));
+}
+int64_t flat_size(const smc_ctx* c) { return c->segs.back().off + (int64_t)c->J * c->segs.back().size; }
+
+}  // namespace
+
+extern "C" {
+
+const char* smc_status_string(smc_status s) {
+    switch (s) {
+        case SMC_OK: return "ok";
+        case SMC_EINVAL: return "invalid argument";
+        case SMC_ENOMEM: return "out of memory";
+        case SMC_ECUDA: return "CUDA error";
+        case SMC_ESTATE: return "invalid state";
+        case SMC_ENUMERIC: return "numerical failure";
+        case SMC_ETIMEOUT: return "device wait timed out";
+        case SMC_EUNSUPPORTED: return "unsupported";
+    }
+    return "unknown";
+}
+
+const char* smc_last_error(const smc_ctx* c) { return c ? c->last_error.c_str() : "no context"; }
+
+int64_t smc_num_params(const smc_ctx* c) { return c ? c->D : 0; }
+
+smc_status smc_init(const smc_model* model, const smc_data* train, const smc_config* cfg, smc_ctx** out) {
+    if (!out) return SMC_EINVAL;
+    *out = nullptr;
+    if (!model || !train || !cfg || model->version != SMC_ABI_VERSION || cfg->version != SMC_ABI_VERSION)
+        return SMC_EINVAL;
+    if (cfg->n_particles < 1 || cfg->n_particles > kMaxParticles || model->n_layers < 1 ||
+        model->n_layers > kMaxLayers || !model->layers || train->n < 1 || !train->x || !(model->prior_sigma > 0))
+        return SMC_EINVAL;
+    smc_ctx* c = new smc_ctx();
+    c->J = cfg->n_particles;
+    c->precision = cfg->precision;
+    c->resampler = cfg->resampler;
+    c->scaled = cfg->scaled ? 1 : 0;
+    c->seed = cfg->seed;
+    c->stream = (cudaStream_t)cfg->stream;
+    c->timing = cfg->timing != 0;
+    c->likelihood = model->likelihood;
+    c->activation = model->activation;
+    c->prior_sigma = model->prior_sigma;
+    c->noise_sigma = model->noise_sigma > 0 ? model->noise_sigma : 1.0;
+    c->chunk = cfg->chunk_rows;
+    c->split_state = cfg->seed ^ 0xA5A5A5A5A5A5A5A5ull;
+    auto bad = [&](const std::string& m) { c->last_error = m; delete c; return SMC_EINVAL; };
+
+    // ---- layer shapes, activations, parameter segments
+    int cc = model->in_c, hh = model->in_h, ww = model->in_w;
+    if (cc < 1 || hh < 1 || ww < 1) return bad("input shape");
+    c->in_feat = (int64_t)cc * hh * ww;
+    int last_param = -1;
+    for (int l = 0; l < model->n_layers; ++l)
+        if (model->layers[l].kind != SMC_LAYER_MAXPOOL2) last_param = l;
+    if (last_param != model->n_layers - 1) return bad("the last layer must be dense or conv");
+    int64_t canon = 0, off = 0;
+    for (int l = 0; l < model->n_layers; ++l) {
+        const smc_layer& m = model->layers[l];
+        Layer L{};
+        L.kind = m.kind;
+        L.in_c = cc; L.in_h = hh; L.in_w = ww;
+        int64_t wsz = 0, bsz = 0;
+        if (m.kind == SMC_LAYER_DENSE) {
+            if (m.n_in != (int64_t)cc * hh * ww || m.n_out < 1) return bad("dense layer shape");
+            L.in_c = m.n_in; L.in_h = 1; L.in_w = 1;
+            L.out_c = m.n_out; L.out_h = 1; L.out_w = 1;
+            wsz = (int64_t)m.n_out * m.n_in;
+            bsz = m.n_out;
+        } else if (m.kind == SMC_LAYER_CONV) {
+            if (m.n_in != cc || m.n_out < 1 || m.ksize < 1 || m.ksize > 5 || m.ksize > hh || m.ksize > ww)
+                return bad("conv layer shape");
+            L.ksize = m.ksize;
+            L.out_c = m.n_out; L.out_h = hh - m.ksize + 1; L.out_w = ww - m.ksize + 1;
+            wsz = (int64_t)m.n_out * m.n_in * m.ksize * m.ksize;
+            bsz = m.n_out;
+        } else if (m.kind == SMC_LAYER_MAXPOOL2) {
+            if (hh < 2 || ww < 2) return bad("pool input too small");
+            L.out_c = cc; L.out_h = hh / 2; L.out_w = ww / 2;
+        } else {
+            return bad("unknown layer kind");
+        }
+        L.act = (m.kind == SMC_LAYER_MAXPOOL2 || l == last_param) ? SMC_ACT_IDENTITY : model->activation;
+        if (wsz > 0) {
+            L.seg_w = (int)c->segs.size();
+            c->segs.push_back({wsz, off, canon});
+            canon += wsz;
+            off = rup(off + (int64_t)c->J * wsz, 64);
+            L.seg_b = (int)c->segs.size();
+            c->segs.push_back({bsz, off, canon});
+            canon += bsz;
+            off = rup(off + (int64_t)c->J * bsz, 64);
+        }
+        c->layers.push_back(L);
+        cc = L.out_c; hh = L.out_h; ww = L.out_w;
+    }
+    if ((int)c->segs.size() > kMaxSegments) return bad("too many layers");
+    c->D = canon;
+    c->n_out = (int)c->layers.back().out_feat();
+    if (c->likelihood == SMC_LIK_CATEGORICAL && (c->n_out < 2 || c->n_out > 16)) return bad("2..16 classes");
+    if (c->likelihood == SMC_LIK_GAUSSIAN && c->n_out != 1) return bad("Gaussian likelihood needs one output");
+    if (c->likelihood == SMC_LIK_CATEGORICAL && !train->y_class) return bad("class labels missing");
+    if (c->likelihood == SMC_LIK_GAUSSIAN && !train->y_value) return bad("regression targets missing");
+    if (c->precision == SMC_PREC_BF16) {
+        std::string why;
+        if (tc_check_model(c, &why) != SMC_OK) {
+            c->last_error = why;
+            delete c;
+            return SMC_EUNSUPPORTED;
+        }
+    } else if (c->precision != SMC_PREC_FP32) {
+        return bad("precision");
+    }
+
+    smc_status st = SMC_OK;
+    auto cfail = [&](cudaError_t e, const char* w) {
+        st = cuda_check(c, e, w);
+        return st;
+    };
+    cudaGetDevice(&c->device);
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+
+    // ---- training data in the annealed order
+    c->N = train->n;
+    c->Npad = rup(c->N, 128);
+    c->perm.resize(c->N);
+    for (int64_t i = 0; i < c->N; ++i) c->perm[i] = (int32_t)i;
+    fisher_yates(c->perm, c->seed);
+    const size_t xbytes = (size_t)c->N * c->in_feat * sizeof(float);
+    float* xsrc = nullptr;
+    int32_t* ysrc = nullptr;
+    float* yvsrc = nullptr;
+    int32_t* perm_dev = nullptr;
+    bool ok = dalloc(c->X, (size_t)c->N * c->in_feat) && dalloc(c->Y, c->N) && dalloc(c->Yv, c->N) &&
+              dalloc(perm_dev, c->N);
+    if (ok && !train->on_device) {
+        ok = dalloc(xsrc, (size_t)c->N * c->in_feat) && dalloc(ysrc, c->N) && dalloc(yvsrc, c->N);
+    }
+    if (!ok) {
+        cudaFree(xsrc); cudaFree(ysrc); cudaFree(yvsrc); cudaFree(perm_dev);
+        free_all(c);
+        delete c;
+        return SMC_ENOMEM;
+    }
+    const float* xs = train->x;
+    const int32_t* ys = train->y_class;
+    const float* yvs = train->y_value;
+    cudaError_t e = cudaSuccess;
+    if (!train->on_device) {
+        e = cudaMemcpyAsync(xsrc, train->x, xbytes, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess && ys) e = cudaMemcpyAsync(ysrc, ys, c->N * 4, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess && yvs) e = cudaMemcpyAsync(yvsrc, yvs, c->N * 4, cudaMemcpyHostToDevice, c->stream);
+        xs = xsrc;
+        ys = ys ? ysrc : nullptr;
+        yvs = yvs ? yvsrc : nullptr;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(perm_dev, c->perm.data(), c->N * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_permute_rows(c, xs, ys, yvs, perm_dev);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(xsrc); cudaFree(ysrc); cudaFree(yvsrc); cudaFree(perm_dev);
+    if (e != cudaSuccess) {
+        cfail(e, "data upload");
+        std::string m = c->last_error;
+        free_all(c);
+        delete c;
+        (void)m;
+        return SMC_ECUDA;
+    }
+
+    // ---- particle state
+    const int64_t flat = flat_size(c);
+    c->flat = flat;
+    const int J = c->J;
+    ok = dalloc(c->theta, flat) && dalloc(c->theta_alt, flat) && dalloc(c->mom, flat) && dalloc(c->grad, flat) &&
+         dalloc(c->grad_alt, flat) && dalloc(c->logw, J) && dalloc(c->wn, J) && dalloc(c->logpi, J) &&
+         dalloc(c->logpi_alt, J) && dalloc(c->la, J) && dalloc(c->lb, J) && dalloc(c->la_alt, J) &&
+         dalloc(c->lb_alt, J) && dalloc(c->part, (size_t)3 * J * kMaxPartChunks) &&
+         dalloc(c->stats_dev, 16 + kMaxParticles) && dalloc(c->anc, J) && dalloc(c->u_dev, J) &&
+         dalloc(c->err_dev, 1) && dalloc(c->inv_mass, kMaxSegments);
+    if (ok) ok = cudaMallocHost((void**)&c->stats_host, 64 * sizeof(double)) == cudaSuccess;
+    if (ok && c->precision == SMC_PREC_BF16) {
+        c->xta_rows = rup(c->in_feat + 1, 8);
+        ok = dalloc(c->shadow, (size_t)J * c->segs[c->layers[0].seg_w].size) &&
+             dalloc(c->Xb, (size_t)c->Npad * c->in_feat) && dalloc(c->XTa, (size_t)c->xta_rows * c->Npad);
+    }
+    if (ok) ok = ((c->precision == SMC_PREC_BF16) ? tc_alloc(c) : simt_alloc(c)) == SMC_OK;
+    if (!ok) {
+        free_all(c);
+        delete c;
+        return SMC_ENOMEM;
+    }
+    cudaMemsetAsync(c->theta, 0, flat * sizeof(float), c->stream);
+    cudaMemsetAsync(c->grad, 0, flat * sizeof(float), c->stream);
+    cudaMemsetAsync(c->part, 0, (size_t)3 * J * kMaxPartChunks * sizeof(double), c->stream);
+    cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
+    std::vector<float> ones(kMaxSegments, 1.0f);
+    e = cudaMemcpyAsync(c->inv_mass, ones.data(), kMaxSegments * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && c->precision == SMC_PREC_BF16) e = launch_bf16_data(c);
+    // theta_0 ~ q_0 = N(0, sigma^2 I) (eq. init_weight)
+    if (e == cudaSuccess) e = launch_prior_draw(c);
+    if (e == cudaSuccess) e = launch_shadow(c);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return SMC_ECUDA;
+    }
+    *out = c;
+    return SMC_OK;
+}
+
+void smc_destroy(smc_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+smc_status smc_set_schedule(smc_ctx* c, const smc_schedule* s, smc_step_stats* stats) {
+    if (!c || !s) return SMC_EINVAL;
+    if (!ok_ctx(c)) return SMC_ESTATE;
+    if (s->kind < SMC_SCHED_CONSTANT || s->kind > SMC_SCHED_SDA || s->C < 1 || s->kappa < 1 || s->K < 1 ||
+        s->k_start < 0)
+        return fail(c, SMC_EINVAL, "schedule arguments");
+    c->sched = *s;
+    c->k = s->k_start;
+    if (s->kind == SMC_SCHED_SDA) {
+        // eq. sda_initial_target: the first C rows tempered by beta_0, nothing fully included yet
+        c->rows_a = 0;
+        c->coef_a = 1.0;
+        c->rows_b = std::min<int64_t>(s->C, c->N);
+        c->beta = s->beta0 > 0 ? s->beta0 : 0.1;
+        c->coef_b = c->beta;
+    } else {
+        set_regions_fixed(c);
+    }
+    c->target_id++;
+    c->step_index = 0;
+    smc_status st = engine_eval(c);
+    if (st != SMC_OK) return st;
+    cudaError_t e = launch_sqnorm(c, 0);
+    if (e == cudaSuccess) e = launch_weights(c, 0);
+    if (e != cudaSuccess) return cuda_check(c, e, "initial weights");
+    c->scheduled = true;
+    return read_stats(c, stats, 1, "set_schedule");
+}
+
+smc_status smc_step(smc_ctx* c, const smc_step_params* p, smc_step_stats* stats) {
+    if (!c || !p) return SMC_EINVAL;
+    if (!ok_ctx(c) || !c->scheduled) return SMC_ESTATE;
+    if (!(p->h >= 0.0) || p->S < 1 || p->S > 1000) return fail(c, SMC_EINVAL, "step arguments");
+    if (p->proposal != SMC_PROPOSAL_PLAIN) return fail(c, SMC_EUNSUPPORTED, "learned proposal not built");
+    int evals = 0;
+    smc_status st;
+    // gradient of log pi_k at theta_{k-1} (the target may have changed since it was cached)
+    if (c->grad_target_id != c->target_id) {
+        if ((st = engine_eval(c)) != SMC_OK) return st;
+        ++evals;
+    }
+    cudaError_t e = launch_momentum(c, c->pending_noise);
+    c->pending_noise = false;
+    const double h = p->h;
+    fam_begin(c, F_LEAPFROG);
+    if (e == cudaSuccess) e = launch_leapfrog(c, 0, 0.5 * h, h, 0);
+    fam_end(c, F_LEAPFROG);
+    if (e != cudaSuccess) return cuda_check(c, e, "leapfrog");
+    for (int s = 0; s < p->S; ++s) {
+        if ((st = engine_eval(c)) != SMC_OK) return st;
+        ++evals;
+        fam_begin(c, F_LEAPFROG);
+        e = (s + 1 < p->S) ? launch_leapfrog(c, 1, h, h, 0) : launch_leapfrog(c, 2, 0.5 * h, 0.0, 0);
+        fam_end(c, F_LEAPFROG);
+        if (e != cudaSuccess) return cuda_check(c, e, "leapfrog");
+    }
+    fam_begin(c, F_WEIGHTS);
+    e = launch_weights(c, 1);
+    fam_end(c, F_WEIGHTS);
+    if (e != cudaSuccess) return cuda_check(c, e, "weights");
+    c->step_index++;
+    return read_stats(c, stats, evals, "step");
+}
+
+smc_status smc_anneal_next(smc_ctx* c, smc_anneal_info* info) {
+    if (!c) return SMC_EINVAL;
+    if (!ok_ctx(c) || !c->scheduled) return SMC_ESTATE;
+    const int64_t before = c->rows_a + c->rows_b;
+    int appended = 0;
+    c->k++;
+    if (c->sched.kind != SMC_SCHED_SDA) {
+        const int64_t old_a = c->rows_a;
+        const double old_c = c->coef_a;
+        set_regions_fixed(c);
+        if (c->rows_a != old_a || c->coef_a != old_c) c->target_id++;
+        appended = c->rows_a > old_a;
+    } else if (c->beta >= 1.0) {
+        // "append an additional MB and reinitialise beta" (Sec. 3.1)
+        if (c->rows_a + c->rows_b >= c->N) {
+            c->rows_a = c->N;
+            c->rows_b = 0;
+            c->beta = 1.0;
+        } else {
+            c->rows_a += c->rows_b;
+            c->rows_b = std::min<int64_t>(c->sched.kappa, c->N - c->rows_a);
+            c->beta = c->sched.beta_reinit > 0 ? c->sched.beta_reinit : 0.1;
+            appended = 1;
+        }
+        c->coef_a = 1.0;
+        c->coef_b = c->rows_b > 0 ? c->beta : 0.0;
+        c->target_id++;
+    } else {
+        // eqs. beta_initial_data_k / beta_annealed_k with the weighted moments
+        cudaError_t e = launch_sda_moments(c);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->stats_host + 8, c->stats_dev + 8, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                                c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "sda moments");
+        smc_status st = sync_and_check(c, "sda moments");
+        if (st != SMC_OK) return st;
+        const double e_oh = c->stats_host[8], e_oh2 = c->stats_host[9], e_o = c->stats_host[10],
+                     e_ooh = c->stats_host[11];
+        const double var = e_oh2 - e_oh * e_oh;
+        const double cov = e_ooh - e_o * e_oh;
+        const double den = var + cov;
+        const double dS = c->sched.delta_s > 0 ? c->sched.delta_s : 1.0;
+        double nb;
+        if (den == 0.0 || !std::isfinite(den)) {
+            nb = 1.0;
+        } else {
+            nb = c->beta - dS / den;
+            if (nb <= c->beta) nb = c->beta + dS / den;
+            nb = std::min(nb, 1.0);
+        }
+        c->beta = nb;
+        c->coef_b = nb;
+        c->target_id++;
+    }
+    if (info) {
+        info->appended = appended;
+        info->k = c->k;
+        info->rows = c->rows_a + c->rows_b;
+        info->rows_full = c->sched.kind == SMC_SCHED_SDA ? c->rows_a : c->rows_a;
+        info->beta = c->beta;
+    }
+    (void)before;
+    return SMC_OK;
+}
+
+smc_status smc_resample(smc_ctx* c, int32_t force, int32_t* did) {
+    if (!c) return SMC_EINVAL;
+    if (!ok_ctx(c) || !c->scheduled) return SMC_ESTATE;
+    if (did) *did = 0;
+    if (!force && !(c->ess < 0.5 * c->J)) return SMC_OK;
+    const int kind = c->resampler;
+    const int nu = kind == SMC_RESAMPLE_SYSTEMATIC ? 1 : c->J;
+    std::vector<double> u(nu);
+    for (int i = 0; i < nu; ++i)
+        u[i] = (i < (int)c->pending_u.size()) ? c->pending_u[i] : splitmix_double(c->split_state);
+    c->pending_u.clear();
+    std::memcpy(c->stats_host + 32, u.data(), std::min(nu, 32) * sizeof(double));
+    cudaError_t e = cudaMemcpyAsync(c->u_dev, u.data(), nu * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    fam_begin(c, F_RESAMPLE);
+    if (e == cudaSuccess) e = launch_resample(c, kind, nu);
+    if (e == cudaSuccess) e = launch_gather(c);
+    fam_end(c, F_RESAMPLE);
+    if (e != cudaSuccess) return cuda_check(c, e, "resample");
+    std::swap(c->theta, c->theta_alt);
+    std::swap(c->grad, c->grad_alt);
+    std::swap(c->logpi, c->logpi_alt);
+    std::swap(c->la, c->la_alt);
+    std::swap(c->lb, c->lb_alt);
+    e = launch_shadow(c);
+    if (e != cudaSuccess) return cuda_check(c, e, "shadow");
+    smc_status st = sync_and_check(c, "resample");   // u is a stack buffer
+    if (st != SMC_OK) return st;
+    c->ess = (double)c->J;
+    c->resample_count++;
+    if (did) *did = 1;
+    return SMC_OK;
+}
+
+smc_status smc_posterior_predict(smc_ctx* c, const float* x, int64_t n, int32_t on_device, float* probs) {
+    if (!c || !x || !probs || n < 1) return SMC_EINVAL;
+    if (!ok_ctx(c)) return SMC_ESTATE;
+    if (c->likelihood != SMC_LIK_CATEGORICAL) return fail(c, SMC_EUNSUPPORTED, "predictive needs categorical");
+    const float* xd = x;
+    float* od = probs;
+    float* tx = nullptr;
+    float* to = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!on_device) {
+        if (!dalloc(tx, (size_t)n * c->in_feat) || !dalloc(to, (size_t)n * c->n_out)) {
+            cudaFree(tx);
+            return fail(c, SMC_ENOMEM, "predict buffers");
+        }
+        e = cudaMemcpyAsync(tx, x, (size_t)n * c->in_feat * 4, cudaMemcpyHostToDevice, c->stream);
+        xd = tx;
+        od = to;
+    }
+    smc_status st = SMC_OK;
+    if (e != cudaSuccess) st = cuda_check(c, e, "predict upload");
+    if (st == SMC_OK) st = (c->precision == SMC_PREC_BF16) ? tc_predict(c, xd, n, od) : simt_predict(c, xd, n, od);
+    if (st == SMC_OK && !on_device) {
+        e = cudaMemcpyAsync(probs, od, (size_t)n * c->n_out * 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) st = cuda_check(c, e, "predict download");
+    }
+    if (st == SMC_OK) st = sync_and_check(c, "predict");
+    cudaFree(tx);
+    cudaFree(to);
+    return st;
+}
+
+smc_status smc_upload_rows(smc_ctx* c, int64_t row0, int64_t n, const float* x, const int32_t* y, const float* yv) {
+    if (!c || !x || n < 0 || row0 < 0 || row0 + n > c->N) return SMC_EINVAL;
+    if (!ok_ctx(c)) return SMC_ESTATE;
+    if (n == 0) return SMC_OK;
+    cudaError_t e = cudaMemcpyAsync(c->X + row0 * c->in_feat, x, (size_t)n * c->in_feat * 4, cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e == cudaSuccess && y) e = cudaMemcpyAsync(c->Y + row0, y, n * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && yv) e = cudaMemcpyAsync(c->Yv + row0, yv, n * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && c->precision == SMC_PREC_BF16) e = launch_bf16_data(c);
+    if (e != cudaSuccess) return cuda_check(c, e, "upload rows");
+    return SMC_OK;
+}
+
+smc_status smc_get_state(smc_ctx* c, float* theta, double* logw, double* logpi) {
+    if (!c) return SMC_EINVAL;
+    if (!ok_ctx(c)) return SMC_ESTATE;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && theta) {
+        std::vector<float> seg(flat_size(c));
+        e = cudaMemcpy(seg.data(), c->theta, seg.size() * 4, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) seg_to_canon(c, seg, theta);
+    }
+    if (e == cudaSuccess && logw) e = cudaMemcpy(logw, c->logw, c->J * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && logpi) e = cudaMemcpy(logpi, c->logpi, c->J * 8, cudaMemcpyDeviceToHost);
+    return cuda_check(c, e, "get_state");
+}
+
+smc_status smc_set_state(smc_ctx* c, const float* theta, const double* logw, const double* logpi) {
+    if (!c) return SMC_EINVAL;
+    if (!ok_ctx(c)) return SMC_ESTATE;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && theta) {
+        std::vector<float> seg;
+        canon_to_seg(c, theta, seg);
+        e = cudaMemcpy(c->theta, seg.data(), seg.size() * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = launch_shadow(c);
+        c->grad_target_id = ~0ull;
+    }
+    if (e == cudaSuccess && logw) e = cudaMemcpy(c->logw, logw, c->J * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && logpi) e = cudaMemcpy(c->logpi, logpi, c->J * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && logw) {
+        e = launch_normalise_only(c);
+        if (e == cudaSuccess) return read_stats(c, nullptr, 0, "set_state");
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_check(c, e, "set_state");
+}
+
+smc_status smc_set_noise(smc_ctx* c, const float* z) {
+    if (!c || !z) return SMC_EINVAL;
+    if (!ok_ctx(c)) return SMC_ESTATE;
+    if (!c->z_inject && !dalloc(c->z_inject, (size_t)c->J * c->D)) return fail(c, SMC_ENOMEM, "noise staging");
+    cudaError_t e = cudaMemcpyAsync(c->z_inject, z, (size_t)c->J * c->D * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "set_noise");
+    c->pending_noise = true;
+    return SMC_OK;
+}
+
+smc_status smc_set_uniforms(smc_ctx* c, const double* u, int32_t n) {
+    if (!c || !u || n < 1 || n > c->J) return SMC_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!(u[i] >= 0.0 && u[i] < 1.0)) return fail(c, SMC_EINVAL, "uniform outside [0, 1)");
+    c->pending_u.assign(u, u + n);
+    return SMC_OK;
+}
+
+smc_status smc_eval(smc_ctx* c, double* logpi, float* grad_ll, double* la, double* lb) {
+    if (!c) return SMC_EINVAL;
+    if (!ok_ctx(c) || !c->scheduled) return SMC_ESTATE;
+    smc_status st = engine_eval(c);
+    if (st != SMC_OK) return st;
+    cudaError_t e = launch_sqnorm(c, 0);
+    if (e == cudaSuccess) e = launch_weights(c, 3);
+    if (e != cudaSuccess) return cuda_check(c, e, "eval");
+    if ((st = sync_and_check(c, "eval")) != SMC_OK) return st;
+    if (logpi) e = cudaMemcpy(logpi, c->stats_dev + 16, c->J * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && la) e = cudaMemcpy(la, c->la, c->J * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && lb) e = cudaMemcpy(lb, c->lb, c->J * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && grad_ll) {
+        std::vector<float> seg(flat_size(c));
+        e = cudaMemcpy(seg.data(), c->grad, seg.size() * 4, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) seg_to_canon(c, seg, grad_ll);
+    }
+    return cuda_check(c, e, "eval copy");
+}
+
+smc_status smc_get_permutation(smc_ctx* c, int32_t* perm) {
+    if (!c || !perm) return SMC_EINVAL;
+    std::memcpy(perm, c->perm.data(), c->perm.size() * sizeof(int32_t));
+    return SMC_OK;
+}
+
+smc_status smc_get_weights(smc_ctx* c, double* wn) {
+    if (!c || !wn) return SMC_EINVAL;
+    if (!ok_ctx(c)) return SMC_ESTATE;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(wn, c->wn, c->J * 8, cudaMemcpyDeviceToHost);
+    return cuda_check(c, e, "get_weights");
+}
+
+smc_status smc_get_ancestors(smc_ctx* c, int32_t* anc) {
+    if (!c || !anc) return SMC_EINVAL;
+    if (!ok_ctx(c)) return SMC_ESTATE;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(anc, c->anc, c->J * 4, cudaMemcpyDeviceToHost);
+    return cuda_check(c, e, "get_ancestors");
+}
+
+smc_status smc_get_counters(smc_ctx* c, int64_t* launches, double* times, int32_t n_fam, int64_t* calls) {
+    if (!c) return SMC_EINVAL;
+    if (launches) *launches = c->launches;
+    for (int f = 0; f < std::min<int>(n_fam, kFamilies); ++f) {
+        if (times) times[f] = c->fam_ms[f];
+        if (calls) calls[f] = c->fam_calls[f];
+    }
+    return SMC_OK;
+}
+
+smc_status smc_reset_counters(smc_ctx* c) {
+    if (!c) return SMC_EINVAL;
+    c->launches = 0;
+    for (int f = 0; f < kFamilies; ++f) { c->fam_ms[f] = 0; c->fam_calls[f] = 0; }
+    return SMC_OK;
+}
+
+// ------------------------------------------------------------ stateless
+smc_status smc_k_normalise(const double* logw, int32_t J, double* wn, double* ess, void* stream) {
+    if (!logw || !wn || !ess || J < 1 || J > kMaxParticles) return SMC_EINVAL;
+    cudaError_t e = k_normalise(logw, J, wn, ess, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    return e == cudaSuccess ? SMC_OK : SMC_ECUDA;
+}
+
+smc_status smc_k_resample(const double* wn, int32_t J, int32_t kind, const double* u_host, int32_t* anc,
+                          void* stream) {
+    if (!wn || !u_host || !anc || J < 1 || J > kMaxParticles) return SMC_EINVAL;
+    if (kind != SMC_RESAMPLE_SYSTEMATIC && kind != SMC_RESAMPLE_MULTINOMIAL) return SMC_EINVAL;
+    const int nu = kind == SMC_RESAMPLE_SYSTEMATIC ? 1 : J;
+    for (int i = 0; i < nu; ++i)
+        if (!(u_host[i] >= 0.0 && u_host[i] < 1.0)) return SMC_EINVAL;
+    double* ud = nullptr;
+    if (cudaMalloc(&ud, nu * sizeof(double)) != cudaSuccess) return SMC_ENOMEM;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(ud, u_host, nu * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = k_resample(wn, J, kind, ud, nu, anc, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(ud);
+    return e == cudaSuccess ? SMC_OK : SMC_ECUDA;
+}
+
+smc_status smc_k_philox_normals(uint64_t seed, uint32_t sid, uint32_t it, uint64_t off, int64_t n, float* out,
+                                void* stream) {
+    if (!out || n < 0) return SMC_EINVAL;
+    if (n == 0) return SMC_OK;
+    cudaError_t e = k_philox_normals(seed, sid, it, off, n, out, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    return e == cudaSuccess ? SMC_OK : SMC_ECUDA;
+}
+
+smc_status smc_k_philox_u32(uint32_t k0, uint32_t k1, uint32_t c2, uint32_t c3, int64_t n, uint32_t* out,
+                            void* stream) {
+    if (!out || n < 0) return SMC_EINVAL;
+    if (n == 0) return SMC_OK;
+    cudaError_t e = k_philox_u32(k0, k1, c2, c3, n, out, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    return e == cudaSuccess ? SMC_OK : SMC_ECUDA;
+}
+
+smc_status smc_k_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int64_t M,
+                           int64_t N, int64_t K, int32_t accumulate, void* stream) {
+    if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < N || (lda % 8) || (ldb % 8))
+        return SMC_EINVAL;
+    if (M > (1 << 30) || N > (1 << 30) || K > (1 << 30)) return SMC_EINVAL;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int* err = nullptr;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return SMC_ENOMEM;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = tc_gemm_public(A, lda, B, ldb, C, ldc, M, N, K, accumulate, s, err, sms);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (e != cudaSuccess) return SMC_ECUDA;
+    return herr ? SMC_ETIMEOUT : SMC_OK;
+}
+
+}  // extern "C"

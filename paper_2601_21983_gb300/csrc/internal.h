@@ -1,0 +1,216 @@
+// Internal declarations of libsmc: the sampler context, the parameter layout in
+// HBM and the engine entry points shared by the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/smc.h"
+
+namespace smc {
+
+constexpr int kMaxSegments = 32;
+constexpr int kMaxLayers = 16;
+constexpr int kMaxParticles = 4096;
+constexpr int kFamilies = 9;
+enum Family { F_FWD_GEMM = 0, F_HEAD = 1, F_WGRAD_GEMM = 2, F_HIDDEN_GEMM = 3, F_LEAPFROG = 4,
+              F_WEIGHTS = 5, F_RESAMPLE = 6, F_SIMT_NET = 7, F_REDUCE = 8 };
+
+// Philox stream identifiers (counter word 3).
+enum : uint32_t { RNG_PRIOR = 1, RNG_MOMENTUM = 2 };
+
+// Parameter layout in HBM ("segment-major"): every W and every b of every
+// parametric layer is one segment stored [J][size] contiguously, so a dense
+// layer's weights for all particles form one [J*n_out][n_in] matrix - the
+// operand layout of the grouped contractions.  Segments follow each other.
+struct Segment {
+    int64_t size;      // elements per particle
+    int64_t off;       // start of the [J][size] block in the flat buffer
+    int64_t canon;     // start within one particle's canonical vector
+};
+
+struct Layer {
+    int kind;                  // SMC_LAYER_*
+    int in_c, in_h, in_w;      // input feature map (dense: in_c = features, h = w = 1)
+    int out_c, out_h, out_w;
+    int ksize;
+    int act;                   // activation applied to this layer's output
+    int seg_w = -1, seg_b = -1;
+    int64_t in_feat() const { return (int64_t)in_c * in_h * in_w; }
+    int64_t out_feat() const { return (int64_t)out_c * out_h * out_w; }
+};
+
+struct DevTimer {
+    cudaEvent_t a = nullptr, b = nullptr;
+};
+
+}  // namespace smc
+
+struct smc_ctx {
+    // -------- configuration
+    int J = 0;
+    int64_t D = 0;
+    int64_t flat = 0;                // floats in the padded segment-major buffer
+    int precision = SMC_PREC_FP32;
+    int resampler = SMC_RESAMPLE_SYSTEMATIC;
+    int scaled = 1;
+    int likelihood = SMC_LIK_CATEGORICAL;
+    int activation = SMC_ACT_TANH;
+    double prior_sigma = 1.0, noise_sigma = 1.0;
+    uint64_t seed = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 148;
+    bool timing = false;
+    bool failed = false;
+    std::string last_error;
+
+    std::vector<smc::Layer> layers;
+    std::vector<smc::Segment> segs;
+    int n_out = 0;                   // logits per sample
+    int64_t in_feat = 0;
+
+    // -------- data (annealed order: row r of the device copy is training row perm[r])
+    int64_t N = 0, Npad = 0;
+    std::vector<int32_t> perm;
+    float* X = nullptr;              // [N][in_feat] float32
+    int32_t* Y = nullptr;            // [N] class labels
+    float* Yv = nullptr;             // [N] regression targets
+    __nv_bfloat16* Xb = nullptr;     // [Npad][in_feat]        (BF16 engine)
+    __nv_bfloat16* XTa = nullptr;    // [in_feat+1 (pad 8)][Npad], last used row = 1 (BF16 engine)
+    int64_t xta_rows = 0;
+
+    // -------- particle state (segment-major FP32)
+    float* theta = nullptr;          // [J*D]
+    float* theta_alt = nullptr;      // gather target
+    float* mom = nullptr;            // momentum [J*D]
+    float* grad = nullptr;           // cached sum_i c_i grad log p at theta under the current target
+    float* grad_alt = nullptr;
+    __nv_bfloat16* shadow = nullptr; // BF16 copy of the first layer's W segment (BF16 engine)
+    double* logw = nullptr;          // [J]
+    double* wn = nullptr;            // [J]
+    double* logpi = nullptr;         // [J] log pi of the target the particles were last weighted under
+    double* logpi_alt = nullptr;
+    double* la = nullptr;            // [J] unweighted log-likelihood sums, fully weighted rows
+    double* lb = nullptr;            // [J] tempered block
+    double* la_alt = nullptr;
+    double* lb_alt = nullptr;
+    double* part = nullptr;          // [3][J][kMaxPartChunks] per-particle partial sums
+    int part_chunks = 0;
+    double* stats_dev = nullptr;     // small device scratch for statistics
+    double* stats_host = nullptr;    // pinned mirror
+    int32_t* anc = nullptr;          // [J]
+    double* u_dev = nullptr;         // [J] uniforms
+    int* err_dev = nullptr;          // device-side error flag (timeouts)
+    float* inv_mass = nullptr;       // [n_segments] per-segment inverse mass (learned proposal)
+    float* z_inject = nullptr;       // device staging for injected momenta (canonical order)
+
+    // -------- network workspace
+    int64_t chunk = 0;               // rows per chunk
+    std::vector<float*> act;         // SIMT: [J][chunk][feat_l] per layer
+    std::vector<uint8_t*> pool_idx;  // SIMT: argmax per pool layer
+    float* delta[2] = {nullptr, nullptr};
+    float* rowll = nullptr;          // [J][chunk]
+    // BF16 engine workspace
+    __nv_bfloat16* H1 = nullptr;     // [chunk_pad][J*H]
+    __nv_bfloat16* dZT = nullptr;    // [J*H][chunk_pad]
+    float* head_part = nullptr;      // [slices][J][C*H + C]
+    double* head_ll = nullptr;       // [slices][J][2]
+    int64_t head_slices_cap = 0;
+    float* gemm_part = nullptr;      // split-K partials
+    int64_t gemm_part_cap = 0;
+
+    // -------- schedule / target
+    bool scheduled = false;
+    smc_schedule sched{};
+    int k = 0;
+    int64_t rows_a = 0, rows_b = 0;  // fully weighted rows, tempered block rows
+    double coef_a = 1.0, coef_b = 0.0, beta = 1.0;
+    uint64_t target_id = 0, grad_target_id = ~0ull;  // cached gradient validity
+    double ess = 0.0;
+    int step_index = 0;
+    int resample_count = 0;
+    uint64_t split_state = 0;        // host SplitMix64 state for resampling uniforms
+    std::vector<double> pending_u;   // injected uniforms
+    bool pending_noise = false;
+
+    // -------- accounting
+    int64_t launches = 0;
+    double fam_ms[smc::kFamilies] = {0};
+    int64_t fam_calls[smc::kFamilies] = {0};
+    smc::DevTimer timers[smc::kFamilies];
+};
+
+namespace smc {
+
+constexpr int kMaxPartChunks = 64;
+
+// error helpers (api.cu)
+smc_status fail(smc_ctx* c, smc_status s, const std::string& msg);
+smc_status cuda_check(smc_ctx* c, cudaError_t e, const char* what);
+
+// per-family timing around launches
+void fam_begin(smc_ctx* c, int fam);
+void fam_end(smc_ctx* c, int fam);
+
+// ----- SMC kernels (k_smc.cu)
+struct SegTable {
+    int n;
+    int64_t size[kMaxSegments], off[kMaxSegments], canon[kMaxSegments];
+    int tc[kMaxSegments];   // 1: segment has a BF16 shadow
+};
+SegTable seg_table(const smc_ctx* c);
+cudaError_t launch_prior_draw(smc_ctx* c);
+cudaError_t launch_momentum(smc_ctx* c, bool injected);
+cudaError_t launch_leapfrog(smc_ctx* c, int phase, double h_kick, double h_drift, int pidx);
+cudaError_t launch_sqnorm(smc_ctx* c, int pidx);
+cudaError_t launch_weights(smc_ctx* c, int mode);
+cudaError_t launch_normalise_only(smc_ctx* c);
+cudaError_t launch_sda_moments(smc_ctx* c);
+cudaError_t launch_resample(smc_ctx* c, int kind, int nu);
+cudaError_t launch_gather(smc_ctx* c);
+cudaError_t launch_shadow(smc_ctx* c);
+cudaError_t launch_permute_rows(smc_ctx* c, const float* src, const int32_t* srcy, const float* srcyv,
+                                const int32_t* perm_dev);
+cudaError_t launch_bf16_data(smc_ctx* c);
+cudaError_t launch_predict_reduce(smc_ctx* c, const float* logits, int64_t sj, int64_t sm, int64_t n,
+                                  float* out, double* acc_scratch);
+// stateless
+cudaError_t k_normalise(const double* logw, int J, double* wn, double* ess, cudaStream_t s);
+cudaError_t k_resample(const double* wn, int J, int kind, const double* u, int nu, int32_t* anc,
+                       cudaStream_t s);
+cudaError_t k_philox_normals(uint64_t seed, uint32_t sid, uint32_t it, uint64_t off, int64_t n,
+                             float* out, cudaStream_t s);
+cudaError_t k_philox_u32(uint32_t k0, uint32_t k1, uint32_t c2, uint32_t c3, int64_t n, uint32_t* out,
+                         cudaStream_t s);
+
+// ----- FP32 SIMT network engine (k_simt.cu)
+smc_status simt_alloc(smc_ctx* c);
+void simt_free(smc_ctx* c);
+// Evaluate sum_i c_i grad log p and the region log-likelihood sums at the current
+// particles over rows [0, rows_a + rows_b) into c->grad, c->la, c->lb.
+smc_status simt_eval(smc_ctx* c);
+// Weighted predictive probabilities for n rows of device x into device out [n][C].
+smc_status simt_predict(smc_ctx* c, const float* x, int64_t n, float* out);
+
+// ----- BF16 tensor-core engine (k_tc.cu)
+smc_status tc_check_model(const smc_ctx* c, std::string* why);
+smc_status tc_alloc(smc_ctx* c);
+void tc_free(smc_ctx* c);
+smc_status tc_eval(smc_ctx* c);
+smc_status tc_predict(smc_ctx* c, const float* x, int64_t n, float* out);
+cudaError_t tc_gemm_public(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
+                           int64_t M, int64_t N, int64_t K, int accumulate, cudaStream_t s, int* err_dev,
+                           int num_sms);
+
+}  // namespace smc
+
+// Launch helper: counts the launch and checks the launch error.
+#define SMC_LAUNCH(ctx, ...)                      \
+    do {                                          \
+        __VA_ARGS__;                              \
+        (ctx)->launches++;                        \
+    } while (0)

