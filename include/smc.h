@@ -161,7 +161,8 @@ void smc_destroy(smc_ctx* ctx);
 /* Human-readable name of a status code (static storage). */
 const char* smc_status_string(smc_status s);
 
-/* Last error message recorded by a context (static per context; never NULL). */
+/* Last error message recorded by a context (never NULL); with ctx = NULL, the
+ * last error of a stateless entry point on the calling thread. */
 const char* smc_last_error(const smc_ctx* ctx);
 
 /* Parameter count D of one particle. */
@@ -268,6 +269,24 @@ smc_status smc_k_normalise(const double* logw_dev, int32_t J, double* wn_dev,
  * and uniforms u (host: 1 value for systematic, J for multinomial). */
 smc_status smc_k_resample(const double* wn_dev, int32_t J, int32_t kind,
                           const double* u_host, int32_t* ancestors_dev, void* stream);
+
+/* Same result as smc_k_resample, for callers that cannot allocate device
+ * memory: code that runs while a stream is being captured, code under an
+ * allocator that owns all device memory, or a loop that cannot afford the
+ * device-wide synchronisation a cudaFree implies.  It calls no cudaMalloc,
+ * cudaFree or allocating library routine; the uniforms are staged in a static
+ * 32 KiB device array (4096 doubles) that every GPU loading the library keeps
+ * until the process exits.  The paper has no counterpart: this is a service of
+ * the library.  J above 4096 is rejected with SMC_EINVAL; smc_last_error(NULL)
+ * then names the limit.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current), so make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's uniforms; calls that overlap on the GPU (different
+ * streams, or threads) race on it, so serialise them.  The call synchronises
+ * `stream` before returning.  Device pointers wn_dev / ancestors_dev as in
+ * smc_k_resample; u_host is host memory. */
+smc_status smc_k_resample_noalloc(const double* wn_dev, int32_t J, int32_t kind,
+                                  const double* u_host, int32_t* ancestors_dev, void* stream);
 
 /* n standard normals of the (seed, stream_id, iteration) Philox4x32-10 +
  * Box-Muller sequence starting at `offset` (device float32 out). */

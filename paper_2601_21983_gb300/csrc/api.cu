@@ -198,7 +198,7 @@ const char* smc_status_string(smc_status s) {
     return "unknown";
 }
 
-const char* smc_last_error(const smc_ctx* c) { return c ? c->last_error.c_str() : "no context"; }
+const char* smc_last_error(const smc_ctx* c) { return c ? c->last_error.c_str() : smc::stateless_error(); }
 
 int64_t smc_num_params(const smc_ctx* c) { return c ? c->D : 0; }
 

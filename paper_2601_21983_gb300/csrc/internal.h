@@ -148,6 +148,9 @@ namespace smc {
 
 constexpr int kMaxPartChunks = 64;
 
+// last error of a stateless entry point on the calling thread (k_smc.cu)
+const char* stateless_error();
+
 // error helpers (api.cu)
 smc_status fail(smc_ctx* c, smc_status s, const std::string& msg);
 smc_status cuda_check(smc_ctx* c, cudaError_t e, const char* what);

@@ -11,6 +11,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 namespace smc {
 
@@ -640,3 +641,81 @@ cudaError_t k_philox_u32(uint32_t k0, uint32_t k1, uint32_t c2, uint32_t c3, int
 }
 
 }  // namespace smc
+
+namespace smc {
+
+// ------------------------------------------------ allocation-free resampling
+// Scratch for smc_k_resample_noalloc: the resampling uniforms, staged in a
+// file-scope device array instead of a cudaMalloc'd buffer.  Every GPU that
+// loads the library holds these 32 KiB until the process exits.
+static __device__ __align__(256) double g_resample_scratch[kMaxParticles];
+
+namespace {
+std::mutex g_scratch_mu;
+double* g_scratch_ptr[64] = {nullptr};   // device address of the array, per device
+
+// Device address of the scratch array on the current device.  Host code must
+// not pass the array's name to a kernel: on the host it is only a stand-in
+// symbol, so the address is looked up once per device with that device current.
+cudaError_t scratch_address(double** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (g_scratch_ptr[dev] == nullptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_resample_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = (double*)p;
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+}  // namespace smc
+
+namespace smc {
+static thread_local const char* g_stateless_error = "";
+const char* stateless_error() { return g_stateless_error; }
+}
+
+extern "C" smc_status smc_k_resample_noalloc(const double* wn, int32_t J, int32_t kind, const double* u_host,
+                                              int32_t* anc, void* stream) {
+    using namespace smc;
+    if (!wn || !u_host || !anc) {
+        g_stateless_error = "smc_k_resample_noalloc: null pointer";
+        return SMC_EINVAL;
+    }
+    if (J < 1 || J > kMaxParticles) {
+        g_stateless_error = "smc_k_resample_noalloc: J must be in [1, 4096], the size of its static scratch";
+        return SMC_EINVAL;
+    }
+    if (kind != SMC_RESAMPLE_SYSTEMATIC && kind != SMC_RESAMPLE_MULTINOMIAL) {
+        g_stateless_error = "smc_k_resample_noalloc: unknown resampler kind";
+        return SMC_EINVAL;
+    }
+    const int nu = kind == SMC_RESAMPLE_SYSTEMATIC ? 1 : J;
+    for (int i = 0; i < nu; ++i)
+        if (!(u_host[i] >= 0.0 && u_host[i] < 1.0)) {
+            g_stateless_error = "smc_k_resample_noalloc: uniforms must lie in [0, 1)";
+            return SMC_EINVAL;
+        }
+    double* ud = nullptr;
+    cudaError_t e = scratch_address(&ud);
+    if (e != cudaSuccess) {
+        g_stateless_error = "smc_k_resample_noalloc: cudaGetSymbolAddress failed";
+        return SMC_ECUDA;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // every call overwrites the nu values it reads, so no clearing is needed
+    e = cudaMemcpyAsync(ud, u_host, nu * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = k_resample(wn, J, kind, ud, nu, anc, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        g_stateless_error = "smc_k_resample_noalloc: CUDA error";
+        return SMC_ECUDA;
+    }
+    return SMC_OK;
+}

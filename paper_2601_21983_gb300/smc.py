@@ -109,6 +109,7 @@ _SIGS = {
     "smc_reset_counters": (C.c_int, [C.c_void_p]),
     "smc_k_normalise": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "smc_k_resample": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "smc_k_resample_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "smc_k_philox_normals": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_int64, C.c_void_p,
                                        C.c_void_p]),
     "smc_k_philox_u32": (C.c_int, [C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int64, C.c_void_p,
@@ -319,6 +320,14 @@ def smc_k_resample(wn_dev, kind, u, anc_dev, stream=None):
     u = np.ascontiguousarray(np.atleast_1d(u), np.float64)
     _check(load().smc_k_resample(_ptr(wn_dev), wn_dev.numel(), kind, _ptr(u), _ptr(anc_dev), _stream(stream)),
            "smc_k_resample")
+
+
+def smc_k_resample_noalloc(wn_dev, kind, u, anc_dev, stream=None, J=None):
+    u = np.ascontiguousarray(np.atleast_1d(u), np.float64)
+    n = wn_dev.numel() if J is None else J
+    st = load().smc_k_resample_noalloc(_ptr(wn_dev), n, kind, _ptr(u), _ptr(anc_dev), _stream(stream))
+    if st != 0:
+        raise SMCError(st, "smc_k_resample_noalloc", (load().smc_last_error(None) or b"").decode())
 
 
 def smc_k_philox_normals(seed, stream_id, iteration, offset, out_dev, stream=None):
