@@ -205,6 +205,9 @@ smc_status tc_alloc(smc_ctx* c);
 void tc_free(smc_ctx* c);
 smc_status tc_eval(smc_ctx* c);
 smc_status tc_predict(smc_ctx* c, const float* x, int64_t n, float* out);
+// head / adjoint on mma.sync fragments (k_head.cu)
+cudaError_t launch_head_mma(smc_ctx* c, int H, int C, int mc, int64_t g0, int act, const float* W2, const float* b2,
+                            const __nv_bfloat16* H1, int64_t ldh, int slot, int nsl, int rows_per_slice);
 cudaError_t tc_gemm_public(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
                            int64_t M, int64_t N, int64_t K, int accumulate, cudaStream_t s, int* err_dev,
                            int num_sms);

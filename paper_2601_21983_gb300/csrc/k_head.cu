@@ -1,0 +1,362 @@
+// K3 on tensor cores: the head and adjoint of the BF16 engine for a network
+// with one hidden layer, for all J particles.
+//
+// Per particle j and row i (Sec. 3, eq. approx-grad with coefficient c_i):
+//   z = W2 h + b2,  log p(y|x) = z_y - LSE(z),  dl = c_i (e_y - softmax(z)),
+//   dZ1 = (W2^T dl) * act'(h),  dW2 += dl h^T,  db2 += dl,  db1 += dZ1.
+// The three small contractions run as mma.sync.m16n8k16 BF16 (FP32
+// accumulate) on 16-row tiles:
+//   logits  [16 x 16cls]  = H [16 x HP] . W2^T      (A: ldmatrix of the H tile)
+//   dH      [16 x HP]     = dl [16 x 16] . W2        (A: the logits' C fragments)
+//   dW2^T   [HP x 16]    += H^T [HP x 32] . dl      (A: ldmatrix.trans of the H tile)
+// Each warp streams 32-row tiles: H rows are read once with cp.async into a
+// double-buffered tile (the next tile is in flight while the current one is
+// computed), dZ1 is staged in shared memory and written transposed
+// [J*H][rows] with 64-byte row segments.  db1 / dW2 / db2 / log-likelihood sums are reduced in a fixed
+// order into per-slice partials (same layout as the reduce kernel expects:
+// dW2 [C*H] | db2 [C] | db1 [H] per (slice, particle)).
+#include "internal.h"
+
+namespace smc {
+namespace {
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(su32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(su32(p)));
+}
+// D += A (16x16, row) * B (16x8, col), BF16 inputs, FP32 accumulators
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// 8-byte async global->shared copy; src_bytes = 0 fills zeros without reading
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(su32(dst)), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ __forceinline__ float2 unpack2(uint32_t u) {
+    return __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&u));
+}
+__device__ __forceinline__ float act_grad(int act, float h) {
+    if (act == SMC_ACT_TANH) return 1.0f - h * h;
+    if (act == SMC_ACT_RELU) return h > 0.0f ? 1.0f : 0.0f;
+    return 1.0f;
+}
+
+}  // namespace
+
+// KT: hidden width padded to 16*KT (H <= 16*KT, H % 4 == 0); classes C <= 16.
+template <int KT>
+__global__ void __launch_bounds__(128) head_mma_kernel(
+    const __nv_bfloat16* __restrict__ H1, int64_t ldh, int H, int C, int rows, int64_t g0, int64_t rows_a,
+    float ca, float cb, const int32_t* __restrict__ Y, const float* __restrict__ W2, const float* __restrict__ b2,
+    int act, __nv_bfloat16* __restrict__ dZT, int64_t ldz, float* __restrict__ part_w, double* __restrict__ part_l,
+    int slot_base, int J, int rows_per_slice) {
+    constexpr int HP = 16 * KT;       // padded hidden width
+    constexpr int NT2 = 2 * KT;       // 8-column hidden tiles
+    constexpr int HS = HP + 8;        // H-tile row stride (elements): ldmatrix rows land in distinct banks
+    constexpr int DS = 24;            // dl-tile / W2^T row stride (elements)
+    constexpr int ZS = 40;            // dZ staging row stride (elements)
+    extern __shared__ __align__(16) uint8_t smraw[];
+    __nv_bfloat16* W2s = reinterpret_cast<__nv_bfloat16*>(smraw);   // [16][HS]  classes x hidden
+    __nv_bfloat16* W2Ts = W2s + 16 * HS;                              // [HP][DS]  hidden x classes
+    float* bs = reinterpret_cast<float*>(W2Ts + HP * DS);              // [16]
+    __nv_bfloat16* wbase = reinterpret_cast<__nv_bfloat16*>(bs + 16);
+    constexpr int WARP_ELEMS = 2 * 32 * HS + 32 * DS + HP * ZS;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, q4 = lane & 3;
+    const int j = blockIdx.y, sl = blockIdx.x;
+    __nv_bfloat16* Hbuf = wbase + warp * WARP_ELEMS; // 2 x [32][HS]  hidden activations (double buffer)
+    __nv_bfloat16* Dl = Hbuf + 2 * 32 * HS;          // [32][DS]  dlogits of the tile
+    __nv_bfloat16* Zs = Dl + 32 * DS;                // [HP][ZS]  dZ1 of the tile, transposed
+
+    const float* W2j = W2 + (int64_t)j * C * H;
+    for (int i = t; i < 16 * HS; i += 128) {
+        const int c = i / HS, k = i % HS;
+        W2s[i] = __float2bfloat16_rn((c < C && k < H) ? W2j[c * H + k] : 0.0f);
+    }
+    for (int i = t; i < HP * DS; i += 128) {
+        const int k = i / DS, c = i % DS;
+        W2Ts[i] = __float2bfloat16_rn((c < C && k < H) ? W2j[c * H + k] : 0.0f);
+    }
+    if (t < 16) bs[t] = (t < C) ? b2[(int64_t)j * C + t] : 0.0f;
+    __syncthreads();
+
+    float accW[KT][2][4];
+    float db1[NT2][2];
+    float db2[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < KT; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) accW[a][b][e] = 0.0f;
+#pragma unroll
+    for (int a = 0; a < NT2; ++a) { db1[a][0] = 0.0f; db1[a][1] = 0.0f; }
+    double la = 0.0, lb = 0.0;
+
+    const int r_begin = sl * rows_per_slice, r_end = min(rows, r_begin + rows_per_slice);
+    const int cls[4] = {2 * q4, 2 * q4 + 1, 8 + 2 * q4, 9 + 2 * q4};   // classes of this thread's C fragments
+    const int nq = H / 4;                                                // 8-byte pieces per row
+    // pad columns [H, HP) of both buffers stay zero for the whole kernel
+    for (int i = lane; i < 2 * 32 * (HP / 4); i += 32) {
+        const int b = i / (32 * (HP / 4)), rem = i % (32 * (HP / 4));
+        const int r = rem / (HP / 4), c4 = rem % (HP / 4);
+        if (4 * c4 >= H) *reinterpret_cast<uint2*>(Hbuf + b * 32 * HS + r * HS + 4 * c4) = make_uint2(0u, 0u);
+    }
+    auto issue_tile = [&](__nv_bfloat16* dst, int tbase) {
+        for (int i = lane; i < 32 * nq; i += 32) {
+            const int r = i / nq, c4 = i % nq;
+            const int m = tbase + r;
+            const bool ok = m < r_end;
+            const __nv_bfloat16* src = H1 + (ok ? ((int64_t)m * ldh + (int64_t)j * H + 4 * c4) : 0);
+            cp_async8(dst + r * HS + 4 * c4, src, ok ? 8 : 0);
+        }
+        cp_async_commit();
+    };
+    int buf = 0;
+    if (r_begin + 32 * warp < r_end) issue_tile(Hbuf, r_begin + 32 * warp);
+    for (int tile0 = r_begin + 32 * warp; tile0 < r_end; tile0 += 128) {
+        // ---- 1. the tile's hidden activations: wait for this tile, prefetch the next
+        __nv_bfloat16* Hs = Hbuf + buf * 32 * HS;
+        const int nxt = tile0 + 128;
+        if (nxt < r_end) {
+            issue_tile(Hbuf + (buf ^ 1) * 32 * HS, nxt);
+            cp_async_wait1();
+        } else {
+            cp_async_wait0();
+        }
+        int ylab[2][2];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int m = tile0 + 16 * mt + g + 8 * half;
+                ylab[mt][half] = (m < r_end) ? Y[g0 + m] : -1;
+            }
+        __syncwarp();
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const int r0 = 16 * mt;
+            // ---- 2. logits = H W2^T
+            uint32_t af[KT][4];
+            float cz[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+            for (int kt = 0; kt < KT; ++kt) {
+                ldsm_x4(af[kt], Hs + (r0 + (lane & 15)) * HS + 16 * kt + (lane >> 4) * 8);
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    const __nv_bfloat16* w = W2s + (8 * nt + g) * HS + 16 * kt + 2 * q4;
+                    mma16816(cz[nt], af[kt], *reinterpret_cast<const uint32_t*>(w),
+                             *reinterpret_cast<const uint32_t*>(w + 8));
+                }
+            }
+            // ---- 3. log-softmax, log-likelihood, dlogits (rows g and g+8 of the m-tile)
+            float dl[2][4];
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int m = tile0 + r0 + g + 8 * half;
+                const bool valid = m < r_end;
+                float z[4];
+                z[0] = cz[0][2 * half] + bs[cls[0]];
+                z[1] = cz[0][2 * half + 1] + bs[cls[1]];
+                z[2] = cz[1][2 * half] + bs[cls[2]];
+                z[3] = cz[1][2 * half + 1] + bs[cls[3]];
+                float mx = -INFINITY;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) if (cls[e] < C) mx = fmaxf(mx, z[e]);
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+                float se = 0.0f;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) if (cls[e] < C) se += expf(z[e] - mx);
+                se += __shfl_xor_sync(0xffffffffu, se, 1);
+                se += __shfl_xor_sync(0xffffffffu, se, 2);
+                const float lse = mx + logf(se);
+                const int64_t gr = g0 + m;
+                const int yy = ylab[mt][half];
+                const float coef = (gr < rows_a) ? ca : cb;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    float d = 0.0f;
+                    if (valid && cls[e] < C) d = coef * (((cls[e] == yy) ? 1.0f : 0.0f) - expf(z[e] - lse));
+                    if (valid && cls[e] == yy) {
+                        const float ll = z[e] - lse;
+                        if (gr < rows_a) la += ll; else lb += ll;
+                    }
+                    dl[e >> 1][2 * half + (e & 1)] = d;
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) db2[e] += dl[e >> 1][e & 1] + dl[e >> 1][2 + (e & 1)];
+            // dl as an A fragment (C-fragment layout of the two class tiles = A layout of 16x16)
+            uint32_t adl[4] = {pack2(dl[0][0], dl[0][1]), pack2(dl[0][2], dl[0][3]), pack2(dl[1][0], dl[1][1]),
+                               pack2(dl[1][2], dl[1][3])};
+            *reinterpret_cast<uint32_t*>(Dl + (r0 + g) * DS + 2 * q4) = adl[0];
+            *reinterpret_cast<uint32_t*>(Dl + (r0 + g + 8) * DS + 2 * q4) = adl[1];
+            *reinterpret_cast<uint32_t*>(Dl + (r0 + g) * DS + 8 + 2 * q4) = adl[2];
+            *reinterpret_cast<uint32_t*>(Dl + (r0 + g + 8) * DS + 8 + 2 * q4) = adl[3];
+            // ---- 4. dH = dl W2, dZ1 = dH * act'(h), db1
+#pragma unroll
+            for (int n2 = 0; n2 < NT2; ++n2) {
+                const __nv_bfloat16* w = W2Ts + (8 * n2 + g) * DS + 2 * q4;
+                float d[4] = {0.f, 0.f, 0.f, 0.f};
+                mma16816(d, adl, *reinterpret_cast<const uint32_t*>(w), *reinterpret_cast<const uint32_t*>(w + 8));
+                const float2 hA = unpack2((n2 & 1) ? af[n2 >> 1][2] : af[n2 >> 1][0]);   // row g
+                const float2 hB = unpack2((n2 & 1) ? af[n2 >> 1][3] : af[n2 >> 1][1]);   // row g+8
+                const float z0 = d[0] * act_grad(act, hA.x), z1 = d[1] * act_grad(act, hA.y);
+                const float z2 = d[2] * act_grad(act, hB.x), z3 = d[3] * act_grad(act, hB.y);
+                db1[n2][0] += z0 + z2;
+                db1[n2][1] += z1 + z3;
+                const int col = 8 * n2 + 2 * q4;
+                Zs[col * ZS + r0 + g] = __float2bfloat16_rn(z0);
+                Zs[(col + 1) * ZS + r0 + g] = __float2bfloat16_rn(z1);
+                Zs[col * ZS + r0 + g + 8] = __float2bfloat16_rn(z2);
+                Zs[(col + 1) * ZS + r0 + g + 8] = __float2bfloat16_rn(z3);
+            }
+        }
+        __syncwarp();
+        // ---- 5. dW2^T += H^T dl over the tile's 32 rows
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+            uint32_t bd[4];
+            {
+                const int mi = lane >> 3, i = lane & 7;
+                ldsm_x4_t(bd, Dl + (16 * kk + (mi & 1) * 8 + i) * DS + (mi >> 1) * 8);
+            }
+#pragma unroll
+            for (int mh = 0; mh < KT; ++mh) {
+                uint32_t at[4];
+                const int mi = lane >> 3, i = lane & 7;
+                ldsm_x4_t(at, Hs + (16 * kk + (mi >> 1) * 8 + i) * HS + 16 * mh + (mi & 1) * 8);
+                mma16816(accW[mh][0], at, bd[0], bd[1]);
+                mma16816(accW[mh][1], at, bd[2], bd[3]);
+            }
+        }
+        // ---- 6. dZ1 tile -> HBM, transposed: two hidden rows of 32 samples per instruction
+        {
+            const int half = lane >> 4, rr = 2 * (lane & 15);
+            const int m = tile0 + rr;
+            for (int p0 = 0; p0 < H; p0 += 2) {
+                const int p = p0 + half;
+                if (p < H && m < r_end) {
+                    const uint32_t v = *reinterpret_cast<const uint32_t*>(Zs + p * ZS + rr);
+                    __nv_bfloat16* dst = dZT + ((int64_t)j * H + p) * ldz + m;
+                    if (m + 1 < r_end) *reinterpret_cast<uint32_t*>(dst) = v;
+                    else *dst = *reinterpret_cast<const __nv_bfloat16*>(&v);
+                }
+            }
+        }
+        __syncwarp();
+        buf ^= 1;
+    }
+
+    // ---------------------------------------------------- block reductions
+    // db1, db2: sum over the 8 row groups of the warp (lanes with equal q4)
+#pragma unroll
+    for (int a = 0; a < NT2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int o = 4; o < 32; o <<= 1) db1[a][b] += __shfl_xor_sync(0xffffffffu, db1[a][b], o);
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int o = 4; o < 32; o <<= 1) db2[e] += __shfl_xor_sync(0xffffffffu, db2[e], o);
+    __syncthreads();   // per-warp tiles are free now: reuse them for the cross-warp sums
+    float* red = reinterpret_cast<float*>(wbase);           // [4][16][HP] dW2, [4][HP] db1, [4][16] db2
+    float* redW = red;
+    float* red1 = red + 4 * 16 * HP;
+    float* red2 = red1 + 4 * HP;
+#pragma unroll
+    for (int mh = 0; mh < KT; ++mh)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            const int hid = 16 * mh + g, c0 = 8 * nt + 2 * q4;
+            redW[(warp * 16 + c0) * HP + hid] = accW[mh][nt][0];
+            redW[(warp * 16 + c0 + 1) * HP + hid] = accW[mh][nt][1];
+            redW[(warp * 16 + c0) * HP + hid + 8] = accW[mh][nt][2];
+            redW[(warp * 16 + c0 + 1) * HP + hid + 8] = accW[mh][nt][3];
+        }
+    if (g == 0) {
+#pragma unroll
+        for (int a = 0; a < NT2; ++a) {
+            red1[warp * HP + 8 * a + 2 * q4] = db1[a][0];
+            red1[warp * HP + 8 * a + 2 * q4 + 1] = db1[a][1];
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) red2[warp * 16 + cls[e]] = db2[e];
+    }
+    __syncthreads();
+    const int per = C * H + C + H;
+    const int64_t slot = slot_base + sl;
+    float* pw = part_w + (slot * J + j) * (int64_t)per;
+    for (int i = t; i < C * H; i += 128) {
+        const int c = i / H, hid = i % H;
+        pw[i] = ((redW[(0 * 16 + c) * HP + hid] + redW[(1 * 16 + c) * HP + hid]) + redW[(2 * 16 + c) * HP + hid]) +
+                redW[(3 * 16 + c) * HP + hid];
+    }
+    for (int i = t; i < C; i += 128) pw[C * H + i] = ((red2[i] + red2[16 + i]) + red2[32 + i]) + red2[48 + i];
+    for (int i = t; i < H; i += 128)
+        pw[C * H + C + i] = ((red1[i] + red1[HP + i]) + red1[2 * HP + i]) + red1[3 * HP + i];
+    double* rl = reinterpret_cast<double*>(red2 + 64);     // [2][128], after the float sums
+    rl[t] = la;
+    rl[128 + t] = lb;
+    __syncthreads();
+    for (int st = 64; st > 0; st >>= 1) {
+        if (t < st) { rl[t] += rl[t + st]; rl[128 + t] += rl[128 + t + st]; }
+        __syncthreads();
+    }
+    if (t == 0) {
+        part_l[(slot * J + j) * 2 + 0] = rl[0];
+        part_l[(slot * J + j) * 2 + 1] = rl[128];
+    }
+}
+
+template <int KT>
+static cudaError_t launch_head_mma_t(smc_ctx* c, int H, int C, int mc, int64_t g0, int act, const float* W2,
+                                     const float* b2, const __nv_bfloat16* H1, int64_t ldh, int slot, int nsl,
+                                     int rows_per_slice) {
+    constexpr int HP = 16 * KT, HS = HP + 8, DS = 24, ZS = 40;
+    const size_t tiles = (size_t)(16 * HS + HP * DS) * 2 + 16 * 4 + (size_t)4 * (2 * 32 * HS + 32 * DS + HP * ZS) * 2;
+    const size_t reds = (size_t)(4 * 16 * HP + 4 * HP + 64) * 4 + 2 * 128 * 8 + (size_t)(16 * HS + HP * DS) * 2 + 64;
+    const size_t smem = tiles > reds ? tiles : reds;
+    static size_t set = 0;
+    if (smem > set) {
+        cudaError_t e = cudaFuncSetAttribute(head_mma_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        set = smem;
+    }
+    SMC_LAUNCH(c, head_mma_kernel<KT><<<dim3(nsl, c->J), 128, smem, c->stream>>>(
+                      H1, ldh, H, C, mc, g0, c->rows_a, (float)c->coef_a, (float)c->coef_b, c->Y, W2, b2, act, c->dZT,
+                      c->chunk, c->head_part, c->head_ll, slot, c->J, rows_per_slice));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_head_mma(smc_ctx* c, int H, int C, int mc, int64_t g0, int act, const float* W2, const float* b2,
+                            const __nv_bfloat16* H1, int64_t ldh, int slot, int nsl, int rows_per_slice) {
+    if (H <= 16 * 7 && H > 16 * 6)
+        return launch_head_mma_t<7>(c, H, C, mc, g0, act, W2, b2, H1, ldh, slot, nsl, rows_per_slice);
+    if (H <= 16 * 3) return launch_head_mma_t<3>(c, H, C, mc, g0, act, W2, b2, H1, ldh, slot, nsl, rows_per_slice);
+    return launch_head_mma_t<8>(c, H, C, mc, g0, act, W2, b2, H1, ldh, slot, nsl, rows_per_slice);
+}
+
+}  // namespace smc

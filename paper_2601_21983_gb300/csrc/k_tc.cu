@@ -5,14 +5,13 @@
 //                              = every particle's first-layer weights stacked: one
 //                              dense GEMM; epilogue adds b1, applies the activation
 //                              and stores H1 [M][J*H] in BF16.
-//   K3  head + adjoint (SIMT)  per particle and row: logits = W2 h + b2, log-softmax,
+//   K3  head + adjoint          per particle and row: logits = W2 h + b2, log-softmax,
 //                              c_i-weighted log-likelihood, dlogits = c_i (e_y - softmax),
 //                              dZ1 = (W2^T dlogits) * act'(h) stored transposed
-//                              [J*H][M] in BF16; dW2/db2 and the log-likelihood sums
-//                              as fixed-order per-slice partials.
-//   K5  [dW1 | db1] = dZ1^T [X | 1]   one dense GEMM with K = M (rows); the extra
-//                              column of ones in the transposed input yields the
-//                              bias gradient.
+//                              [J*H][M] in BF16; dW2/db2/db1 and the log-likelihood
+//                              sums as fixed-order per-slice partials (k_head.cu,
+//                              mma.sync tensor-core fragments).
+//   K5  dW1 = dZ1^T X          one dense GEMM with K = M (rows).
 //
 // K1/K5 run on tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulators in TMEM),
 // operands staged by TMA (cp.async.bulk.tensor, 128-byte swizzle) through a
@@ -103,6 +102,17 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
         ::"r"(su32(dst)), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(su32(bar))
         : "memory");
 }
+
+// TMA store of a [rows][cols] box from shared memory (bulk async-group)
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* tm, const void* src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+                 ::"l"((uint64_t)tm), "r"(x), "r"(y), "r"(su32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)), "r"(ncols)
@@ -234,7 +244,8 @@ struct Cfg {
     static constexpr uint32_t TCOLS = (ACC * BN <= 128) ? 128u : (ACC * BN <= 256) ? 256u : 512u;
     static constexpr int N0 = BN > 256 ? 256 : BN;
     static constexpr int N1 = BN - N0;
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+    static constexpr int STAGING = 4 * 2 * 32 * 32 * 2;   // 4 epilogue warps x 2 buffers x [32][32] BF16
+    static constexpr int SMEM = STAGES * STAGE_BYTES + STAGING + 1024 /*align*/ + 256 /*barriers*/;
     static_assert(BN % 16 == 0 && N0 % 16 == 0 && N1 % 16 == 0, "N must be a multiple of 16");
     static_assert(BN % BNBOX == 0 && BNBOX <= 256, "TMA box rows <= 256");
     static_assert(ACC * BN <= 512, "TMEM has 512 columns");
@@ -243,11 +254,13 @@ struct Cfg {
 
 template <int BN, int BNBOX, int STAGES>
 __global__ void __launch_bounds__(192, 1)
-gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs g) {
+gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+            const __grid_constant__ CUtensorMap tmC, const GemmArgs g) {
     using C = Cfg<BN, BNBOX, STAGES>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + STAGES * C::STAGE_BYTES);
+    uint8_t* staging = smem + STAGES * C::STAGE_BYTES;
+    uint64_t* full = (uint64_t*)(staging + C::STAGING);
     uint64_t* empty = full + STAGES;
     uint64_t* tfull = empty + STAGES;
     uint64_t* tempty = tfull + C::ACC;
@@ -348,11 +361,22 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         // ---------------------------------------------------- epilogue (warps 2..5)
         const int wq = warp & 3;
         const int row_l = wq * 32 + lane;
+        constexpr int NCH = (BN + 31) / 32;
+        uint8_t* my_stage = staging + (warp - 2) * 2 * 2048;   // two [32][32] BF16 buffers of this warp
         int acc = 0;
         uint32_t aph = 0;
+        int chunk_no = 0;
         for (int u = blockIdx.x; u < g.num_units; u += gridDim.x) {
             int tm, tn, ks;
             decode(g, u, tm, tn, ks);
+            float bq[NCH];
+            if (g.epi == EPI_BF16_BIAS_ACT) {
+#pragma unroll
+                for (int q = 0; q < NCH; ++q) {
+                    const int col = tn * BN + 32 * q + lane;
+                    bq[q] = (col < g.N) ? g.bias[col] : 0.0f;      // prefetched before the accumulator wait
+                }
+            }
             if (!mbar_wait(tfull + acc, aph, abort_flag)) {
                 raise_abort(g, abort_flag, ERR_EPILOGUE);
                 break;
@@ -360,19 +384,63 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             tc_fence_after();
             const int row = tm * BM + row_l;
             const uint32_t tb = tbase + (uint32_t)(acc * BN) + ((uint32_t)(wq * 32) << 16);
+            if (g.epi == EPI_BF16_BIAS_ACT) {
+#pragma unroll
+                for (int q = 0; q < NCH; ++q) {
+                    uint32_t r[32];
+                    __syncwarp();
+                    TMEM_LD32(tb + (uint32_t)(32 * q), r);
+                    tmem_ld_wait();
+                    uint32_t pk[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const float b0 = __shfl_sync(0xffffffffu, bq[q], 2 * i);
+                        const float b1 = __shfl_sync(0xffffffffu, bq[q], 2 * i + 1);
+                        __nv_bfloat162 v = __floats2bfloat162_rn(act_f(g.act, __uint_as_float(r[2 * i]) + b0),
+                                                                 act_f(g.act, __uint_as_float(r[2 * i + 1]) + b1));
+                        pk[i] = *reinterpret_cast<uint32_t*>(&v);
+                    }
+                    // reuse of this buffer: the store issued two chunks ago must have read it
+                    uint8_t* buf = my_stage + (chunk_no & 1) * 2048;
+                    if (lane == 0 && chunk_no >= 2) bulk_wait_read1();
+                    __syncwarp();
+                    // row `lane` of the [32][32] box: four 16-byte pieces, written in a
+                    // lane-rotated order so the 8 lanes of each phase hit distinct banks
+#pragma unroll
+                    for (int it = 0; it < 4; ++it) {
+                        const int pc = (it + (lane >> 1)) & 3;
+                        const uint4 v0 = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        const uint4 v1 = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                        const uint4 v2 = make_uint4(pk[8], pk[9], pk[10], pk[11]);
+                        const uint4 v3 = make_uint4(pk[12], pk[13], pk[14], pk[15]);
+                        const uint4 v = pc == 0 ? v0 : (pc == 1 ? v1 : (pc == 2 ? v2 : v3));
+                        *reinterpret_cast<uint4*>(buf + lane * 64 + pc * 16) = v;
+                    }
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_2d(&tmC, buf, tn * BN + 32 * q, tm * BM + wq * 32);
+                        bulk_commit();
+                    }
+                    ++chunk_no;
+                }
+            } else {
 #pragma unroll 1
-            for (int c = 0; c < BN; c += 32) {
-                uint32_t r[32];
-                __syncwarp();
-                TMEM_LD32(tb + (uint32_t)c, r);
-                tmem_ld_wait();
-                epi_store(g, row, tn * BN + c, min(32, BN - c), ks, r);
+                for (int c = 0; c < BN; c += 32) {
+                    uint32_t r[32];
+                    __syncwarp();
+                    TMEM_LD32(tb + (uint32_t)c, r);
+                    tmem_ld_wait();
+                    epi_store(g, row, tn * BN + c, min(32, BN - c), ks, r);
+                }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty + acc);
             if (++acc == C::ACC) { acc = 0; aph ^= 1; }
         }
+        if (lane == 0) bulk_wait_all();   // outstanding output stores complete before the CTA exits
+        __syncwarp();
     }
     tc_fence_before();
     __syncthreads();
@@ -411,13 +479,33 @@ static bool make_tmap(CUtensorMap* m, const void* base, uint64_t inner, uint64_t
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 2-D BF16 tensor [outer][inner] for TMA stores: box {32, 32}, no swizzle.
+static bool make_store_tmap(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t pitch) {
+    auto enc = encode_fn();
+    if (!enc) return false;
+    if (((uintptr_t)base & 15) || (pitch & 15)) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {pitch};
+    cuuint32_t box[2] = {32, 32};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int BN, int BNBOX, int STAGES>
 static cudaError_t launch_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, GemmArgs g, cudaStream_t s,
                                int num_sms) {
     using C = Cfg<BN, BNBOX, STAGES>;
-    CUtensorMap ta, tb;
+    CUtensorMap ta, tb, tc;
     if (!make_tmap(&ta, A, (uint64_t)g.K, (uint64_t)g.M, (uint64_t)lda * 2, BM)) return cudaErrorInvalidValue;
     if (!make_tmap(&tb, B, (uint64_t)g.K, (uint64_t)g.N, (uint64_t)ldb * 2, BNBOX)) return cudaErrorInvalidValue;
+    if (g.epi == EPI_BF16_BIAS_ACT) {
+        if (!make_store_tmap(&tc, g.out, (uint64_t)g.N, (uint64_t)g.M, (uint64_t)g.ldo * 2))
+            return cudaErrorInvalidValue;
+    } else {
+        tc = ta;   // unused by the FP32 epilogue
+    }
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(gemm_kernel<BN, BNBOX, STAGES>,
@@ -426,7 +514,7 @@ static cudaError_t launch_gemm(const void* A, int64_t lda, const void* B, int64_
         attr_set = true;
     }
     const int grid = std::max(1, std::min(g.num_units, num_sms));
-    gemm_kernel<BN, BNBOX, STAGES><<<grid, 192, C::SMEM, s>>>(ta, tb, g);
+    gemm_kernel<BN, BNBOX, STAGES><<<grid, 192, C::SMEM, s>>>(ta, tb, tc, g);
     return cudaGetLastError();
 }
 
@@ -456,161 +544,6 @@ static int choose_kslices(int tiles, int kb_total, int num_sms, int max_s) {
 }  // namespace tcg
 
 using namespace tcg;
-
-// ------------------------------------------------------------ head kernels
-// K3: per particle j (blockIdx.y) and a slice of rows (blockIdx.x), 128 threads,
-// one row per thread per 128-row tile.  The thread keeps its row's hidden
-// activations h[H] in registers; logits, log-softmax, dlogits and
-// dZ1 = (W2^T dlogits) * act'(h) are computed in FP32.  dZ1 goes to HBM in
-// BF16 (transposed, the weight-gradient GEMM's operand); db1 is summed in FP32
-// (warp shuffles, then per-warp rows of shared memory); dW2 = sum_rows dl h^T
-// through a shared-memory transpose.  All sums run in a fixed order.
-// HT/CT: compile-time hidden width / classes (0: runtime H <= 128, C <= 16).
-template <int HT, int CT>
-__global__ void __launch_bounds__(128) tc_head_kernel(
-    const __nv_bfloat16* __restrict__ H1, int64_t ldh, int H_, int C_, int rows, int64_t g0, int64_t rows_a,
-    float ca, float cb, const int32_t* __restrict__ Y, const float* __restrict__ W2, const float* __restrict__ b2,
-    int act, __nv_bfloat16* __restrict__ dZT, int64_t ldz, float* __restrict__ part_w, double* __restrict__ part_l,
-    int slot_base, int J, int rows_per_slice) {
-    constexpr int HM = HT > 0 ? HT : 128;      // register array extent
-    constexpr int CM = CT > 0 ? CT : 16;
-    const int H = HT > 0 ? HT : H_;
-    const int C = CT > 0 ? CT : C_;
-    extern __shared__ float sm[];
-    const int HP = H + 1;
-    float* hs = sm;                       // [128][H+1]   h of the tile (fp32)
-    float* dls = hs + 128 * HP;           // [128][CM]    dlogits of the tile
-    float* Ws = dls + 128 * CM;           // [C][H]
-    float* bs = Ws + CM * HM;             // [C]
-    float* dbw = bs + CM;                 // [4][H]       per-warp db1 sums
-    float* WsT = dbw + 4 * H;             // [H][CM]      W2 transposed (class-contiguous)
-    __shared__ double red[2][128];
-    const int j = blockIdx.y, sl = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    for (int i = t; i < C * H; i += 128) Ws[i] = W2[(int64_t)j * C * H + i];
-    for (int i = t; i < C; i += 128) bs[i] = b2[(int64_t)j * C + i];
-    for (int i = t; i < 4 * H; i += 128) dbw[i] = 0.0f;
-    for (int i = t; i < H * CM; i += 128) WsT[i] = ((i % CM) < C) ? W2[(int64_t)j * C * H + (i % CM) * H + i / CM] : 0.0f;
-    float accW[CM];
-#pragma unroll
-    for (int c = 0; c < CM; ++c) accW[c] = 0.0f;
-    float accb = 0.0f;
-    double la = 0.0, lb = 0.0;
-    const int r_begin = sl * rows_per_slice, r_end = min(rows, r_begin + rows_per_slice);
-    __syncthreads();
-    for (int tile0 = r_begin; tile0 < r_end; tile0 += 128) {
-        const int m = tile0 + t;
-        const bool valid = m < r_end;
-        // h as packed BF16 pairs (the values the forward GEMM stored), 8-byte loads
-        __nv_bfloat162 h2[HM / 2];
-        const __nv_bfloat16* src = H1 + (int64_t)m * ldh + (int64_t)j * H;
-        if (HT > 0 && (HM % 4) == 0) {
-#pragma unroll
-            for (int q = 0; q < HM / 4; ++q) {
-                uint2 v = valid ? *(const uint2*)(src + 4 * q) : make_uint2(0u, 0u);
-                h2[2 * q] = *(__nv_bfloat162*)&v.x;
-                h2[2 * q + 1] = *(__nv_bfloat162*)&v.y;
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < HM / 2; ++q) {
-                const __nv_bfloat16 a = (2 * q < H && valid) ? src[2 * q] : __float2bfloat16_rn(0.0f);
-                const __nv_bfloat16 b = (2 * q + 1 < H && valid) ? src[2 * q + 1] : __float2bfloat16_rn(0.0f);
-                h2[q] = __halves2bfloat162(a, b);
-            }
-        }
-        float z[CM], dl[CM];
-#pragma unroll 1
-        for (int c = 0; c < C; ++c) {
-            float a0 = bs[c], a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;   // four independent FMA chains
-            const float* w = Ws + c * H;
-#pragma unroll
-            for (int q = 0; q < HM / 2; q += 2) {
-                const float2 hv = __bfloat1622float2(h2[q]);
-                if (2 * q < H) a0 = fmaf(w[2 * q], hv.x, a0);
-                if (2 * q + 1 < H) a1 = fmaf(w[2 * q + 1], hv.y, a1);
-                if (q + 1 < HM / 2) {
-                    const float2 hw = __bfloat1622float2(h2[q + 1]);
-                    if (2 * q + 2 < H) a2 = fmaf(w[2 * q + 2], hw.x, a2);
-                    if (2 * q + 3 < H) a3 = fmaf(w[2 * q + 3], hw.y, a3);
-                }
-            }
-            dls[t * CM + c] = (a0 + a1) + (a2 + a3);   // logits parked in this thread's dlogits row
-        }
-#pragma unroll
-        for (int c = 0; c < CM; ++c) { z[c] = (c < C) ? dls[t * CM + c] : 0.0f; dl[c] = 0.0f; }
-        if (valid) {
-            float zmax = z[0];
-#pragma unroll
-            for (int c = 1; c < CM; ++c) if (c < C) zmax = fmaxf(zmax, z[c]);
-            float s = 0.0f;
-#pragma unroll
-            for (int c = 0; c < CM; ++c) if (c < C) s += expf(z[c] - zmax);
-            const float lse = zmax + logf(s);
-            const int64_t g = g0 + m;
-            const int yy = Y[g];
-            float zy = 0.0f;
-#pragma unroll
-            for (int c = 0; c < CM; ++c) if (c == yy) zy = z[c];
-            const float ll = zy - lse;
-            const float coef = (g < rows_a) ? ca : cb;
-            if (g < rows_a) la += ll; else lb += ll;
-#pragma unroll
-            for (int c = 0; c < CM; ++c)
-                if (c < C) dl[c] = coef * (((c == yy) ? 1.0f : 0.0f) - expf(z[c] - lse));
-        }
-#pragma unroll
-        for (int c = 0; c < CM; ++c) dls[t * CM + c] = dl[c];
-#pragma unroll
-        for (int k = 0; k < HM; ++k) {
-            if (k < H) {
-                const float hv = (k & 1) ? __high2float(h2[k / 2]) : __low2float(h2[k / 2]);
-                hs[t * HP + k] = hv;
-                float dh = 0.0f;
-#pragma unroll
-                for (int c = 0; c < CM; ++c) if (c < C) dh = fmaf(dl[c], WsT[k * CM + c], dh);
-                const float dz = dh * (act == SMC_ACT_TANH ? 1.0f - hv * hv
-                                                           : (act == SMC_ACT_RELU ? (hv > 0.0f ? 1.0f : 0.0f) : 1.0f));
-                if (valid) dZT[((int64_t)j * H + k) * ldz + m] = __float2bfloat16_rn(dz);
-                float r = dz;                              // invalid rows carry dz = 0
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-                if (lane == 0) dbw[warp * H + k] += r;
-            }
-        }
-        __syncthreads();
-        if (t < H) {
-            for (int r = 0; r < 128; ++r) {
-                const float hv = hs[r * HP + t];
-#pragma unroll
-                for (int c = 0; c < CM; ++c) if (c < C) accW[c] = fmaf(dls[r * CM + c], hv, accW[c]);
-            }
-        }
-        if (t < C)
-            for (int r = 0; r < 128; ++r) accb += dls[r * CM + t];
-        __syncthreads();
-    }
-    // partial layout per (slot, j): dW2 [C*H] | db2 [C] | db1 [H]
-    const int per = C * H + C + H;
-    const int64_t slot = slot_base + sl;
-    const int64_t pw = (slot * J + j) * (int64_t)per;
-    if (t < H) {
-#pragma unroll
-        for (int c = 0; c < CM; ++c) if (c < C) part_w[pw + c * H + t] = accW[c];
-        part_w[pw + C * H + C + t] = ((dbw[t] + dbw[H + t]) + dbw[2 * H + t]) + dbw[3 * H + t];
-    }
-    if (t < C) part_w[pw + C * H + t] = accb;
-    red[0][t] = la;
-    red[1][t] = lb;
-    __syncthreads();
-    for (int st = 64; st > 0; st >>= 1) {
-        if (t < st) { red[0][t] += red[0][t + st]; red[1][t] += red[1][t + st]; }
-        __syncthreads();
-    }
-    if (t == 0) {
-        part_l[(slot * J + j) * 2 + 0] = red[0][0];
-        part_l[(slot * J + j) * 2 + 1] = red[1][0];
-    }
-}
 
 // Sum the per-slice partials in slot order: W2/b2/b1 gradients and LL sums.
 __global__ void head_reduce_kernel(const float* __restrict__ part_w, const double* __restrict__ part_l, int nslots,
@@ -683,7 +616,10 @@ smc_status tc_check_model(const smc_ctx* c, std::string* why) {
     }
     if (c->likelihood != SMC_LIK_CATEGORICAL) { *why = "BF16 path: categorical likelihood only"; return SMC_EUNSUPPORTED; }
     if (c->in_feat % 8 != 0) { *why = "BF16 path: input features must be a multiple of 8"; return SMC_EUNSUPPORTED; }
-    if (c->layers[0].out_feat() > 128) { *why = "BF16 path: hidden width must be <= 128"; return SMC_EUNSUPPORTED; }
+    if (c->layers[0].out_feat() > 128 || c->layers[0].out_feat() % 4 != 0) {
+        *why = "BF16 path: hidden width must be a multiple of 4 and <= 128";
+        return SMC_EUNSUPPORTED;
+    }
     if (c->n_out > 16) { *why = "BF16 path: at most 16 classes"; return SMC_EUNSUPPORTED; }
     return SMC_OK;
 }
@@ -734,32 +670,13 @@ static cudaError_t tc_forward_layer1(smc_ctx* c, const __nv_bfloat16* x, int64_t
     return e;
 }
 
-template <int HT, int CT>
-static cudaError_t launch_head_t(smc_ctx* c, int H, int C, int mc, int64_t g0, int act, const Layer& L1, int slot,
-                                 int nsl, int rows_per_slice) {
-    constexpr int HM = HT > 0 ? HT : 128;
-    constexpr int CM = CT > 0 ? CT : 16;
-    const size_t smem = (size_t)(128 * (H + 1) + 128 * CM + CM * HM + CM + 4 * H + HM * CM) * sizeof(float);
-    static size_t set = 0;
-    if (smem > set) {
-        cudaError_t e = cudaFuncSetAttribute(tc_head_kernel<HT, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        set = smem;
-    }
-    fam_begin(c, F_HEAD);
-    SMC_LAUNCH(c, tc_head_kernel<HT, CT><<<dim3(nsl, c->J), 128, smem, c->stream>>>(
-                      c->H1, ldh_of(c), H, C, mc, g0, c->rows_a, (float)c->coef_a, (float)c->coef_b, c->Y,
-                      c->theta + c->segs[L1.seg_w].off, c->theta + c->segs[L1.seg_b].off, act, c->dZT, c->chunk,
-                      c->head_part, c->head_ll, slot, c->J, rows_per_slice));
-    fam_end(c, F_HEAD);
-    return cudaGetLastError();
-}
-
 static cudaError_t launch_head(smc_ctx* c, int H, int C, int mc, int64_t g0, int act, const Layer& L1, int slot,
                                int nsl, int rows_per_slice) {
-    if (H == 100 && C == 10) return launch_head_t<100, 10>(c, H, C, mc, g0, act, L1, slot, nsl, rows_per_slice);
-    return launch_head_t<0, 0>(c, H, C, mc, g0, act, L1, slot, nsl, rows_per_slice);
+    fam_begin(c, F_HEAD);
+    cudaError_t e = launch_head_mma(c, H, C, mc, g0, act, c->theta + c->segs[L1.seg_w].off,
+                                    c->theta + c->segs[L1.seg_b].off, c->H1, ldh_of(c), slot, nsl, rows_per_slice);
+    fam_end(c, F_HEAD);
+    return e;
 }
 
 smc_status tc_eval(smc_ctx* c) {
@@ -769,7 +686,7 @@ smc_status tc_eval(smc_ctx* c) {
     const int64_t JH = (int64_t)c->J * H, Din = c->in_feat;
     const int64_t M = c->rows_a + c->rows_b;
     const int64_t ch = c->chunk;
-    const int rows_per_slice = 1024;
+    const int rows_per_slice = 4096;
     int slot = 0;
     cudaError_t e;
     for (int64_t g0 = 0; g0 < M; g0 += ch) {
