@@ -63,8 +63,9 @@ __device__ __forceinline__ float act_grad(int act, float h) {
 
 }  // namespace
 
-// KT: hidden width padded to 16*KT (H <= 16*KT, H % 4 == 0); classes C <= 16.
-template <int KT>
+// KT: hidden width padded to 16*KT (H <= 16*KT, H % 4 == 0); classes C <= 16;
+// ACT: activation of the hidden layer (SMC_ACT_*).
+template <int KT, int ACT>
 __global__ void __launch_bounds__(128) head_mma_kernel(
     const __nv_bfloat16* __restrict__ H1, int64_t ldh, int H, int C, int rows, int64_t g0, int64_t rows_a,
     float ca, float cb, const int32_t* __restrict__ Y, const float* __restrict__ W2, const float* __restrict__ b2,
@@ -122,12 +123,13 @@ __global__ void __launch_bounds__(128) head_mma_kernel(
         if (4 * c4 >= H) *reinterpret_cast<uint2*>(Hbuf + b * 32 * HS + r * HS + 4 * c4) = make_uint2(0u, 0u);
     }
     auto issue_tile = [&](__nv_bfloat16* dst, int tbase) {
-        for (int i = lane; i < 32 * nq; i += 32) {
-            const int r = i / nq, c4 = i % nq;
-            const int m = tbase + r;
-            const bool ok = m < r_end;
-            const __nv_bfloat16* src = H1 + (ok ? ((int64_t)m * ldh + (int64_t)j * H + 4 * c4) : 0);
-            cp_async8(dst + r * HS + 4 * c4, src, ok ? 8 : 0);
+        for (int c4 = lane; c4 < nq; c4 += 32) {
+            const __nv_bfloat16* src = H1 + (int64_t)tbase * ldh + (int64_t)j * H + 4 * c4;
+#pragma unroll 8
+            for (int r = 0; r < 32; ++r) {
+                const bool ok = tbase + r < r_end;
+                cp_async8(dst + r * HS + 4 * c4, ok ? src + (int64_t)r * ldh : H1, ok ? 8 : 0);
+            }
         }
         cp_async_commit();
     };
@@ -221,8 +223,8 @@ __global__ void __launch_bounds__(128) head_mma_kernel(
                 mma16816(d, adl, *reinterpret_cast<const uint32_t*>(w), *reinterpret_cast<const uint32_t*>(w + 8));
                 const float2 hA = unpack2((n2 & 1) ? af[n2 >> 1][2] : af[n2 >> 1][0]);   // row g
                 const float2 hB = unpack2((n2 & 1) ? af[n2 >> 1][3] : af[n2 >> 1][1]);   // row g+8
-                const float z0 = d[0] * act_grad(act, hA.x), z1 = d[1] * act_grad(act, hA.y);
-                const float z2 = d[2] * act_grad(act, hB.x), z3 = d[3] * act_grad(act, hB.y);
+                const float z0 = d[0] * act_grad(ACT, hA.x), z1 = d[1] * act_grad(ACT, hA.y);
+                const float z2 = d[2] * act_grad(ACT, hB.x), z3 = d[3] * act_grad(ACT, hB.y);
                 db1[n2][0] += z0 + z2;
                 db1[n2][1] += z1 + z3;
                 const int col = 8 * n2 + 2 * q4;
@@ -250,17 +252,22 @@ __global__ void __launch_bounds__(128) head_mma_kernel(
                 mma16816(accW[mh][1], at, bd[2], bd[3]);
             }
         }
-        // ---- 6. dZ1 tile -> HBM, transposed: two hidden rows of 32 samples per instruction
+        // ---- 6. dZ1 tile -> HBM, transposed: 8 hidden rows x 32 samples per instruction
         {
-            const int half = lane >> 4, rr = 2 * (lane & 15);
+            const int seg = lane & 3, rr = 8 * seg;
             const int m = tile0 + rr;
-            for (int p0 = 0; p0 < H; p0 += 2) {
-                const int p = p0 + half;
+            const bool full = m + 8 <= r_end;
+            for (int p0 = 0; p0 < H; p0 += 8) {
+                const int p = p0 + (lane >> 2);
                 if (p < H && m < r_end) {
-                    const uint32_t v = *reinterpret_cast<const uint32_t*>(Zs + p * ZS + rr);
+                    const uint4 v = *reinterpret_cast<const uint4*>(Zs + p * ZS + rr);
                     __nv_bfloat16* dst = dZT + ((int64_t)j * H + p) * ldz + m;
-                    if (m + 1 < r_end) *reinterpret_cast<uint32_t*>(dst) = v;
-                    else *dst = *reinterpret_cast<const __nv_bfloat16*>(&v);
+                    if (full) {
+                        *reinterpret_cast<uint4*>(dst) = v;
+                    } else {
+                        const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
+                        for (int i = 0; i < 8 && m + i < r_end; ++i) dst[i] = e[i];
+                    }
                 }
             }
         }
@@ -330,7 +337,7 @@ __global__ void __launch_bounds__(128) head_mma_kernel(
     }
 }
 
-template <int KT>
+template <int KT, int ACT>
 static cudaError_t launch_head_mma_t(smc_ctx* c, int H, int C, int mc, int64_t g0, int act, const float* W2,
                                      const float* b2, const __nv_bfloat16* H1, int64_t ldh, int slot, int nsl,
                                      int rows_per_slice) {
@@ -340,23 +347,34 @@ static cudaError_t launch_head_mma_t(smc_ctx* c, int H, int C, int mc, int64_t g
     const size_t smem = tiles > reds ? tiles : reds;
     static size_t set = 0;
     if (smem > set) {
-        cudaError_t e = cudaFuncSetAttribute(head_mma_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(head_mma_kernel<KT, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         set = smem;
     }
-    SMC_LAUNCH(c, head_mma_kernel<KT><<<dim3(nsl, c->J), 128, smem, c->stream>>>(
+    SMC_LAUNCH(c, head_mma_kernel<KT, ACT><<<dim3(nsl, c->J), 128, smem, c->stream>>>(
                       H1, ldh, H, C, mc, g0, c->rows_a, (float)c->coef_a, (float)c->coef_b, c->Y, W2, b2, act, c->dZT,
                       c->chunk, c->head_part, c->head_ll, slot, c->J, rows_per_slice));
     return cudaGetLastError();
 }
 
+template <int KT>
+static cudaError_t launch_head_mma_k(smc_ctx* c, int H, int C, int mc, int64_t g0, int act, const float* W2,
+                                     const float* b2, const __nv_bfloat16* H1, int64_t ldh, int slot, int nsl,
+                                     int rows_per_slice) {
+    if (act == SMC_ACT_RELU)
+        return launch_head_mma_t<KT, SMC_ACT_RELU>(c, H, C, mc, g0, act, W2, b2, H1, ldh, slot, nsl, rows_per_slice);
+    if (act == SMC_ACT_TANH)
+        return launch_head_mma_t<KT, SMC_ACT_TANH>(c, H, C, mc, g0, act, W2, b2, H1, ldh, slot, nsl, rows_per_slice);
+    return launch_head_mma_t<KT, SMC_ACT_IDENTITY>(c, H, C, mc, g0, act, W2, b2, H1, ldh, slot, nsl, rows_per_slice);
+}
+
 cudaError_t launch_head_mma(smc_ctx* c, int H, int C, int mc, int64_t g0, int act, const float* W2, const float* b2,
                             const __nv_bfloat16* H1, int64_t ldh, int slot, int nsl, int rows_per_slice) {
     if (H <= 16 * 7 && H > 16 * 6)
-        return launch_head_mma_t<7>(c, H, C, mc, g0, act, W2, b2, H1, ldh, slot, nsl, rows_per_slice);
-    if (H <= 16 * 3) return launch_head_mma_t<3>(c, H, C, mc, g0, act, W2, b2, H1, ldh, slot, nsl, rows_per_slice);
-    return launch_head_mma_t<8>(c, H, C, mc, g0, act, W2, b2, H1, ldh, slot, nsl, rows_per_slice);
+        return launch_head_mma_k<7>(c, H, C, mc, g0, act, W2, b2, H1, ldh, slot, nsl, rows_per_slice);
+    if (H <= 16 * 3) return launch_head_mma_k<3>(c, H, C, mc, g0, act, W2, b2, H1, ldh, slot, nsl, rows_per_slice);
+    return launch_head_mma_k<8>(c, H, C, mc, g0, act, W2, b2, H1, ldh, slot, nsl, rows_per_slice);
 }
 
 }  // namespace smc
