@@ -169,19 +169,24 @@ class Sampler:
             P <- P + h/2 grad log pi(theta);  theta <- theta + h M^-1 P;
             P <- P + h/2 grad log pi(theta).
         The gradient at the start is taken under pi_k (reading r6).  S = 1 is
-        Langevin dynamics (Sec. 2.1).  The L-kernel is the reversed-momentum
+        Langevin dynamics (Sec. 2.1).  h may be one value or one per particle and
+        inv_mass one [D] vector or one per particle ([J, D]): each particle's
+        weight then uses its own kernel.  The L-kernel is the reversed-momentum
         kernel, so (eq. weight_update_fp, reading r7)
             log w_k = log w_{k-1} + log pi_k(theta_k) - log pi_{k-1}(theta_{k-1})
                       + log N(-P_k; 0, M) - log N(P^0; 0, M),
         the Gaussian normalisers cancelling.  A non-finite log pi_k gives
         log w_k = -inf (reading r8)."""
         inv_mass = np.ones(self.D) if inv_mass is None else np.asarray(inv_mass, dtype=np.float64)
+        hs = np.broadcast_to(np.asarray(h, dtype=np.float64), (self.J,))
+        ims = np.broadcast_to(inv_mass, (self.J, self.D))
         z = np.asarray(z, dtype=np.float64)
         for j in range(self.J):
-            P0 = z[j] / np.sqrt(inv_mass)
-            theta, P, (logpi, _, la, lb) = leapfrog(self.target, self.theta[j], P0, h, S, inv_mass)
-            ke0 = 0.5 * float(P0 @ (inv_mass * P0))
-            ke1 = 0.5 * float(P @ (inv_mass * P))
+            im = ims[j]
+            P0 = z[j] / np.sqrt(im)
+            theta, P, (logpi, _, la, lb) = leapfrog(self.target, self.theta[j], P0, float(hs[j]), S, im)
+            ke0 = 0.5 * float(P0 @ (im * P0))
+            ke1 = 0.5 * float(P @ (im * P))
             inc = logpi - self.logpi[j] - ke1 + ke0
             self.logw[j] = self.logw[j] + inc if math.isfinite(inc) else -math.inf
             self.theta[j], self.logpi[j], self.la[j], self.lb[j] = theta, logpi, la, lb
