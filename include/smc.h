@@ -62,7 +62,8 @@ enum {
     SMC_SCHED_CONSTANT = 0, SMC_SCHED_FB = 1, SMC_SCHED_CTR = 2,
     SMC_SCHED_LINEAR = 3, SMC_SCHED_AUTOMATED = 4, SMC_SCHED_SDA = 5
 };
-enum { SMC_PROPOSAL_PLAIN = 0, SMC_PROPOSAL_LEARNED = 1 };
+enum { SMC_PROPOSAL_PLAIN = 0, SMC_PROPOSAL_LEARNED = 1, SMC_PROPOSAL_EXPLORE = 2 };
+#define SMC_LEARNED_NUM_PARAMS 706   /* 8-64-2 network: W1 [64][8], b1 [64], W2 [2][64], b2 [2] */
 
 /* One layer.  DENSE: n_in -> n_out.  CONV: valid ksize x ksize cross-correlation,
  * stride 1, n_in = c_in channels -> n_out = c_out channels.  MAXPOOL2: 2x2 max
@@ -120,9 +121,19 @@ typedef struct {
 } smc_schedule;
 
 typedef struct {
-    double h;                  /* leapfrog step size */
+    double h;                  /* leapfrog step size (of the plain proposal) */
     int32_t S;                 /* leapfrog steps (S = 1: Langevin dynamics) */
-    int32_t proposal;          /* SMC_PROPOSAL_* */
+    int32_t proposal;          /* SMC_PROPOSAL_PLAIN: M = I, step h.
+                                  SMC_PROPOSAL_LEARNED: per-segment mass and step from the
+                                    learned network (not in the paper); falls back to PLAIN for
+                                    one iteration after a learned move left J_eff < J/10.
+                                  SMC_PROPOSAL_EXPLORE: particles split into `groups` groups,
+                                    group g > 0 moving with the network's proposal perturbed by
+                                    explore_sigma N(0, 1) in log space; the best group (mean squared
+                                    jump x group ESS / group size) becomes a training row. */
+    int32_t groups;            /* EXPLORE: candidate groups (2..16) */
+    int32_t pad_;
+    double explore_sigma;      /* EXPLORE: perturbation scale */
 } smc_step_params;
 
 typedef struct {
@@ -133,7 +144,8 @@ typedef struct {
     int32_t k;                 /* iteration index */
     int32_t n_nonfinite;       /* particles whose log pi was not finite (log w set to -inf) */
     int32_t grad_evals;        /* gradient evaluations over D_k made by the call */
-    int32_t pad_;
+    int32_t proposal_used;     /* SMC_PROPOSAL_* actually used (PLAIN after a fallback) */
+    double h_used;             /* step of group 0 */
 } smc_step_stats;
 
 typedef struct {
@@ -212,6 +224,42 @@ smc_status smc_posterior_predict(smc_ctx* ctx, const float* x_test, int64_t n,
  * iteration. */
 smc_status smc_upload_rows(smc_ctx* ctx, int64_t row0, int64_t n,
                            const float* x, const int32_t* y_class, const float* y_value);
+
+/* ------------------------------------------ learned proposal (not in the paper) */
+
+/* Get (host out [SMC_LEARNED_NUM_PARAMS]) and/or set (host in) the proposal
+ * network's FP32 parameters; either pointer may be NULL.  A new context holds
+ * a network whose output layer is zero, i.e. the plain proposal. */
+smc_status smc_learned_params(smc_ctx* ctx, float* get, const float* set);
+
+/* Fit the network to the collected training rows by full-batch Adam (FP32,
+ * hand-written backward pass on the GPU) for `epochs` epochs at rate lr;
+ * *loss gets the mean squared error of the last epoch (may be NULL).
+ * SMC_ESTATE when no rows were collected. */
+smc_status smc_learned_train(smc_ctx* ctx, int32_t epochs, double lr, double* loss);
+
+/* Number of collected training rows; features [n][8] and targets [n][2] copied
+ * to host buffers when non-NULL (capacity given by *n_rows on input). */
+smc_status smc_learned_data(smc_ctx* ctx, int64_t* n_rows, float* features, float* targets);
+smc_status smc_learned_reset_data(smc_ctx* ctx);
+
+/* Replace the collected training rows by host features [n][8] and targets
+ * [n][2] (n <= 16384). */
+smc_status smc_learned_load_data(smc_ctx* ctx, const float* features, const float* targets, int64_t n);
+
+/* Features [n_seg][8], candidates [groups][n_seg + 1] (log inverse masses, then
+ * log step multiplier) and scores [groups + 1] (last: index of the best group)
+ * of the last learned / exploring step (host buffers, each may be NULL). */
+smc_status smc_learned_last(smc_ctx* ctx, float* features, float* candidates, double* scores);
+
+/* Number of parameter segments (one W and one b per parametric layer). */
+int32_t smc_num_segments(const smc_ctx* ctx);
+
+/* Loss and gradient of the proposal network's mean squared error for host
+ * features [n][8], targets [n][2] and parameters [SMC_LEARNED_NUM_PARAMS],
+ * computed by the library's training kernel (host outputs). */
+smc_status smc_k_learned_loss_grad(const float* features, const float* targets, int64_t n, const float* params,
+                                   float* grad, double* loss, void* stream);
 
 /* ------------------------------------------------ state access (tests, tools) */
 

@@ -151,8 +151,9 @@ void free_all(smc_ctx* c) {
     if (c->precision == SMC_PREC_BF16) tc_free(c); else simt_free(c);
     void* ps[] = {c->X, c->Y, c->Yv, c->Xb, c->XTa, c->theta, c->theta_alt, c->mom, c->grad, c->grad_alt,
                   c->shadow, c->logw, c->wn, c->logpi, c->logpi_alt, c->la, c->lb, c->la_alt, c->lb_alt, c->part,
-                  c->stats_dev, c->anc, c->u_dev, c->err_dev, c->inv_mass, c->z_inject};
+                  c->stats_dev, c->anc, c->u_dev, c->err_dev, c->z_inject};
     for (void* p : ps) cudaFree(p);
+    lp_free(c);
     if (c->stats_host) cudaFreeHost(c->stats_host);
     for (auto& t : c->timers) {
         if (t.a) cudaEventDestroy(t.a);
@@ -354,9 +355,9 @@ smc_status smc_init(const smc_model* model, const smc_data* train, const smc_con
     ok = dalloc(c->theta, flat) && dalloc(c->theta_alt, flat) && dalloc(c->mom, flat) && dalloc(c->grad, flat) &&
          dalloc(c->grad_alt, flat) && dalloc(c->logw, J) && dalloc(c->wn, J) && dalloc(c->logpi, J) &&
          dalloc(c->logpi_alt, J) && dalloc(c->la, J) && dalloc(c->lb, J) && dalloc(c->la_alt, J) &&
-         dalloc(c->lb_alt, J) && dalloc(c->part, (size_t)3 * J * kMaxPartChunks) &&
-         dalloc(c->stats_dev, 16 + kMaxParticles) && dalloc(c->anc, J) && dalloc(c->u_dev, J) &&
-         dalloc(c->err_dev, 1) && dalloc(c->inv_mass, kMaxSegments);
+         dalloc(c->lb_alt, J) && dalloc(c->part, (size_t)4 * J * kMaxPartChunks) &&
+         dalloc(c->stats_dev, 16 + kMaxParticles + 64) && dalloc(c->anc, J) && dalloc(c->u_dev, J) &&
+         dalloc(c->err_dev, 1);
     if (ok) ok = cudaMallocHost((void**)&c->stats_host, 64 * sizeof(double)) == cudaSuccess;
     if (ok && c->precision == SMC_PREC_BF16) {
         c->xta_rows = rup(c->in_feat + 1, 8);
@@ -371,10 +372,9 @@ smc_status smc_init(const smc_model* model, const smc_data* train, const smc_con
     }
     cudaMemsetAsync(c->theta, 0, flat * sizeof(float), c->stream);
     cudaMemsetAsync(c->grad, 0, flat * sizeof(float), c->stream);
-    cudaMemsetAsync(c->part, 0, (size_t)3 * J * kMaxPartChunks * sizeof(double), c->stream);
+    cudaMemsetAsync(c->part, 0, (size_t)4 * J * kMaxPartChunks * sizeof(double), c->stream);
     cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
-    std::vector<float> ones(kMaxSegments, 1.0f);
-    e = cudaMemcpyAsync(c->inv_mass, ones.data(), kMaxSegments * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    e = lp_alloc(c);
     if (e == cudaSuccess && c->precision == SMC_PREC_BF16) e = launch_bf16_data(c);
     // theta_0 ~ q_0 = N(0, sigma^2 I) (eq. init_weight)
     if (e == cudaSuccess) e = launch_prior_draw(c);
@@ -429,7 +429,11 @@ smc_status smc_step(smc_ctx* c, const smc_step_params* p, smc_step_stats* stats)
     if (!c || !p) return SMC_EINVAL;
     if (!ok_ctx(c) || !c->scheduled) return SMC_ESTATE;
     if (!(p->h >= 0.0) || p->S < 1 || p->S > 1000) return fail(c, SMC_EINVAL, "step arguments");
-    if (p->proposal != SMC_PROPOSAL_PLAIN) return fail(c, SMC_EUNSUPPORTED, "learned proposal not built");
+    if (p->proposal < SMC_PROPOSAL_PLAIN || p->proposal > SMC_PROPOSAL_EXPLORE)
+        return fail(c, SMC_EINVAL, "unknown proposal");
+    if (p->proposal == SMC_PROPOSAL_EXPLORE &&
+        (p->groups < 2 || p->groups > kMaxGroups || p->groups > c->J || !(p->explore_sigma >= 0.0)))
+        return fail(c, SMC_EINVAL, "exploration needs 2..16 groups (<= J) and sigma >= 0");
     int evals = 0;
     smc_status st;
     // gradient of log pi_k at theta_{k-1} (the target may have changed since it was cached)
@@ -437,7 +441,25 @@ smc_status smc_step(smc_ctx* c, const smc_step_params* p, smc_step_stats* stats)
         if ((st = engine_eval(c)) != SMC_OK) return st;
         ++evals;
     }
-    cudaError_t e = launch_momentum(c, c->pending_noise);
+    int used = p->proposal;
+    if (used == SMC_PROPOSAL_LEARNED && c->lp_fallback) {
+        used = SMC_PROPOSAL_PLAIN;
+        c->lp_fallback = false;
+    }
+    cudaError_t e = cudaSuccess;
+    int G = 0;
+    if (used == SMC_PROPOSAL_PLAIN) {
+        c->lp_groups = 0;
+        c->lp_track_jump = false;
+    } else {
+        G = used == SMC_PROPOSAL_EXPLORE ? p->groups : 1;
+        e = lp_prepare(c, G, used == SMC_PROPOSAL_EXPLORE ? p->explore_sigma : 0.0, false);
+        if (e != cudaSuccess) return cuda_check(c, e, "learned proposal");
+        c->lp_groups = G;
+        c->lp_track_jump = used == SMC_PROPOSAL_EXPLORE;
+    }
+    c->lp_last_groups = G;
+    e = launch_momentum(c, c->pending_noise);
     c->pending_noise = false;
     const double h = p->h;
     fam_begin(c, F_LEAPFROG);
@@ -456,8 +478,30 @@ smc_status smc_step(smc_ctx* c, const smc_step_params* p, smc_step_stats* stats)
     e = launch_weights(c, 1);
     fam_end(c, F_WEIGHTS);
     if (e != cudaSuccess) return cuda_check(c, e, "weights");
+    if (used == SMC_PROPOSAL_EXPLORE) {
+        e = lp_score(c, G);
+        if (e != cudaSuccess) return cuda_check(c, e, "candidate scores");
+    }
+    double hs = 1.0;
+    if (G > 0) {
+        float hs0 = 1.0f;
+        e = cudaMemcpyAsync(&hs0, c->lp_hscale, sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "step scale");
+        st = read_stats(c, stats, evals, "step");
+        hs = hs0;
+    } else {
+        st = read_stats(c, stats, evals, "step");
+    }
     c->step_index++;
-    return read_stats(c, stats, evals, "step");
+    c->lp_groups = 0;
+    c->lp_track_jump = false;
+    c->lp_last_h = h * hs;
+    if (used == SMC_PROPOSAL_LEARNED && c->ess < 0.1 * c->J) c->lp_fallback = true;
+    if (stats) {
+        stats->proposal_used = used;
+        stats->h_used = h * hs;
+    }
+    return st;
 }
 
 smc_status smc_anneal_next(smc_ctx* c, smc_anneal_info* info) {
@@ -713,6 +757,105 @@ smc_status smc_reset_counters(smc_ctx* c) {
     c->launches = 0;
     for (int f = 0; f < kFamilies; ++f) { c->fam_ms[f] = 0; c->fam_calls[f] = 0; }
     return SMC_OK;
+}
+
+// ------------------------------------------------------- learned proposal
+smc_status smc_learned_params(smc_ctx* c, float* get, const float* set) {
+    if (!c) return SMC_EINVAL;
+    if (!ok_ctx(c)) return SMC_ESTATE;
+    const int np = learned_num_params();
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && get) e = cudaMemcpy(get, c->lp_params, np * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && set) {
+        e = cudaMemcpy(c->lp_params, set, np * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(c->lp_adam, 0, 2 * np * sizeof(float));
+        c->lp_train_steps = 0;
+    }
+    return cuda_check(c, e, "learned params");
+}
+
+smc_status smc_learned_train(smc_ctx* c, int32_t epochs, double lr, double* loss) {
+    if (!c || epochs < 1 || !(lr > 0.0)) return SMC_EINVAL;
+    if (!ok_ctx(c)) return SMC_ESTATE;
+    if (c->lp_rows < 1) return fail(c, SMC_ESTATE, "no training rows collected");
+    cudaError_t e = lp_train(c, epochs, lr, c->stats_dev + 15, c->lp_train_steps);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    double l = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpy(&l, c->stats_dev + 15, sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_check(c, e, "learned train");
+    c->lp_train_steps += epochs;
+    if (loss) *loss = l;
+    return SMC_OK;
+}
+
+smc_status smc_learned_data(smc_ctx* c, int64_t* n_rows, float* F, float* T) {
+    if (!c || !n_rows) return SMC_EINVAL;
+    if (!ok_ctx(c)) return SMC_ESTATE;
+    const int64_t cap = *n_rows;
+    *n_rows = c->lp_rows;
+    const int64_t n = std::min(cap, c->lp_rows);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && F && n > 0) e = cudaMemcpy(F, c->lp_dataF, n * 8 * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && T && n > 0) e = cudaMemcpy(T, c->lp_dataT, n * 2 * sizeof(float), cudaMemcpyDeviceToHost);
+    return cuda_check(c, e, "learned data");
+}
+
+smc_status smc_learned_reset_data(smc_ctx* c) {
+    if (!c) return SMC_EINVAL;
+    c->lp_rows = 0;
+    return SMC_OK;
+}
+
+smc_status smc_learned_load_data(smc_ctx* c, const float* F, const float* T, int64_t n) {
+    if (!c || !F || !T || n < 1) return SMC_EINVAL;
+    if (!ok_ctx(c)) return SMC_ESTATE;
+    if (n > c->lp_cap) return fail(c, SMC_EINVAL, "more rows than the training buffer holds (16384)");
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(c->lp_dataF, F, n * 8 * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->lp_dataT, T, n * 2 * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_check(c, e, "learned load data");
+    c->lp_rows = n;
+    return SMC_OK;
+}
+
+smc_status smc_learned_last(smc_ctx* c, float* F, float* cand, double* scores) {
+    if (!c) return SMC_EINVAL;
+    if (!ok_ctx(c)) return SMC_ESTATE;
+    const int nseg = (int)c->segs.size();
+    const int G = std::max(1, c->lp_last_groups);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && F) e = cudaMemcpy(F, c->lp_feat, nseg * 8 * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && cand)
+        e = cudaMemcpy(cand, c->lp_cand, G * (nseg + 1) * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && scores)
+        e = cudaMemcpy(scores, c->stats_dev + 16 + kMaxParticles, (G + 1) * sizeof(double), cudaMemcpyDeviceToHost);
+    return cuda_check(c, e, "learned last");
+}
+
+int32_t smc_num_segments(const smc_ctx* c) { return c ? (int32_t)c->segs.size() : 0; }
+
+smc_status smc_k_learned_loss_grad(const float* F, const float* T, int64_t n, const float* params, float* grad,
+                                   double* loss, void* stream) {
+    if (!F || !T || !params || !grad || !loss || n < 1 || n > 65536) return SMC_EINVAL;
+    const int np = learned_num_params();
+    cudaStream_t s = (cudaStream_t)stream;
+    float *dF = nullptr, *dT = nullptr, *dP = nullptr, *dG = nullptr, *dS = nullptr;
+    double* dL = nullptr;
+    cudaError_t e = cudaMalloc(&dF, n * 8 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&dT, n * 2 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&dP, np * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&dG, np * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&dS, n * 130 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&dL, sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dF, F, n * 8 * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dT, T, n * 2 * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dP, params, np * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = lp_loss_grad(dF, dT, (int)n, dP, dS, dL, dG, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(grad, dG, np * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(loss, dL, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dF); cudaFree(dT); cudaFree(dP); cudaFree(dG); cudaFree(dS); cudaFree(dL);
+    return e == cudaSuccess ? SMC_OK : SMC_ECUDA;
 }
 
 // ------------------------------------------------------------ stateless

@@ -17,6 +17,7 @@ constexpr int kMaxSegments = 32;
 constexpr int kMaxLayers = 16;
 constexpr int kMaxParticles = 4096;
 constexpr int kFamilies = 9;
+constexpr int kMaxGroups = 16;        // candidate groups of the learned proposal
 enum Family { F_FWD_GEMM = 0, F_HEAD = 1, F_WGRAD_GEMM = 2, F_HIDDEN_GEMM = 3, F_LEAPFROG = 4,
               F_WEIGHTS = 5, F_RESAMPLE = 6, F_SIMT_NET = 7, F_REDUCE = 8 };
 
@@ -105,7 +106,25 @@ struct smc_ctx {
     int32_t* anc = nullptr;          // [J]
     double* u_dev = nullptr;         // [J] uniforms
     int* err_dev = nullptr;          // device-side error flag (timeouts)
-    float* inv_mass = nullptr;       // [n_segments] per-segment inverse mass (learned proposal)
+    // -------- learned proposal (not in the paper; k_learned.cu)
+    int lp_groups = 0;               // 0: plain leapfrog; >= 1: per-group mass/step below are used
+    bool lp_track_jump = false;      // leapfrog records squared jumps (candidate scoring)
+    float* lp_inv_mass = nullptr;    // [kMaxGroups][n_seg] inverse mass per group and segment
+    float* lp_hscale = nullptr;      // [kMaxGroups] step multiplier per group
+    float* lp_params = nullptr;      // network parameters (FP32)
+    float* lp_adam = nullptr;        // Adam moments [2][n_params]
+    float* lp_feat = nullptr;        // features of the current iteration [n_seg][8]
+    float* lp_cand = nullptr;        // candidate (a_s..., b) per group [kMaxGroups][n_seg + 1]
+    float* lp_dataF = nullptr;       // collected features [cap][8]
+    float* lp_dataT = nullptr;       // collected targets [cap][2]
+    float* lp_scratch = nullptr;     // training scratch [cap][66]
+    double* lp_feat_part = nullptr;  // feature partial sums [n_seg][blocks][4]
+    int64_t lp_rows = 0, lp_cap = 0;
+    int64_t lp_feat_blocks = 0;
+    bool lp_fallback = false;        // plain proposal for the next iteration (ESS fell below J/10)
+    double lp_last_h = 0.0;
+    int lp_train_steps = 0;          // Adam steps taken so far (bias correction)
+    int lp_last_groups = 0;
     float* z_inject = nullptr;       // device staging for injected momenta (canonical order)
 
     // -------- network workspace
@@ -189,6 +208,16 @@ cudaError_t k_philox_normals(uint64_t seed, uint32_t sid, uint32_t it, uint64_t 
                              float* out, cudaStream_t s);
 cudaError_t k_philox_u32(uint32_t k0, uint32_t k1, uint32_t c2, uint32_t c3, int64_t n, uint32_t* out,
                          cudaStream_t s);
+
+// ----- learned proposal (k_learned.cu)
+int learned_num_params();
+cudaError_t lp_alloc(smc_ctx* c);
+void lp_free(smc_ctx* c);
+cudaError_t lp_prepare(smc_ctx* c, int G, double sigma, bool force_plain);
+cudaError_t lp_score(smc_ctx* c, int G);
+cudaError_t lp_train(smc_ctx* c, int epochs, double lr, double* loss_dev, int step0);
+cudaError_t lp_loss_grad(const float* F, const float* T, int n, float* params, float* scratch, double* loss,
+                         float* grad, cudaStream_t s);
 
 // ----- FP32 SIMT network engine (k_simt.cu)
 smc_status simt_alloc(smc_ctx* c);

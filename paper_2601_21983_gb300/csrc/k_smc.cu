@@ -7,6 +7,7 @@
 // order by the single-block weight kernel, so every result is run-to-run
 // deterministic.
 #include "internal.h"
+#include "rng.cuh"
 
 #include <math.h>
 
@@ -26,44 +27,6 @@ SegTable seg_table(const smc_ctx* c) {
     }
     if (c->precision == SMC_PREC_BF16 && !c->layers.empty()) t.tc[c->layers[0].seg_w] = 1;
     return t;
-}
-
-// ------------------------------------------------------------ Philox4x32-10
-// Salmon et al., SC 2011: ten rounds of two 32x32->64 multiplies, Weyl key bumps.
-__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r) {
-            k.x += 0x9E3779B9u;
-            k.y += 0xBB67AE85u;
-        }
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-    }
-    return c;
-}
-
-// Box-Muller on (u1, u2) = ((x0 + 1) 2^-32, x1 2^-32).  ln u1 is taken through
-// log1p of (u1 - 1) = -(~x0) 2^-32 when u1 > 1/2 so that u1 near 1 keeps its
-// precision in float32.
-__device__ __forceinline__ float2 box_muller(uint32_t x0, uint32_t x1) {
-    float lnu;
-    if (x0 < 0x80000000u)
-        lnu = logf(((float)x0 + 1.0f) * 2.3283064365386963e-10f);
-    else
-        lnu = log1pf(-(float)(~x0) * 2.3283064365386963e-10f);
-    const float r = sqrtf(-2.0f * lnu);
-    float s, co;
-    sincospif((float)x1 * 4.656612873077393e-10f, &s, &co);
-    return make_float2(r * co, r * s);
-}
-
-__device__ __forceinline__ void normals4(uint64_t seed, uint32_t sid, uint32_t it, uint64_t q, float out[4]) {
-    const uint4 x = philox10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), it, sid),
-                             make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-    const float2 a = box_muller(x.x, x.y), b = box_muller(x.z, x.w);
-    out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
 }
 
 // canonical element e = j*D + d  ->  segment-major address
@@ -146,21 +109,31 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
 //   phase 1 (middle): P += h_kick grad; theta += h_drift M^-1 P      (fused half-kicks, h_kick = h)
 //   phase 2 (last):   P += h_kick grad; KE1 += P'M^-1 P/2
 // Phases 0 and 1 also accumulate |theta|^2 and refresh the BF16 shadow.
+// The particles may be split into G groups (particle j in group j*G/J), group g
+// using inverse masses inv_mass[g*n_seg + s] per segment and steps scaled by
+// hscale[g] (the learned proposal; plain: G = 1, all ones).  With theta_old
+// given, phase 0 saves the starting particles and phase 2 accumulates the
+// squared jump |theta_k - theta_{k-1}|^2 per particle.
 template <int PHASE>
 __global__ void __launch_bounds__(256) leapfrog_kernel(float* __restrict__ theta, float* __restrict__ mom,
                                                        const float* __restrict__ grad,
                                                        __nv_bfloat16* __restrict__ shadow, SegTable t,
-                                                       const float* __restrict__ inv_mass, int J, int nchunks,
+                                                       const float* __restrict__ inv_mass,
+                                                       const float* __restrict__ hscale, int G,
+                                                       float* __restrict__ theta_old, int J, int nchunks,
                                                        float h_kick, float h_drift, float inv_sig2,
                                                        double* __restrict__ part) {
     __shared__ double sh[256];
     const int j = blockIdx.y, ch = blockIdx.x;
-    double ke = 0.0, sq = 0.0;
+    const int grp = (int)(((int64_t)j * G) / J);
+    const float hs = hscale ? hscale[grp] : 1.0f;
+    const float hk = h_kick * hs, hd = h_drift * hs;
+    double ke = 0.0, sq = 0.0, jump = 0.0;
     for (int s = 0; s < t.n; ++s) {
         const int64_t size = t.size[s];
         const int64_t lo = size * ch / nchunks, hi = size * (ch + 1) / nchunks;
         const int64_t base = t.off[s] + (int64_t)j * size;
-        const float im = inv_mass ? inv_mass[s] : 1.0f;
+        const float im = inv_mass ? inv_mass[grp * t.n + s] : 1.0f;
         const float sqrt_m = rsqrtf(im);
         const bool has_shadow = t.tc[s] != 0;
         for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
@@ -168,29 +141,36 @@ __global__ void __launch_bounds__(256) leapfrog_kernel(float* __restrict__ theta
             float th = theta[idx];
             float p = mom[idx];
             if (PHASE == 0) {
+                if (theta_old) theta_old[idx] = th;
                 p *= sqrt_m;
                 ke += 0.5 * (double)(im * p * p);
             }
             const float g = grad[idx] - th * inv_sig2;
-            p = fmaf(h_kick, g, p);
+            p = fmaf(hk, g, p);
             if (PHASE != 2) {
-                th = fmaf(h_drift * im, p, th);
+                th = fmaf(hd * im, p, th);
                 theta[idx] = th;
                 sq += (double)th * (double)th;
                 if (has_shadow) shadow[(int64_t)j * size + e] = __float2bfloat16_rn(th);
             } else {
                 ke += 0.5 * (double)(im * p * p);
+                if (theta_old) {
+                    const double d = (double)th - (double)theta_old[idx];
+                    jump += d * d;
+                }
             }
             mom[idx] = p;
         }
     }
     ke = block_sum(ke, sh);
     sq = block_sum(sq, sh);
+    if (PHASE == 2 && theta_old) jump = block_sum(jump, sh);
     if (threadIdx.x == 0) {
-        // part layout: [q][J][kMaxPartChunks], q = 0 KE0, 1 KE1, 2 |theta|^2
+        // part layout: [q][J][kMaxPartChunks], q = 0 KE0, 1 KE1, 2 |theta|^2, 3 squared jump
         if (PHASE == 0) part[(0 * (int64_t)J + j) * kMaxPartChunks + ch] = ke;
         if (PHASE == 2) part[(1 * (int64_t)J + j) * kMaxPartChunks + ch] = ke;
         if (PHASE != 2) part[(2 * (int64_t)J + j) * kMaxPartChunks + ch] = sq;
+        if (PHASE == 2 && theta_old) part[(3 * (int64_t)J + j) * kMaxPartChunks + ch] = jump;
     }
 }
 
@@ -530,21 +510,22 @@ cudaError_t launch_leapfrog(smc_ctx* c, int phase, double h_kick, double h_drift
     dim3 grid(c->part_chunks, c->J);
     const float inv_sig2 = (float)(1.0 / (c->prior_sigma * c->prior_sigma));
     const SegTable t = seg_table(c);
+    const float* im = c->lp_groups > 0 ? c->lp_inv_mass : nullptr;
+    const float* hsc = c->lp_groups > 0 ? c->lp_hscale : nullptr;
+    const int G = c->lp_groups > 0 ? c->lp_groups : 1;
+    float* told = c->lp_track_jump ? c->theta_alt : nullptr;
     if (phase == 0)
-        SMC_LAUNCH(c, leapfrog_kernel<0><<<grid, 256, 0, c->stream>>>(c->theta, c->mom, c->grad, c->shadow, t,
-                                                                     c->inv_mass, c->J, c->part_chunks,
-                                                                     (float)h_kick, (float)h_drift, inv_sig2,
-                                                                     c->part));
+        SMC_LAUNCH(c, leapfrog_kernel<0><<<grid, 256, 0, c->stream>>>(c->theta, c->mom, c->grad, c->shadow, t, im, hsc,
+                                                                     G, told, c->J, c->part_chunks, (float)h_kick,
+                                                                     (float)h_drift, inv_sig2, c->part));
     else if (phase == 1)
-        SMC_LAUNCH(c, leapfrog_kernel<1><<<grid, 256, 0, c->stream>>>(c->theta, c->mom, c->grad, c->shadow, t,
-                                                                     c->inv_mass, c->J, c->part_chunks,
-                                                                     (float)h_kick, (float)h_drift, inv_sig2,
-                                                                     c->part));
+        SMC_LAUNCH(c, leapfrog_kernel<1><<<grid, 256, 0, c->stream>>>(c->theta, c->mom, c->grad, c->shadow, t, im, hsc,
+                                                                     G, told, c->J, c->part_chunks, (float)h_kick,
+                                                                     (float)h_drift, inv_sig2, c->part));
     else
-        SMC_LAUNCH(c, leapfrog_kernel<2><<<grid, 256, 0, c->stream>>>(c->theta, c->mom, c->grad, c->shadow, t,
-                                                                     c->inv_mass, c->J, c->part_chunks,
-                                                                     (float)h_kick, (float)h_drift, inv_sig2,
-                                                                     c->part));
+        SMC_LAUNCH(c, leapfrog_kernel<2><<<grid, 256, 0, c->stream>>>(c->theta, c->mom, c->grad, c->shadow, t, im, hsc,
+                                                                     G, told, c->J, c->part_chunks, (float)h_kick,
+                                                                     (float)h_drift, inv_sig2, c->part));
     return cudaGetLastError();
 }
 

@@ -20,7 +20,8 @@ LIK_CATEGORICAL, LIK_GAUSSIAN = 0, 1
 PREC_FP32, PREC_BF16 = 0, 1
 RESAMPLE_SYSTEMATIC, RESAMPLE_MULTINOMIAL = 0, 1
 SCHED = {"constant": 0, "fb": 1, "ctr": 2, "linear": 3, "automated": 4, "sda": 5}
-PROPOSAL_PLAIN, PROPOSAL_LEARNED = 0, 1
+PROPOSAL_PLAIN, PROPOSAL_LEARNED, PROPOSAL_EXPLORE = 0, 1, 2
+LEARNED_NUM_PARAMS = 706
 STATUS = {0: "SMC_OK", 1: "SMC_EINVAL", 2: "SMC_ENOMEM", 3: "SMC_ECUDA", 4: "SMC_ESTATE",
           5: "SMC_ENUMERIC", 6: "SMC_ETIMEOUT", 7: "SMC_EUNSUPPORTED"}
 N_FAMILIES = 9
@@ -63,13 +64,14 @@ class smc_schedule(C.Structure):
 
 
 class smc_step_params(C.Structure):
-    _fields_ = [("h", C.c_double), ("S", C.c_int32), ("proposal", C.c_int32)]
+    _fields_ = [("h", C.c_double), ("S", C.c_int32), ("proposal", C.c_int32), ("groups", C.c_int32),
+                ("pad_", C.c_int32), ("explore_sigma", C.c_double)]
 
 
 class smc_step_stats(C.Structure):
     _fields_ = [("ess", C.c_double), ("mean_logpi", C.c_double), ("beta", C.c_double),
                 ("rows", C.c_int64), ("k", C.c_int32), ("n_nonfinite", C.c_int32),
-                ("grad_evals", C.c_int32), ("pad_", C.c_int32)]
+                ("grad_evals", C.c_int32), ("proposal_used", C.c_int32), ("h_used", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad_"}
@@ -107,6 +109,15 @@ _SIGS = {
     "smc_get_ancestors": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smc_get_counters": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_void_p, C.c_int32, C.c_void_p]),
     "smc_reset_counters": (C.c_int, [C.c_void_p]),
+    "smc_learned_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "smc_learned_train": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.POINTER(C.c_double)]),
+    "smc_learned_data": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p]),
+    "smc_learned_reset_data": (C.c_int, [C.c_void_p]),
+    "smc_learned_load_data": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
+    "smc_learned_last": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "smc_num_segments": (C.c_int32, [C.c_void_p]),
+    "smc_k_learned_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                          C.POINTER(C.c_double), C.c_void_p]),
     "smc_k_normalise": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "smc_k_resample": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "smc_k_resample_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -217,9 +228,9 @@ def smc_set_schedule(ctx, sched):
     return st.as_dict()
 
 
-def smc_step(ctx, h, S, proposal=PROPOSAL_PLAIN):
+def smc_step(ctx, h, S, proposal=PROPOSAL_PLAIN, groups=0, explore_sigma=0.0):
     st = smc_step_stats()
-    p = smc_step_params(h, S, proposal)
+    p = smc_step_params(h, S, proposal, groups, 0, explore_sigma)
     _check(load().smc_step(ctx, C.byref(p), C.byref(st)), "smc_step", ctx)
     return st.as_dict()
 
@@ -285,6 +296,62 @@ def smc_get_weights(ctx, J):
     w = np.empty(J, np.float64)
     _check(load().smc_get_weights(ctx, _ptr(w)), "smc_get_weights", ctx)
     return w
+
+
+def smc_learned_params(ctx, set_params=None):
+    got = np.empty(LEARNED_NUM_PARAMS, np.float32)
+    sp = None if set_params is None else np.ascontiguousarray(set_params, np.float32)
+    _check(load().smc_learned_params(ctx, _ptr(got), _ptr(sp)), "smc_learned_params", ctx)
+    return got
+
+
+def smc_learned_train(ctx, epochs, lr):
+    loss = C.c_double(0.0)
+    _check(load().smc_learned_train(ctx, epochs, lr, C.byref(loss)), "smc_learned_train", ctx)
+    return loss.value
+
+
+def smc_learned_data(ctx, cap=16384):
+    n = C.c_int64(cap)
+    F = np.empty((cap, 8), np.float32)
+    T = np.empty((cap, 2), np.float32)
+    _check(load().smc_learned_data(ctx, C.byref(n), _ptr(F), _ptr(T)), "smc_learned_data", ctx)
+    k = min(cap, n.value)
+    return F[:k].copy(), T[:k].copy()
+
+
+def smc_learned_reset_data(ctx):
+    _check(load().smc_learned_reset_data(ctx), "smc_learned_reset_data", ctx)
+
+
+def smc_learned_load_data(ctx, F, T):
+    F = np.ascontiguousarray(F, np.float32)
+    T = np.ascontiguousarray(T, np.float32)
+    _check(load().smc_learned_load_data(ctx, _ptr(F), _ptr(T), F.shape[0]), "smc_learned_load_data", ctx)
+
+
+def smc_num_segments(ctx):
+    return int(load().smc_num_segments(ctx))
+
+
+def smc_learned_last(ctx, groups=1):
+    ns = smc_num_segments(ctx)
+    F = np.empty((ns, 8), np.float32)
+    cand = np.empty((max(groups, 1), ns + 1), np.float32)
+    sc = np.empty(max(groups, 1) + 1, np.float64)
+    _check(load().smc_learned_last(ctx, _ptr(F), _ptr(cand), _ptr(sc)), "smc_learned_last", ctx)
+    return F, cand, sc
+
+
+def smc_k_learned_loss_grad(F, T, params, stream=None):
+    F = np.ascontiguousarray(F, np.float32)
+    T = np.ascontiguousarray(T, np.float32)
+    P = np.ascontiguousarray(params, np.float32)
+    g = np.empty(LEARNED_NUM_PARAMS, np.float32)
+    loss = C.c_double(0.0)
+    _check(load().smc_k_learned_loss_grad(_ptr(F), _ptr(T), F.shape[0], _ptr(P), _ptr(g), C.byref(loss),
+                                          _stream(stream)), "smc_k_learned_loss_grad")
+    return loss.value, g
 
 
 def smc_get_permutation(ctx, N):

@@ -58,5 +58,6 @@ def test_struct_sizes_match_header_layout():
     import ctypes as C
     from paper_2601_21983_gb300 import smc
     assert C.sizeof(smc.smc_layer) == 16
-    assert C.sizeof(smc.smc_step_stats) == 48
+    assert C.sizeof(smc.smc_step_stats) == 56
+    assert C.sizeof(smc.smc_step_params) == 32
     assert C.sizeof(smc.smc_schedule) == 56
