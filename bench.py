@@ -161,6 +161,100 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_tta(args):
+    """Time to test accuracy, learned vs plain proposal (configuration c3):
+    the network is trained on exploratory trajectories of the same setup with
+    other seeds, then both proposals run the same Linear-DA schedule from the
+    same seed; the clock runs over the sampler iterations (GPU-synchronous,
+    test-set evaluation excluded) until the test accuracy first reaches the plain
+    run's final accuracy minus 0.5 pt."""
+    import torch
+    from paper_2601_21983_gb300 import smc as S
+    S.load()
+    stream = torch.cuda.current_stream()
+    n = args.n
+    X, y = make_data(n, seed=0)
+    import synthetic
+    Xt, yt = synthetic.template_images(10000, seed=0, test=True)
+    Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    Xtd = torch.from_numpy(Xt).cuda()
+    probs = torch.empty((10000, NCLS), device="cuda", dtype=torch.float32)
+    model = S.make_model([("dense", DIN, H), ("dense", H, NCLS)], (DIN,), S.ACT_RELU)
+    K = args.tta_iters
+
+    def new_ctx(seed):
+        ctx = S.smc_init(model, Xd, y_class=yd, cfg=S.make_config(args.J, seed, S.PREC_BF16, stream=stream))
+        S.smc_set_schedule(ctx, S.make_schedule("linear", MB, MB, K))
+        return ctx
+
+    # ---- training data from the sampler's own exploratory iterations (other seeds)
+    t0 = time.perf_counter()
+    trainer = new_ctx(100)
+    for rnd, seed in enumerate([100, 101, 102]):
+        ctx = trainer if rnd == 0 else new_ctx(seed)
+        if rnd > 0:
+            S.smc_learned_params(ctx, S.smc_learned_params(trainer))
+            F0, T0 = S.smc_learned_data(trainer)
+            S.smc_learned_load_data(ctx, F0, T0)
+        for k in range(1, args.tta_explore):
+            S.smc_anneal_next(ctx)
+            S.smc_resample(ctx)
+            S.smc_step(ctx, STEP_H, S_LF, S.PROPOSAL_EXPLORE, groups=8, explore_sigma=0.5)
+        S.smc_learned_train(ctx, 300, 0.01)
+        if rnd > 0:
+            S.smc_learned_params(trainer, S.smc_learned_params(ctx))
+            F1, T1 = S.smc_learned_data(ctx)
+            S.smc_learned_load_data(trainer, F1, T1)
+            S.smc_destroy(ctx)
+    trained = S.smc_learned_params(trainer)
+    rows = len(S.smc_learned_data(trainer)[0])
+    S.smc_destroy(trainer)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+
+    def run(prop):
+        ctx = new_ctx(7)
+        if prop == S.PROPOSAL_LEARNED:
+            S.smc_learned_params(ctx, trained)
+        curve, clock = [], 0.0
+        for k in range(1, K):
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            S.smc_anneal_next(ctx)
+            S.smc_resample(ctx)
+            st = S.smc_step(ctx, STEP_H, S_LF, prop)
+            torch.cuda.synchronize()
+            clock += time.perf_counter() - a
+            if k % args.tta_every == 0 or k == K - 1:
+                S.smc_posterior_predict(ctx, Xtd, probs)
+                acc = float((probs.argmax(dim=1).cpu().numpy() == yt).mean())
+                curve.append((k, clock, acc, st["h_used"], st["ess"]))
+        S.smc_destroy(ctx)
+        return curve
+
+    plain = run(S.PROPOSAL_PLAIN)
+    learned = run(S.PROPOSAL_LEARNED)
+    target = plain[-1][2] - 0.005
+
+    def tta(curve):
+        for k, t, acc, _, _ in curve:
+            if acc >= target:
+                return t, k
+        return None, None
+
+    tp, kp = tta(plain)
+    tl, kl = tta(learned)
+    line = {"metric": "time-to-test-acc", "unit": "s", "higher_is_better": False,
+            "value": tl, "plain_value": tp, "speedup": (tp / tl) if (tp and tl) else None,
+            "target_acc": target, "plain_final_acc": plain[-1][2], "learned_final_acc": learned[-1][2],
+            "iters_to_target": {"plain": kp, "learned": kl}, "train_seconds": train_s, "train_rows": rows,
+            "curve_plain": plain, "curve_learned": learned,
+            "config": {"workload": f"c3: MLP {DIN}-{H}-{NCLS} ReLU, J={args.J}, {n} synthetic images, Linear DA "
+                                   f"(C=kappa={MB}, K={K}), HMC S={S_LF}, h={STEP_H}, BF16",
+                       "test_rows": 10000, "eval_every": args.tta_every}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -172,10 +266,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline", action="store_true")
+    ap.add_argument("--tta", action="store_true", help="time-to-test-accuracy, learned vs plain proposal")
+    ap.add_argument("--tta-iters", type=int, default=80)
+    ap.add_argument("--tta-explore", type=int, default=30)
+    ap.add_argument("--tta-every", type=int, default=4)
     args = ap.parse_args()
     args.steps = max(1, args.steps)
     if args.impl == "reference":
         return run_reference(args)
+    if args.tta:
+        return run_tta(args)
 
     import torch
     from paper_2601_21983_gb300 import smc as S

@@ -40,6 +40,14 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
+// Store four 8x8 BF16 matrices transposed: fragment element (row g, cols 2t, 2t+1)
+// of matrix i lands in row 2t / 2t+1, column g of the matrix whose 8 row
+// addresses lanes 8i..8i+7 supply.
+__device__ __forceinline__ void stsm_x4_t(void* p, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {
+    asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1,%2,%3,%4};" ::"r"(su32(p)), "r"(r0),
+                 "r"(r1), "r"(r2), "r"(r3)
+                 : "memory");
+}
 // 8-byte async global->shared copy; src_bytes = 0 fills zeros without reading
 __device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(su32(dst)), "l"(src), "r"(src_bytes) : "memory");
@@ -111,7 +119,7 @@ __global__ void __launch_bounds__(128) head_mma_kernel(
             for (int e = 0; e < 4; ++e) accW[a][b][e] = 0.0f;
 #pragma unroll
     for (int a = 0; a < NT2; ++a) { db1[a][0] = 0.0f; db1[a][1] = 0.0f; }
-    double la = 0.0, lb = 0.0;
+    float la = 0.0f, lb = 0.0f;     // this thread's share; widened to FP64 in the block sum
 
     const int r_begin = sl * rows_per_slice, r_end = min(rows, r_begin + rows_per_slice);
     const int cls[4] = {2 * q4, 2 * q4 + 1, 8 + 2 * q4, 9 + 2 * q4};   // classes of this thread's C fragments
@@ -192,7 +200,7 @@ __global__ void __launch_bounds__(128) head_mma_kernel(
                 se += __shfl_xor_sync(0xffffffffu, se, 1);
                 se += __shfl_xor_sync(0xffffffffu, se, 2);
                 const float lse = mx + logf(se);
-                const int64_t gr = g0 + m;
+                const int64_t gr = g0 + m;   // global row of this sample
                 const int yy = ylab[mt][half];
                 const float coef = (gr < rows_a) ? ca : cb;
 #pragma unroll
@@ -215,23 +223,27 @@ __global__ void __launch_bounds__(128) head_mma_kernel(
             *reinterpret_cast<uint32_t*>(Dl + (r0 + g + 8) * DS + 2 * q4) = adl[1];
             *reinterpret_cast<uint32_t*>(Dl + (r0 + g) * DS + 8 + 2 * q4) = adl[2];
             *reinterpret_cast<uint32_t*>(Dl + (r0 + g + 8) * DS + 8 + 2 * q4) = adl[3];
-            // ---- 4. dH = dl W2, dZ1 = dH * act'(h), db1
+            // ---- 4. dH = dl W2, dZ1 = dH * act'(h), db1; dZ1 staged transposed by stmatrix
 #pragma unroll
-            for (int n2 = 0; n2 < NT2; ++n2) {
-                const __nv_bfloat16* w = W2Ts + (8 * n2 + g) * DS + 2 * q4;
-                float d[4] = {0.f, 0.f, 0.f, 0.f};
-                mma16816(d, adl, *reinterpret_cast<const uint32_t*>(w), *reinterpret_cast<const uint32_t*>(w + 8));
-                const float2 hA = unpack2((n2 & 1) ? af[n2 >> 1][2] : af[n2 >> 1][0]);   // row g
-                const float2 hB = unpack2((n2 & 1) ? af[n2 >> 1][3] : af[n2 >> 1][1]);   // row g+8
-                const float z0 = d[0] * act_grad(ACT, hA.x), z1 = d[1] * act_grad(ACT, hA.y);
-                const float z2 = d[2] * act_grad(ACT, hB.x), z3 = d[3] * act_grad(ACT, hB.y);
-                db1[n2][0] += z0 + z2;
-                db1[n2][1] += z1 + z3;
-                const int col = 8 * n2 + 2 * q4;
-                Zs[col * ZS + r0 + g] = __float2bfloat16_rn(z0);
-                Zs[(col + 1) * ZS + r0 + g] = __float2bfloat16_rn(z1);
-                Zs[col * ZS + r0 + g + 8] = __float2bfloat16_rn(z2);
-                Zs[(col + 1) * ZS + r0 + g + 8] = __float2bfloat16_rn(z3);
+            for (int n2 = 0; n2 < NT2; n2 += 2) {
+                uint32_t zp[4];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int n = n2 + u;
+                    const __nv_bfloat16* w = W2Ts + (8 * n + g) * DS + 2 * q4;
+                    float d[4] = {0.f, 0.f, 0.f, 0.f};
+                    mma16816(d, adl, *reinterpret_cast<const uint32_t*>(w), *reinterpret_cast<const uint32_t*>(w + 8));
+                    const float2 hA = unpack2((n & 1) ? af[n >> 1][2] : af[n >> 1][0]);   // row g
+                    const float2 hB = unpack2((n & 1) ? af[n >> 1][3] : af[n >> 1][1]);   // row g+8
+                    const float z0 = d[0] * act_grad(ACT, hA.x), z1 = d[1] * act_grad(ACT, hA.y);
+                    const float z2 = d[2] * act_grad(ACT, hB.x), z3 = d[3] * act_grad(ACT, hB.y);
+                    db1[n][0] += z0 + z2;
+                    db1[n][1] += z1 + z3;
+                    zp[2 * u] = pack2(z0, z1);       // rows g,   hidden 8n + 2t, +1
+                    zp[2 * u + 1] = pack2(z2, z3);   // rows g+8
+                }
+                const int mi = lane >> 3, i = lane & 7;
+                stsm_x4_t(Zs + (8 * (n2 + (mi >> 1)) + i) * ZS + r0 + (mi & 1) * 8, zp[0], zp[1], zp[2], zp[3]);
             }
         }
         __syncwarp();
@@ -324,8 +336,8 @@ __global__ void __launch_bounds__(128) head_mma_kernel(
     for (int i = t; i < H; i += 128)
         pw[C * H + C + i] = ((red1[i] + red1[HP + i]) + red1[2 * HP + i]) + red1[3 * HP + i];
     double* rl = reinterpret_cast<double*>(red2 + 64);     // [2][128], after the float sums
-    rl[t] = la;
-    rl[128 + t] = lb;
+    rl[t] = (double)la;
+    rl[128 + t] = (double)lb;
     __syncthreads();
     for (int st = 64; st > 0; st >>= 1) {
         if (t < st) { rl[t] += rl[t + st]; rl[128 + t] += rl[128 + t + st]; }

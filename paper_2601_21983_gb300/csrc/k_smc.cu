@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256) leapfrog_kernel(float* __restrict__ theta
     const int grp = (int)(((int64_t)j * G) / J);
     const float hs = hscale ? hscale[grp] : 1.0f;
     const float hk = h_kick * hs, hd = h_drift * hs;
-    double ke = 0.0, sq = 0.0, jump = 0.0;
+    float ke = 0.0f, sq = 0.0f, jump = 0.0f;          // per-thread shares, widened to FP64 in the block sum
     for (int s = 0; s < t.n; ++s) {
         const int64_t size = t.size[s];
         const int64_t lo = size * ch / nchunks, hi = size * (ch + 1) / nchunks;
@@ -143,34 +143,34 @@ __global__ void __launch_bounds__(256) leapfrog_kernel(float* __restrict__ theta
             if (PHASE == 0) {
                 if (theta_old) theta_old[idx] = th;
                 p *= sqrt_m;
-                ke += 0.5 * (double)(im * p * p);
+                ke = fmaf(0.5f * im * p, p, ke);
             }
             const float g = grad[idx] - th * inv_sig2;
             p = fmaf(hk, g, p);
             if (PHASE != 2) {
                 th = fmaf(hd * im, p, th);
                 theta[idx] = th;
-                sq += (double)th * (double)th;
+                sq = fmaf(th, th, sq);
                 if (has_shadow) shadow[(int64_t)j * size + e] = __float2bfloat16_rn(th);
             } else {
-                ke += 0.5 * (double)(im * p * p);
+                ke = fmaf(0.5f * im * p, p, ke);
                 if (theta_old) {
-                    const double d = (double)th - (double)theta_old[idx];
-                    jump += d * d;
+                    const float d = th - theta_old[idx];
+                    jump = fmaf(d, d, jump);
                 }
             }
             mom[idx] = p;
         }
     }
-    ke = block_sum(ke, sh);
-    sq = block_sum(sq, sh);
-    if (PHASE == 2 && theta_old) jump = block_sum(jump, sh);
+    const double ked = block_sum((double)ke, sh);
+    const double sqd = block_sum((double)sq, sh);
+    const double jd = (PHASE == 2 && theta_old) ? block_sum((double)jump, sh) : 0.0;
     if (threadIdx.x == 0) {
         // part layout: [q][J][kMaxPartChunks], q = 0 KE0, 1 KE1, 2 |theta|^2, 3 squared jump
-        if (PHASE == 0) part[(0 * (int64_t)J + j) * kMaxPartChunks + ch] = ke;
-        if (PHASE == 2) part[(1 * (int64_t)J + j) * kMaxPartChunks + ch] = ke;
-        if (PHASE != 2) part[(2 * (int64_t)J + j) * kMaxPartChunks + ch] = sq;
-        if (PHASE == 2 && theta_old) part[(3 * (int64_t)J + j) * kMaxPartChunks + ch] = jump;
+        if (PHASE == 0) part[(0 * (int64_t)J + j) * kMaxPartChunks + ch] = ked;
+        if (PHASE == 2) part[(1 * (int64_t)J + j) * kMaxPartChunks + ch] = ked;
+        if (PHASE != 2) part[(2 * (int64_t)J + j) * kMaxPartChunks + ch] = sqd;
+        if (PHASE == 2 && theta_old) part[(3 * (int64_t)J + j) * kMaxPartChunks + ch] = jd;
     }
 }
 
