@@ -349,3 +349,79 @@ def test_error_statuses():
             S.smc_set_uniforms(ctx, [1.5])
     finally:
         S.smc_destroy(ctx)
+
+
+# ------------------------------------------------- configuration-shaped cases
+CNN2 = nn.Spec([("conv", 3, 16, 5), ("pool2",), ("conv", 16, 32, 5), ("pool2",), ("dense", 800, 10)],
+               (3, 32, 32), nn.TANH)
+MLP4 = nn.Spec([("dense", 784, 400), ("dense", 400, 400), ("dense", 400, 10)], (784,), nn.RELU)
+
+
+def test_cnn_config_sda_parity():
+    """3x32x32 10-class smooth-field images, CNN conv5x5 3->16, pool, conv5x5
+    16->32, pool, fc 800->10 (tanh), SDA schedule: FP32 engine against the
+    oracle over three iterations (anneal, resample, move)."""
+    N, J = 96, 4
+    X, y = synthetic.smooth_field_images(N, seed=12)
+    ctx, orc, _ = make_pair(CNN2, X, y, J, seed=12, chunk=40)
+    try:
+        th0 = synthetic.particles(J, CNN2.n_params, 12, std=0.1)
+        S.smc_set_state(ctx, th0)
+        S.smc_set_schedule(ctx, S.make_schedule("sda", 32, 32, 20, delta_s=20.0))
+        orc.set_schedule("sda", 32, 32, 20, th0, delta_s=20.0)
+        lp, g, la, lb = S.smc_eval(ctx, J, CNN2.n_params)
+        rlp, rg, rla, rlb = oracle_eval(orc)
+        assert np.allclose(lb, rlb, rtol=1e-5) and _per_particle_rel(g, rg) < 1e-5
+        for k in range(1, 4):
+            beta_prev = orc.sda.beta
+            info = S.smc_anneal_next(ctx)
+            orc.anneal_next()
+            assert info["rows"] == orc.subset_rows
+            assert abs(info["beta"] - orc.sda.beta) <= 1e-3 * abs(orc.sda.beta - beta_prev) + 1e-12
+            S.smc_set_uniforms(ctx, [0.3])
+            S.smc_resample(ctx)
+            orc.resample(u=0.3)
+            z = synthetic.normals((J, CNN2.n_params), 40 + k)
+            S.smc_set_noise(ctx, z)
+            S.smc_step(ctx, 0.005, 2)
+            orc.step(0.005, 2, z)
+            th, _, lp = S.smc_get_state(ctx, J, CNN2.n_params)
+            assert _per_particle_rel(th, orc.theta) < 1e-5 and np.allclose(lp, orc.logpi, rtol=1e-5)
+    finally:
+        S.smc_destroy(ctx)
+
+
+def test_two_hidden_layer_config_parity_and_fd():
+    """MLP 784-400-400-10 ReLU on the MNIST-shaped data: gradient against the
+    oracle and a finite-difference check of the library's own adjoint on 64
+    random coordinates per particle (log pi evaluated by the library)."""
+    N, J = 200, 2
+    X, y = _images(N, 13)
+    ctx, orc, _ = make_pair(MLP4, X, y, J, seed=13)
+    try:
+        th0 = synthetic.particles(J, MLP4.n_params, 13, std=0.05)
+        S.smc_set_state(ctx, th0)
+        S.smc_set_schedule(ctx, S.make_schedule("fb", N, N, 5))
+        orc.set_schedule("fb", N, N, 5, th0)
+        lp, g, la, lb = S.smc_eval(ctx, J, MLP4.n_params)
+        rlp, rg, rla, rlb = oracle_eval(orc)
+        assert np.allclose(lp, rlp, rtol=1e-5) and _per_particle_rel(g, rg) < 1e-5
+        r = np.random.default_rng(13)
+        eps = 1e-2
+        fd_err = []
+        for j in range(J):
+            idx = r.choice(MLP4.n_params, 64, replace=False)
+            for i in idx:
+                vals = []
+                for sgn in (1.0, -1.0):
+                    th = th0.copy()
+                    th[j, i] += sgn * eps
+                    S.smc_set_state(ctx, th)
+                    vals.append(S.smc_eval(ctx, J, MLP4.n_params)[0][j])
+                fd = (vals[0] - vals[1]) / (2 * eps)
+                # gradient of log pi includes the prior term -theta / sigma^2
+                fd_err.append(abs(fd - (g[j, i] - th0[j, i])) / max(1.0, abs(fd)))
+        # a ReLU kink inside +-eps spoils single coordinates, so the bound is on quantiles
+        assert np.median(fd_err) < 1e-2 and np.percentile(fd_err, 90) < 0.05
+    finally:
+        S.smc_destroy(ctx)
