@@ -63,10 +63,11 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
 __device__ __forceinline__ float2 unpack2(uint32_t u) {
     return __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&u));
 }
-__device__ __forceinline__ float act_grad(int act, float h) {
-    if (act == SMC_ACT_TANH) return 1.0f - h * h;
-    if (act == SMC_ACT_RELU) return h > 0.0f ? 1.0f : 0.0f;
-    return 1.0f;
+// d * act'(h) expressed through the activation's output h
+__device__ __forceinline__ float act_bwd(int act, float d, float h) {
+    if (act == SMC_ACT_TANH) return d * (1.0f - h * h);
+    if (act == SMC_ACT_RELU) return h > 0.0f ? d : 0.0f;
+    return d;
 }
 
 }  // namespace
@@ -194,24 +195,27 @@ __global__ void __launch_bounds__(128) head_mma_kernel(
                 for (int e = 0; e < 4; ++e) if (cls[e] < C) mx = fmaxf(mx, z[e]);
                 mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
                 mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-                float se = 0.0f;
+                float ez[4], se = 0.0f;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) if (cls[e] < C) se += expf(z[e] - mx);
+                for (int e = 0; e < 4; ++e) {
+                    ez[e] = (cls[e] < C) ? __expf(z[e] - mx) : 0.0f;
+                    se += ez[e];
+                }
                 se += __shfl_xor_sync(0xffffffffu, se, 1);
                 se += __shfl_xor_sync(0xffffffffu, se, 2);
-                const float lse = mx + logf(se);
+                const float inv_se = __frcp_rn(se);
+                const float lse = mx + __logf(se);
                 const int64_t gr = g0 + m;   // global row of this sample
                 const int yy = ylab[mt][half];
                 const float coef = (gr < rows_a) ? ca : cb;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    float d = 0.0f;
-                    if (valid && cls[e] < C) d = coef * (((cls[e] == yy) ? 1.0f : 0.0f) - expf(z[e] - lse));
-                    if (valid && cls[e] == yy) {
+                    const bool hit = cls[e] == yy;
+                    dl[e >> 1][2 * half + (e & 1)] = valid ? coef * ((hit ? 1.0f : 0.0f) - ez[e] * inv_se) : 0.0f;
+                    if (valid && hit) {
                         const float ll = z[e] - lse;
                         if (gr < rows_a) la += ll; else lb += ll;
                     }
-                    dl[e >> 1][2 * half + (e & 1)] = d;
                 }
             }
 #pragma unroll
@@ -235,8 +239,8 @@ __global__ void __launch_bounds__(128) head_mma_kernel(
                     mma16816(d, adl, *reinterpret_cast<const uint32_t*>(w), *reinterpret_cast<const uint32_t*>(w + 8));
                     const float2 hA = unpack2((n & 1) ? af[n >> 1][2] : af[n >> 1][0]);   // row g
                     const float2 hB = unpack2((n & 1) ? af[n >> 1][3] : af[n >> 1][1]);   // row g+8
-                    const float z0 = d[0] * act_grad(ACT, hA.x), z1 = d[1] * act_grad(ACT, hA.y);
-                    const float z2 = d[2] * act_grad(ACT, hB.x), z3 = d[3] * act_grad(ACT, hB.y);
+                    const float z0 = act_bwd(ACT, d[0], hA.x), z1 = act_bwd(ACT, d[1], hA.y);
+                    const float z2 = act_bwd(ACT, d[2], hB.x), z3 = act_bwd(ACT, d[3], hB.y);
                     db1[n][0] += z0 + z2;
                     db1[n][1] += z1 + z3;
                     zp[2 * u] = pack2(z0, z1);       // rows g,   hidden 8n + 2t, +1
