@@ -38,6 +38,7 @@ enum { ERR_PRODUCER = 0x101, ERR_MMA = 0x102, ERR_EPILOGUE = 0x103 };
 struct GemmArgs {
     int M, N, K;
     int tiles_m, tiles_n, kslices, kb_total, kb_per_slice, num_units;
+    int cs;                 // CTAs per cluster sharing each B tile (units are per cluster)
     int epi;
     void* out;              // BF16 [M][ldo] or FP32 [M][ldo] (+ ks * slice_stride)
     int64_t ldo;
@@ -103,6 +104,25 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
         : "memory");
 }
 
+// TMA load delivered to the same shared-memory offset of every CTA in ctaMask,
+// each completing tx bytes on the mbarrier at the same offset.
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3}], [%4], %5;"
+        ::"r"(su32(dst)), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(su32(bar)), "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // TMA store of a [rows][cols] box from shared memory (bulk async-group)
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* tm, const void* src, int x, int y) {
     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
@@ -137,6 +157,12 @@ __device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t a, uint64_t b, ui
 // Arrive on an mbarrier once every previously issued tcgen05.mma of this thread completed.
 __device__ __forceinline__ void umma_commit(uint64_t* b) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
+                 : "memory");
+}
+// Same, arriving on the mbarrier at this offset in every CTA of ctaMask.
+__device__ __forceinline__ void umma_commit_mc(uint64_t* b, uint16_t mask) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                 ::"r"(su32(b)), "h"(mask)
                  : "memory");
 }
 
@@ -181,11 +207,13 @@ __device__ __forceinline__ void raise_abort(const GemmArgs& g, volatile int* abo
     if (g.err) atomicCAS(g.err, 0, code);
 }
 
-__device__ __forceinline__ void decode(const GemmArgs& g, int u, int& tm, int& tn, int& ks) {
+// Cluster unit u -> this CTA's tile: the CTAs of a cluster share (tn, ks) and take
+// consecutive m-tiles.
+__device__ __forceinline__ void decode(const GemmArgs& g, int u, int rank, int& tm, int& tn, int& ks) {
     tn = u % g.tiles_n;
     const int rest = u / g.tiles_n;
     ks = rest % g.kslices;
-    tm = rest / g.kslices;
+    tm = (rest / g.kslices) * g.cs + rank;
 }
 
 // Epilogue store of 32 accumulator columns of one row.
@@ -235,7 +263,7 @@ __device__ __forceinline__ void epi_store(const GemmArgs& g, int row, int col0, 
     }
 }
 
-template <int BN, int BNBOX, int STAGES>
+template <int BN, int BNBOX, int STAGES, int CS>
 struct Cfg {
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
@@ -248,15 +276,20 @@ struct Cfg {
     static constexpr int SMEM = STAGES * STAGE_BYTES + STAGING + 1024 /*align*/ + 256 /*barriers*/;
     static_assert(BN % 16 == 0 && N0 % 16 == 0 && N1 % 16 == 0, "N must be a multiple of 16");
     static_assert(BN % BNBOX == 0 && BNBOX <= 256, "TMA box rows <= 256");
+    static_assert(CS == 1 || BN == CS * BNBOX, "each CTA of a cluster loads one B slice");
+    static_assert((BNBOX * 128) % 1024 == 0, "B slices start on a swizzle atom");
     static_assert(ACC * BN <= 512, "TMEM has 512 columns");
     static_assert(SMEM <= 232448, "shared memory");
 };
 
-template <int BN, int BNBOX, int STAGES>
+template <int BN, int BNBOX, int STAGES, int CS>
 __global__ void __launch_bounds__(192, 1)
 gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             const __grid_constant__ CUtensorMap tmC, const GemmArgs g) {
-    using C = Cfg<BN, BNBOX, STAGES>;
+    using C = Cfg<BN, BNBOX, STAGES, CS>;
+    const int rank = CS > 1 ? (int)cluster_rank() : 0;
+    const int cid = blockIdx.x / CS, ncl = gridDim.x / CS;
+    constexpr uint16_t kMask = (uint16_t)((1u << CS) - 1);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* staging = smem + STAGES * C::STAGE_BYTES;
@@ -270,7 +303,8 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
+        // empty[s] completes when the MMAs of every CTA of the cluster released stage s
+        for (int s = 0; s < STAGES; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, CS); }
         for (int a = 0; a < C::ACC; ++a) { mbar_init(tfull + a, 1); mbar_init(tempty + a, 4); }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -279,6 +313,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     if (warp == 1) tmem_alloc(tslot, C::TCOLS);
     tc_fence_before();
     __syncthreads();
+    if (CS > 1) cluster_sync();   // the peers' barriers exist before any multicast reaches them
     tc_fence_after();
     const uint32_t tbase = *tslot;
 
@@ -289,19 +324,25 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             uint32_t ph = 0;
             int issued = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < g.num_units && ok; u += gridDim.x) {
+            for (int u = cid; u < g.num_units && ok; u += ncl) {
                 int tm, tn, ks;
-                decode(g, u, tm, tn, ks);
+                decode(g, u, rank, tm, tn, ks);
                 const int kb0 = ks * g.kb_per_slice, kb1 = min(g.kb_total, kb0 + g.kb_per_slice);
                 for (int kb = kb0; kb < kb1; ++kb) {
                     if (!mbar_wait(empty + stage, ph ^ 1, abort_flag)) { ok = false; break; }
-                    mbar_expect_tx(full + stage, C::STAGE_BYTES);
+                    mbar_expect_tx(full + stage, C::STAGE_BYTES);   // A + every B slice of the stage
                     uint8_t* sa = smem + stage * C::STAGE_BYTES;
                     uint8_t* sb = sa + C::A_BYTES;
                     tma_load_2d(sa, &tmA, kb * BK, tm * BM, full + stage);
+                    if (CS == 1) {
 #pragma unroll
-                    for (int b = 0; b < BN / BNBOX; ++b)
-                        tma_load_2d(sb + b * BNBOX * 128, &tmB, kb * BK, tn * BN + b * BNBOX, full + stage);
+                        for (int b = 0; b < BN / BNBOX; ++b)
+                            tma_load_2d(sb + b * BNBOX * 128, &tmB, kb * BK, tn * BN + b * BNBOX, full + stage);
+                    } else {
+                        // this CTA's slice of the shared B tile, delivered to all CTAs of the cluster
+                        tma_load_2d_mc(sb + rank * BNBOX * 128, &tmB, kb * BK, tn * BN + rank * BNBOX, full + stage,
+                                       kMask);
+                    }
                     ++issued;
                     if (++stage == STAGES) { stage = 0; ph ^= 1; }
                 }
@@ -324,9 +365,9 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             int acc = 0;
             uint32_t aph = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < g.num_units && ok; u += gridDim.x) {
+            for (int u = cid; u < g.num_units && ok; u += ncl) {
                 int tm, tn, ks;
-                decode(g, u, tm, tn, ks);
+                decode(g, u, rank, tm, tn, ks);
                 const int kb0 = ks * g.kb_per_slice, kb1 = min(g.kb_total, kb0 + g.kb_per_slice);
                 if (!mbar_wait(tempty + acc, aph ^ 1, abort_flag)) { ok = false; break; }
                 tc_fence_after();
@@ -344,7 +385,8 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         umma_bf16(dt, ad, sdesc(sb + k * 32), ID0, accum);
                         if (C::N1 > 0) umma_bf16(dt + C::N0, ad, sdesc(sb + C::N0 * 128 + k * 32), ID1, accum);
                     }
-                    umma_commit(empty + stage);
+                    if (CS == 1) umma_commit(empty + stage);
+                    else umma_commit_mc(empty + stage, kMask);   // frees the stage in every CTA of the cluster
                     if (++stage == STAGES) { stage = 0; ph ^= 1; }
                 }
                 if (!ok) break;
@@ -366,9 +408,9 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         int acc = 0;
         uint32_t aph = 0;
         int chunk_no = 0;
-        for (int u = blockIdx.x; u < g.num_units; u += gridDim.x) {
+        for (int u = cid; u < g.num_units; u += ncl) {
             int tm, tn, ks;
-            decode(g, u, tm, tn, ks);
+            decode(g, u, rank, tm, tn, ks);
             float bq[NCH];
             if (g.epi == EPI_BF16_BIAS_ACT) {
 #pragma unroll
@@ -444,6 +486,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
     tc_fence_before();
     __syncthreads();
+    if (CS > 1) cluster_sync();   // no CTA leaves while a peer may still multicast into it
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tbase, C::TCOLS);
@@ -493,11 +536,12 @@ static bool make_store_tmap(CUtensorMap* m, const void* base, uint64_t inner, ui
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int BNBOX, int STAGES>
+template <int BN, int BNBOX, int STAGES, int CS>
 static cudaError_t launch_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, GemmArgs g, cudaStream_t s,
                                int num_sms) {
-    using C = Cfg<BN, BNBOX, STAGES>;
+    using C = Cfg<BN, BNBOX, STAGES, CS>;
     CUtensorMap ta, tb, tc;
+    if (g.cs != CS) return cudaErrorInvalidValue;
     if (!make_tmap(&ta, A, (uint64_t)g.K, (uint64_t)g.M, (uint64_t)lda * 2, BM)) return cudaErrorInvalidValue;
     if (!make_tmap(&tb, B, (uint64_t)g.K, (uint64_t)g.N, (uint64_t)ldb * 2, BNBOX)) return cudaErrorInvalidValue;
     if (g.epi == EPI_BF16_BIAS_ACT) {
@@ -506,27 +550,48 @@ static cudaError_t launch_gemm(const void* A, int64_t lda, const void* B, int64_
     } else {
         tc = ta;   // unused by the FP32 epilogue
     }
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_kernel<BN, BNBOX, STAGES>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    auto kern = gemm_kernel<BN, BNBOX, STAGES, CS>;
+    static int max_clusters = -1;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(192, 1, 1);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (max_clusters < 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        cfg.gridDim = dim3((unsigned)(num_sms - num_sms % CS), 1, 1);
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            n = num_sms / CS;
+        }
+        max_clusters = std::min(n, num_sms / CS);
     }
-    const int grid = std::max(1, std::min(g.num_units, num_sms));
-    gemm_kernel<BN, BNBOX, STAGES><<<grid, 192, C::SMEM, s>>>(ta, tb, tc, g);
+    const int clusters = std::max(1, std::min(g.num_units, max_clusters));
+    cfg.gridDim = dim3((unsigned)(clusters * CS), 1, 1);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ta, tb, tc, g);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-// Fill tiling fields; kslices = 1 unless split-K is requested.
-static void plan(GemmArgs& g, int BN, int kslices) {
+// Fill tiling fields; kslices = 1 unless split-K is requested; units are per
+// cluster of cs CTAs (consecutive m-tiles sharing one B tile).
+static void plan(GemmArgs& g, int BN, int kslices, int cs) {
+    g.cs = cs;
     g.tiles_m = (g.M + BM - 1) / BM;
     g.tiles_n = (g.N + BN - 1) / BN;
     g.kb_total = (g.K + BK - 1) / BK;
     kslices = std::max(1, std::min(kslices, g.kb_total));
     g.kb_per_slice = (g.kb_total + kslices - 1) / kslices;
     g.kslices = (g.kb_total + g.kb_per_slice - 1) / g.kb_per_slice;   // every slice non-empty
-    g.num_units = g.tiles_m * g.tiles_n * g.kslices;
+    g.num_units = ((g.tiles_m + cs - 1) / cs) * g.tiles_n * g.kslices;
 }
 
 // Choose a split-K factor that evens out the last wave of persistent CTAs.
@@ -662,9 +727,9 @@ static cudaError_t tc_forward_layer1(smc_ctx* c, const __nv_bfloat16* x, int64_t
     g.act = L0.act;
     g.aug_col = -1;
     g.err = c->err_dev;
-    plan(g, 256, 1);
+    plan(g, 256, 1, 2);
     fam_begin(c, F_FWD_GEMM);
-    cudaError_t e = launch_gemm<256, 256, 4>(x, c->in_feat, c->shadow, c->in_feat, g, c->stream, c->num_sms);
+    cudaError_t e = launch_gemm<256, 128, 4, 2>(x, c->in_feat, c->shadow, c->in_feat, g, c->stream, c->num_sms);
     c->launches++;
     fam_end(c, F_FWD_GEMM);
     return e;
@@ -705,12 +770,12 @@ smc_status tc_eval(smc_ctx* c) {
         g.M = (int)JH; g.N = (int)Din; g.K = (int)mc;
         g.epi = EPI_F32;
         g.err = c->err_dev;
-        plan(g, 400, 1);
+        plan(g, 400, 1, 2);
         const int ks = choose_kslices(g.tiles_m * g.tiles_n, g.kb_total, c->num_sms, 8);
         const int64_t ldp = rup(Din, 4);
         const int64_t slice = JH * ldp;
         int use_ks = (ks > 1 && (int64_t)ks * slice <= c->gemm_part_cap) ? ks : 1;
-        plan(g, 400, use_ks);
+        plan(g, 400, use_ks, 2);
         float* gW1 = c->grad + c->segs[L0.seg_w].off;
         if (g.kslices > 1) {
             g.out = c->gemm_part; g.ldo = ldp; g.slice_stride = slice; g.aug_col = -1;
@@ -718,7 +783,7 @@ smc_status tc_eval(smc_ctx* c) {
             g.out = gW1; g.ldo = Din; g.accumulate = g0 > 0; g.aug_col = -1;
         }
         fam_begin(c, F_WGRAD_GEMM);
-        e = launch_gemm<400, 200, 3>(c->dZT, ch, c->XTa + g0, c->Npad, g, c->stream, c->num_sms);
+        e = launch_gemm<400, 200, 3, 2>(c->dZT, ch, c->XTa + g0, c->Npad, g, c->stream, c->num_sms);
         c->launches++;
         if (e == cudaSuccess && g.kslices > 1) {
             const int64_t n = JH * Din;
@@ -780,11 +845,11 @@ cudaError_t tc_gemm_public(const void* A, int64_t lda, const void* B, int64_t ld
     g.out = Cout; g.ldo = ldc; g.accumulate = accumulate; g.aug_col = -1;
     g.err = err_dev;
     if (N > 256) {
-        plan(g, 400, 1);
-        return launch_gemm<400, 200, 3>(A, lda, B, ldb, g, s, num_sms);
+        plan(g, 400, 1, 2);
+        return launch_gemm<400, 200, 3, 2>(A, lda, B, ldb, g, s, num_sms);
     }
-    plan(g, 256, 1);
-    return launch_gemm<256, 256, 4>(A, lda, B, ldb, g, s, num_sms);
+    plan(g, 256, 1, 2);
+    return launch_gemm<256, 128, 4, 2>(A, lda, B, ldb, g, s, num_sms);
 }
 
 }  // namespace smc
