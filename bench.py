@@ -372,13 +372,30 @@ def main():
         fam = {k: {"ms": times[k], "calls": calls[k]} for k in times if calls[k]}
         hbm, tf_burst, tf_sus, src = peaks()
         M = args.n
-        flops = {"fwd_gemm": 2.0 * M * args.J * H * DIN, "wgrad_gemm": 2.0 * M * args.J * H * (DIN + 1)}
-        dom = max(("fwd_gemm", "wgrad_gemm"), key=lambda k: times[k])
-        avg_ms = times[dom] / max(1, calls[dom])
-        achieved = flops[dom] / (avg_ms / 1e3) / 1e12
-        roof = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": tf_sus, "unit": "TFLOP/s",
-                "frac": achieved / tf_sus, "peak_kind": f"{src} bf16_tflops_sustained", "traffic": None,
-                "flops_per_launch": flops[dom], "avg_launch_ms": avg_ms}
+        act_bytes = 2.0 * M * args.J * H          # one BF16 activation matrix [M][J*H]
+        # algorithmic work per launch: GEMM FLOPs; the head reads H1 and writes dZ1^T
+        work = {"fwd_gemm": ("tensor", 2.0 * M * args.J * H * DIN),
+                "wgrad_gemm": ("tensor", 2.0 * M * args.J * H * DIN),
+                "head": ("hbm", 2.0 * act_bytes + 4.0 * M)}
+        kern = {}
+        for k, (bound, amount) in work.items():
+            if calls.get(k):
+                avg = times[k] / calls[k]
+                if bound == "tensor":
+                    ach = amount / (avg / 1e3) / 1e12
+                    kern[k] = {"bound": "tensor", "achieved": ach, "peak": tf_sus, "unit": "TFLOP/s",
+                               "frac": ach / tf_sus, "avg_launch_ms": avg, "work_per_launch": amount}
+                else:
+                    ach = amount / (avg / 1e3) / 1e9
+                    kern[k] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                               "avg_launch_ms": avg, "work_per_launch": amount}
+        dom = max(kern, key=lambda k: kern[k]["avg_launch_ms"])
+        roof = dict(kern[dom])
+        roof["kernel"] = dom
+        roof["traffic"] = None
+        roof["peak_kind"] = f"{src} " + ("bf16_tflops_sustained" if roof["bound"] == "tensor" else "hbm_gbs")
+        roof["others"] = {k: {"frac": round(v["frac"], 4), "achieved": round(v["achieved"], 1), "unit": v["unit"],
+                              "avg_launch_ms": round(v["avg_launch_ms"], 4)} for k, v in kern.items() if k != dom}
     S.smc_destroy(ctx)
 
     if rank == 0:
