@@ -373,10 +373,17 @@ def main():
         hbm, tf_burst, tf_sus, src = peaks()
         M = args.n
         act_bytes = 2.0 * M * args.J * H          # one BF16 activation matrix [M][J*H]
-        # algorithmic work per launch: GEMM FLOPs; the head reads H1 and writes dZ1^T
+        # algorithmic work per launch: GEMM FLOPs; the unfused head reads H1 and writes
+        # dZ1^T; the fused kernel does the first-layer GEMM plus the head's three
+        # contractions (logits, W2^T dlogits, dlogits h^T)
         work = {"fwd_gemm": ("tensor", 2.0 * M * args.J * H * DIN),
-                "wgrad_gemm": ("tensor", 2.0 * M * args.J * H * DIN),
-                "head": ("hbm", 2.0 * act_bytes + 4.0 * M)}
+                "head": ("hbm", 2.0 * act_bytes + 4.0 * M),
+                "fused_fwd_head": ("tensor", 2.0 * M * args.J * H * DIN + 6.0 * M * args.J * H * NCLS)}
+        if calls.get("fused_fwd_head"):
+            work.pop("head")      # only the particle-image kernel is counted there
+            work["wgrad_gemm"] = ("tensor", 2.0 * M * args.J * H * (DIN + 1))
+        else:
+            work["wgrad_gemm"] = ("tensor", 2.0 * M * args.J * H * DIN)
         kern = {}
         for k, (bound, amount) in work.items():
             if calls.get(k):

@@ -11,7 +11,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsmc.so")
-SOURCES = ["api.cu", "k_smc.cu", "k_simt.cu", "k_tc.cu", "k_head.cu", "k_learned.cu"]
+SOURCES = ["api.cu", "k_smc.cu", "k_simt.cu", "k_tc.cu", "k_head.cu", "k_fused.cu", "k_learned.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -34,7 +34,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
     nvcc = _nvcc()
     objdir = os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)
-    headers = [os.path.join(CSRC, "internal.h"), os.path.join(HERE, "..", "include", "smc.h"), __file__]
+    headers = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".h", ".cuh"))]
+    headers += [os.path.join(HERE, "..", "include", "smc.h"), __file__]
 
     def compile_one(src):
         path = os.path.join(CSRC, src)

@@ -16,10 +16,10 @@ namespace smc {
 constexpr int kMaxSegments = 32;
 constexpr int kMaxLayers = 16;
 constexpr int kMaxParticles = 4096;
-constexpr int kFamilies = 9;
+constexpr int kFamilies = 10;
 constexpr int kMaxGroups = 16;        // candidate groups of the learned proposal
 enum Family { F_FWD_GEMM = 0, F_HEAD = 1, F_WGRAD_GEMM = 2, F_HIDDEN_GEMM = 3, F_LEAPFROG = 4,
-              F_WEIGHTS = 5, F_RESAMPLE = 6, F_SIMT_NET = 7, F_REDUCE = 8 };
+              F_WEIGHTS = 5, F_RESAMPLE = 6, F_SIMT_NET = 7, F_REDUCE = 8, F_FUSED = 9 };
 
 // Philox stream identifiers (counter word 3).
 enum : uint32_t { RNG_PRIOR = 1, RNG_MOMENTUM = 2 };
@@ -139,6 +139,8 @@ struct smc_ctx {
     float* head_part = nullptr;      // [slices][J][C*H + C]
     double* head_ll = nullptr;       // [slices][J][2]
     int64_t head_slices_cap = 0;
+    uint8_t* fimg = nullptr;         // fused kernel: per-particle W2 / b1 / b2 images
+    bool fused = true;               // first-layer GEMM and head in one kernel
     float* gemm_part = nullptr;      // split-K partials
     int64_t gemm_part_cap = 0;
 
@@ -237,6 +239,12 @@ smc_status tc_predict(smc_ctx* c, const float* x, int64_t n, float* out);
 // head / adjoint on mma.sync fragments (k_head.cu)
 cudaError_t launch_head_mma(smc_ctx* c, int H, int C, int mc, int64_t g0, int act, const float* W2, const float* b2,
                             const __nv_bfloat16* H1, int64_t ldh, int slot, int nsl, int rows_per_slice);
+// first-layer GEMM + head / adjoint in one kernel (k_fused.cu)
+int64_t fused_image_bytes(const smc_ctx* c);
+int64_t fused_slots(const smc_ctx* c, int64_t mc);
+cudaError_t launch_fused_images(smc_ctx* c);
+cudaError_t launch_fused_fwd_head(smc_ctx* c, const __nv_bfloat16* x, int64_t g0, int64_t mc, int slot_base,
+                                  int* nslots);
 cudaError_t tc_gemm_public(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
                            int64_t M, int64_t N, int64_t K, int accumulate, cudaStream_t s, int* err_dev,
                            int num_sms);

@@ -16,61 +16,10 @@
 // order into per-slice partials (same layout as the reduce kernel expects:
 // dW2 [C*H] | db2 [C] | db1 [H] per (slice, particle)).
 #include "internal.h"
+#include "mma_ptx.cuh"
 
 namespace smc {
-namespace {
-
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(su32(p)));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(su32(p)));
-}
-// D += A (16x16, row) * B (16x8, col), BF16 inputs, FP32 accumulators
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-// Store four 8x8 BF16 matrices transposed: fragment element (row g, cols 2t, 2t+1)
-// of matrix i lands in row 2t / 2t+1, column g of the matrix whose 8 row
-// addresses lanes 8i..8i+7 supply.
-__device__ __forceinline__ void stsm_x4_t(void* p, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {
-    asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1,%2,%3,%4};" ::"r"(su32(p)), "r"(r0),
-                 "r"(r1), "r"(r2), "r"(r3)
-                 : "memory");
-}
-// 8-byte async global->shared copy; src_bytes = 0 fills zeros without reading
-__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(su32(dst)), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&v);
-}
-__device__ __forceinline__ float2 unpack2(uint32_t u) {
-    return __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&u));
-}
-// d * act'(h) expressed through the activation's output h
-__device__ __forceinline__ float act_bwd(int act, float d, float h) {
-    if (act == SMC_ACT_TANH) return d * (1.0f - h * h);
-    if (act == SMC_ACT_RELU) return h > 0.0f ? d : 0.0f;
-    return d;
-}
-
-}  // namespace
+using namespace mm;
 
 // KT: hidden width padded to 16*KT (H <= 16*KT, H % 4 == 0); classes C <= 16;
 // ACT: activation of the hidden layer (SMC_ACT_*).

@@ -23,7 +23,11 @@
 
 #include <cudaTypedefs.h>
 
+#include "tc_ptx.cuh"
+#include "tmap.cuh"
+
 #include <algorithm>
+#include <stdlib.h>
 #include <math.h>
 
 namespace smc {
@@ -31,7 +35,6 @@ namespace tcg {
 
 constexpr int BM = 128;
 constexpr int BK = 64;                         // 64 BF16 = one 128-byte swizzle row
-constexpr uint64_t kTimeoutNs = 2000000000ull; // 2 s per wait
 enum { EPI_BF16_BIAS_ACT = 0, EPI_F32 = 1 };
 enum { ERR_PRODUCER = 0x101, ERR_MMA = 0x102, ERR_EPILOGUE = 0x103 };
 
@@ -50,151 +53,6 @@ struct GemmArgs {
     int aug_col;            // < 0: none; columns > aug_col are dropped
     int* err;
 };
-
-// ------------------------------------------------------------ PTX wrappers
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t gtimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(su32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait: false on timeout or when another role raised the abort flag.
-__device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
-    if (mbar_try(b, parity)) return true;
-    const uint64_t t0 = gtimer();
-    for (uint32_t it = 1; it < (1u << 26); ++it) {
-        if (mbar_try(b, parity)) return true;
-        if ((it & 127) == 0) {
-            if (abort_flag != nullptr && *abort_flag) return false;
-            if (gtimer() - t0 > kTimeoutNs) return false;
-        }
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(su32(dst)), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(su32(bar))
-        : "memory");
-}
-
-// TMA load delivered to the same shared-memory offset of every CTA in ctaMask,
-// each completing tx bytes on the mbarrier at the same offset.
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar,
-                                               uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3}], [%4], %5;"
-        ::"r"(su32(dst)), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(su32(bar)), "h"(mask)
-        : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// TMA store of a [rows][cols] box from shared memory (bulk async-group)
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* tm, const void* src, int x, int y) {
-    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
-                 ::"l"((uint64_t)tm), "r"(x), "r"(y), "r"(su32(src))
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)), "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulate, M = 128.
-__device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(accum)
-        : "memory");
-}
-// Arrive on an mbarrier once every previously issued tcgen05.mma of this thread completed.
-__device__ __forceinline__ void umma_commit(uint64_t* b) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
-                 : "memory");
-}
-// Same, arriving on the mbarrier at this offset in every CTA of ctaMask.
-__device__ __forceinline__ void umma_commit_mc(uint64_t* b, uint16_t mask) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-                 ::"r"(su32(b)), "h"(mask)
-                 : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row groups 1024 bytes apart (stride byte offset), version 1.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
-    d |= (uint64_t)1 << 46;                 // descriptor version
-    d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
-    return d;
-}
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-#define TMEM_LD32(taddr, r)                                                                                     \
-    asm volatile(                                                                                               \
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "                                                               \
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,"   \
-        "%27,%28,%29,%30,%31}, [%32];"                                                                          \
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),       \
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),              \
-          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),            \
-          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),            \
-          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])                                                                 \
-        : "r"(taddr))
-
-__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ float act_f(int a, float z) {
     if (a == SMC_ACT_TANH) return tanhf(z);
@@ -494,48 +352,6 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 }
 
 // ------------------------------------------------------------- host side
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (fn == nullptr) {
-        cudaDriverEntryPointQueryResult q;
-        void* p = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
-    return fn;
-}
-
-// 2-D BF16 tensor [outer][inner] with row pitch `pitch` bytes; box {64, box_rows}.
-static bool make_tmap(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t pitch,
-                      uint32_t box_rows) {
-    auto enc = encode_fn();
-    if (!enc) return false;
-    if (((uintptr_t)base & 15) || (pitch & 15)) return false;
-    cuuint64_t dims[2] = {inner, outer};
-    cuuint64_t strides[1] = {pitch};
-    cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
-    cuuint32_t es[2] = {1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// 2-D BF16 tensor [outer][inner] for TMA stores: box {32, 32}, no swizzle.
-static bool make_store_tmap(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t pitch) {
-    auto enc = encode_fn();
-    if (!enc) return false;
-    if (((uintptr_t)base & 15) || (pitch & 15)) return false;
-    cuuint64_t dims[2] = {inner, outer};
-    cuuint64_t strides[1] = {pitch};
-    cuuint32_t box[2] = {32, 32};
-    cuuint32_t es[2] = {1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 template <int BN, int BNBOX, int STAGES, int CS>
 static cudaError_t launch_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, GemmArgs g, cudaStream_t s,
                                int num_sms) {
@@ -611,12 +427,13 @@ static int choose_kslices(int tiles, int kb_total, int num_sms, int max_s) {
 using namespace tcg;
 
 // Sum the per-slice partials in slot order: W2/b2/b1 gradients and LL sums.
+// nb1 = H: the partials also hold db1 (unfused head); nb1 = 0: db1 comes from K5.
 __global__ void head_reduce_kernel(const float* __restrict__ part_w, const double* __restrict__ part_l, int nslots,
-                                   int J, int H, int C, float* __restrict__ gW2, float* __restrict__ gb2,
+                                   int J, int H, int C, int nb1, float* __restrict__ gW2, float* __restrict__ gb2,
                                    float* __restrict__ gb1, double* __restrict__ la, double* __restrict__ lb) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int CH = C * H;
-    const int per = CH + C + H;
+    const int per = CH + C + nb1;
     if (t < (int64_t)J * per) {
         const int j = (int)(t / per), e = (int)(t % per);
         float s = 0.0f;
@@ -702,17 +519,28 @@ smc_status tc_alloc(smc_ctx* c) {
     if (cudaMalloc(&c->H1, (size_t)chunk * ldh_of(c) * 2) != cudaSuccess) return SMC_ENOMEM;
     if (cudaMalloc(&c->dZT, (size_t)JH * chunk * 2) != cudaSuccess) return SMC_ENOMEM;
     const int64_t per = (int64_t)c->n_out * H + c->n_out + H;
+    const char* env = getenv("SMC_FUSED_HEAD");
+    c->fused = !(env != nullptr && env[0] == '0');
     c->head_slices_cap = (c->N + 1023) / 1024 + 2 * (c->N / chunk + 2);
+    if (c->fused) {
+        // partial slots of the fused kernel, summed over the chunks of a full pass
+        int64_t need = 0;
+        for (int64_t g0 = 0; g0 < c->N; g0 += chunk) need += fused_slots(c, std::min(chunk, c->N - g0));
+        c->head_slices_cap = std::max(c->head_slices_cap, need);
+        if (cudaMalloc(&c->fimg, (size_t)fused_image_bytes(c)) != cudaSuccess) return SMC_ENOMEM;
+    }
     if (cudaMalloc(&c->head_part, (size_t)c->head_slices_cap * c->J * per * 4) != cudaSuccess) return SMC_ENOMEM;
     if (cudaMalloc(&c->head_ll, (size_t)c->head_slices_cap * c->J * 2 * 8) != cudaSuccess) return SMC_ENOMEM;
-    c->gemm_part_cap = (int64_t)8 * JH * rup(c->in_feat, 4);
+    c->gemm_part_cap = (int64_t)8 * JH * rup(c->in_feat + 1, 4);
     if (cudaMalloc(&c->gemm_part, (size_t)c->gemm_part_cap * 4) != cudaSuccess) return SMC_ENOMEM;
     return SMC_OK;
 }
 
 void tc_free(smc_ctx* c) {
     cudaFree(c->H1); cudaFree(c->dZT); cudaFree(c->head_part); cudaFree(c->head_ll); cudaFree(c->gemm_part);
+    cudaFree(c->fimg);
     c->H1 = nullptr; c->dZT = nullptr; c->head_part = nullptr; c->head_ll = nullptr; c->gemm_part = nullptr;
+    c->fimg = nullptr;
 }
 
 // K1 on rows [0, rows) of a BF16 row-major input x (pitch = in_feat) into c->H1.
@@ -744,61 +572,91 @@ static cudaError_t launch_head(smc_ctx* c, int H, int C, int mc, int64_t g0, int
     return e;
 }
 
+// K5: dW1 (J*H x Din) = dZ1^T X over the chunk's rows (K = mc); with_b1 adds the
+// ones row of the transposed input as column Din, which yields db1 = sum dZ1.
+static cudaError_t launch_wgrad(smc_ctx* c, int64_t g0, int64_t mc, bool with_b1) {
+    const Layer& L0 = c->layers[0];
+    const int64_t JH = (int64_t)c->J * L0.out_feat(), Din = c->in_feat;
+    const int64_t ncol = with_b1 ? Din + 1 : Din;
+    GemmArgs g{};
+    g.M = (int)JH; g.N = (int)ncol; g.K = (int)mc;
+    g.epi = EPI_F32;
+    g.err = c->err_dev;
+    plan(g, 400, 1, 2);
+    const int ks = choose_kslices(g.tiles_m * g.tiles_n, g.kb_total, c->num_sms, 8);
+    const int64_t ldp = rup(ncol, 4);
+    const int64_t slice = JH * ldp;
+    const int use_ks = (ks > 1 && (int64_t)ks * slice <= c->gemm_part_cap) ? ks : 1;
+    plan(g, 400, use_ks, 2);
+    float* gW1 = c->grad + c->segs[L0.seg_w].off;
+    float* gb1 = with_b1 ? c->grad + c->segs[L0.seg_b].off : nullptr;
+    if (g.kslices > 1) {
+        g.out = c->gemm_part; g.ldo = ldp; g.slice_stride = slice; g.aug_col = -1;
+    } else {
+        g.out = gW1; g.ldo = Din; g.accumulate = g0 > 0;
+        g.aug_col = with_b1 ? (int)Din : -1;
+        g.aug_out = gb1;
+    }
+    fam_begin(c, F_WGRAD_GEMM);
+    cudaError_t e = launch_gemm<400, 200, 3, 2>(c->dZT, c->chunk, c->XTa + g0, c->Npad, g, c->stream, c->num_sms);
+    c->launches++;
+    if (e == cudaSuccess && g.kslices > 1) {
+        const int64_t n = JH * ncol;
+        SMC_LAUNCH(c, splitk_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+                          c->gemm_part, g.kslices, slice, JH, (int)ncol, ldp, (int)Din, gW1, gb1, g0 > 0));
+        e = cudaGetLastError();
+    }
+    fam_end(c, F_WGRAD_GEMM);
+    return e;
+}
+
 smc_status tc_eval(smc_ctx* c) {
     const Layer& L0 = c->layers[0];
     const Layer& L1 = c->layers[1];
     const int H = (int)L0.out_feat(), C = c->n_out;
-    const int64_t JH = (int64_t)c->J * H, Din = c->in_feat;
+    const int64_t Din = c->in_feat;
     const int64_t M = c->rows_a + c->rows_b;
     const int64_t ch = c->chunk;
     const int rows_per_slice = 4096;
     int slot = 0;
     cudaError_t e;
+    if (c->fused) {
+        fam_begin(c, F_HEAD);
+        e = launch_fused_images(c);
+        fam_end(c, F_HEAD);
+        if (e != cudaSuccess) return cuda_check(c, e, "particle images");
+    }
     for (int64_t g0 = 0; g0 < M; g0 += ch) {
         const int64_t mc = std::min<int64_t>(ch, M - g0);
-        // K1
-        e = tc_forward_layer1(c, c->Xb + g0 * Din, mc);
-        if (e != cudaSuccess) return cuda_check(c, e, "tcgen05 forward GEMM");
-        // K3
-        const int nsl = (int)((mc + rows_per_slice - 1) / rows_per_slice);
-        if (slot + nsl > c->head_slices_cap) return fail(c, SMC_EINVAL, "head partial buffer too small");
-        e = launch_head(c, H, C, (int)mc, g0, L0.act, L1, slot, nsl, rows_per_slice);
-        if (e != cudaSuccess) return cuda_check(c, e, "head kernel");
-        slot += nsl;
-        // K5: dW1 (JH x Din) = dZ1^T X, K = mc rows
-        GemmArgs g{};
-        g.M = (int)JH; g.N = (int)Din; g.K = (int)mc;
-        g.epi = EPI_F32;
-        g.err = c->err_dev;
-        plan(g, 400, 1, 2);
-        const int ks = choose_kslices(g.tiles_m * g.tiles_n, g.kb_total, c->num_sms, 8);
-        const int64_t ldp = rup(Din, 4);
-        const int64_t slice = JH * ldp;
-        int use_ks = (ks > 1 && (int64_t)ks * slice <= c->gemm_part_cap) ? ks : 1;
-        plan(g, 400, use_ks, 2);
-        float* gW1 = c->grad + c->segs[L0.seg_w].off;
-        if (g.kslices > 1) {
-            g.out = c->gemm_part; g.ldo = ldp; g.slice_stride = slice; g.aug_col = -1;
+        if (c->fused) {
+            // K1 + K3 in one kernel
+            if (slot + fused_slots(c, mc) > c->head_slices_cap) return fail(c, SMC_EINVAL, "head partial buffer too small");
+            int nsl = 0;
+            fam_begin(c, F_FUSED);
+            e = launch_fused_fwd_head(c, c->Xb + g0 * Din, g0, mc, slot, &nsl);
+            fam_end(c, F_FUSED);
+            if (e != cudaSuccess) return cuda_check(c, e, "fused forward GEMM + head");
+            slot += nsl;
         } else {
-            g.out = gW1; g.ldo = Din; g.accumulate = g0 > 0; g.aug_col = -1;
+            // K1
+            e = tc_forward_layer1(c, c->Xb + g0 * Din, mc);
+            if (e != cudaSuccess) return cuda_check(c, e, "tcgen05 forward GEMM");
+            // K3
+            const int nsl = (int)((mc + rows_per_slice - 1) / rows_per_slice);
+            if (slot + nsl > c->head_slices_cap) return fail(c, SMC_EINVAL, "head partial buffer too small");
+            e = launch_head(c, H, C, (int)mc, g0, L0.act, L1, slot, nsl, rows_per_slice);
+            if (e != cudaSuccess) return cuda_check(c, e, "head kernel");
+            slot += nsl;
         }
-        fam_begin(c, F_WGRAD_GEMM);
-        e = launch_gemm<400, 200, 3, 2>(c->dZT, ch, c->XTa + g0, c->Npad, g, c->stream, c->num_sms);
-        c->launches++;
-        if (e == cudaSuccess && g.kslices > 1) {
-            const int64_t n = JH * Din;
-            SMC_LAUNCH(c, splitk_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
-                              c->gemm_part, g.kslices, slice, JH, (int)Din, ldp, (int)Din, gW1, nullptr, g0 > 0));
-            e = cudaGetLastError();
-        }
-        fam_end(c, F_WGRAD_GEMM);
+        e = launch_wgrad(c, g0, mc, c->fused);
         if (e != cudaSuccess) return cuda_check(c, e, "tcgen05 weight-gradient GEMM");
     }
-    // W2 / b2 / b1 gradients and log-likelihood sums
-    const int per = C * H + C + H;
+    // W2 / b2 (/ b1) gradients and log-likelihood sums
+    const int nb1 = c->fused ? 0 : H;
+    const int per = C * H + C + nb1;
     fam_begin(c, F_REDUCE);
     SMC_LAUNCH(c, head_reduce_kernel<<<(unsigned)(((int64_t)c->J * per + 255) / 256), 256, 0, c->stream>>>(
-                      c->head_part, c->head_ll, slot, c->J, H, C, c->grad + c->segs[L1.seg_w].off,
+                      c->head_part, c->head_ll, slot, c->J, H, C, nb1, c->grad + c->segs[L1.seg_w].off,
                       c->grad + c->segs[L1.seg_b].off, c->grad + c->segs[L0.seg_b].off, c->la, c->lb));
     fam_end(c, F_REDUCE);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "head reduce");

@@ -425,3 +425,50 @@ def test_two_hidden_layer_config_parity_and_fd():
         assert np.median(fd_err) < 1e-2 and np.percentile(fd_err, 90) < 0.05
     finally:
         S.smc_destroy(ctx)
+
+
+def test_bf16_full_size_sampled_particles():
+    """The bench workload's shape (MLP 784-100-10 ReLU, J = 256 particles, all
+    60000 rows in one pass, the launch configuration the bench times): log
+    likelihood and whole gradient of sampled particles - both members of the
+    first and last particle pairs and some in between - against the FP64 oracle
+    evaluated one particle at a time."""
+    N, J = 60000, 256
+    X, y = _images(N, 17)
+    ctx, orc, _ = make_pair(MLP1, X, y, J, seed=17, precision=S.PREC_BF16)
+    try:
+        th0 = synthetic.particles(J, MLP1.n_params, 17, std=0.1)
+        S.smc_set_state(ctx, th0)
+        S.smc_set_schedule(ctx, S.make_schedule("fb", N, N, 10))      # |D_0| = N, c_i = 1
+        lp, g, la, lb = S.smc_eval(ctx, J, MLP1.n_params)
+        assert np.all(lb == 0.0)
+        for j in [0, 1, 2, 77, 128, 129, 254, 255]:
+            ll, gg = nn.loglik_grad(MLP1, th0[j], orc.X, orc.y, 1.0)
+            assert abs(la[j] - ll.sum()) <= 2e-2 * abs(ll.sum()), j
+            assert rel_err(g[j], gg) < 2e-2, j
+    finally:
+        S.smc_destroy(ctx)
+
+
+@pytest.mark.parametrize("J,N,chunk", [(8, 700, 0), (5, 1000, 256)])
+def test_bf16_fused_and_unfused_heads_agree(monkeypatch, J, N, chunk):
+    """The forward GEMM with the head in its epilogue against the separate
+    forward GEMM + head kernels on the same particles: same log-likelihoods and
+    gradients up to BF16 rounding of dZ1 in db1 and the summation order."""
+    spec = nn.Spec([("dense", 784, 100), ("dense", 100, 10)], (784,), nn.TANH)
+    X, y = _images(N, 19)
+    th0 = synthetic.particles(J, spec.n_params, 19, std=0.1)
+    out = {}
+    for fused in ("1", "0"):
+        monkeypatch.setenv("SMC_FUSED_HEAD", fused)
+        ctx, _, _ = make_pair(spec, X, y, J, seed=19, precision=S.PREC_BF16, chunk=chunk)
+        try:
+            S.smc_set_state(ctx, th0)
+            S.smc_set_schedule(ctx, S.make_schedule("linear", 256, 256, 10))
+            out[fused] = S.smc_eval(ctx, J, spec.n_params)
+        finally:
+            S.smc_destroy(ctx)
+    (lp1, g1, la1, lb1), (lp0, g0, la0, lb0) = out["1"], out["0"]
+    assert np.allclose(la1, la0, rtol=1e-5) and np.allclose(lb1, lb0, rtol=1e-5, atol=1e-6)
+    assert np.allclose(lp1, lp0, rtol=1e-5)
+    assert _per_particle_rel(g1, g0) < 2e-3
