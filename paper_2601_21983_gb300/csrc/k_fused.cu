@@ -6,8 +6,9 @@
 //   h = act(W1 x + b1),  z = W2 h + b2,  log p(y|x) = z_y - LSE(z),
 //   dl = c_i (e_y - softmax(z)),  dZ1 = (W2^T dl) * act'(h),
 //   dW2 += dl h^T,  db2 += dl.
-// dZ1 is written transposed [J*H][rows] in BF16 for the weight-gradient GEMM
-// (K5), which also yields db1 through the ones row of the transposed input.
+// dZ1 is written transposed [J*H][rows] in BF16 (one TMA box per 16 rows and
+// particle) for the weight-gradient GEMM (K5), which also yields db1 through the
+// ones row of the transposed input.
 //
 // Work unit: 128 rows x one particle pair.  The pair's first-layer rows are one
 // TMA box {64, HP, 2} of the [J][H][Din] weights (rows past H and particles past
@@ -79,7 +80,8 @@ struct FCfg {
     // per-particle image: W2 [16][HS] | W2^T [HP][DS] (BF16) | b1 [HP] | b2 [16] (FP32)
     static constexpr int W2S_ELEMS = 16 * HS;
     static constexpr int W2T_ELEMS = HP * DS;
-    static constexpr int IMG_BYTES = (W2S_ELEMS + W2T_ELEMS) * 2 + HP * 4 + 16 * 4;
+    static constexpr int IMG_RAW = (W2S_ELEMS + W2T_ELEMS) * 2 + HP * 4 + 16 * 4;
+    static constexpr int IMG_BYTES = (IMG_RAW + 255) / 256 * 256;   // keeps the staging tiles 256-byte aligned
     // per epilogue warp: H tile [32][HS] + dlogits [32][DS]; each 16-row half of the H
     // tile is reused as that m-tile's dZ1 staging [HP][16]
     static constexpr int WARP_BYTES = 32 * HS * 2 + 32 * DS * 2;
@@ -90,7 +92,8 @@ struct FCfg {
     static constexpr int SMEM = FIXED + STAGES * STAGE_BYTES;
     static_assert(N <= 256 && N % 16 == 0, "MMA N");
     static_assert(ACC_COLS + N <= 512, "TMEM columns");
-    static_assert(IMG_BYTES % 16 == 0 && WARP_BYTES % 16 == 0 && STAGE_BYTES % 1024 == 0, "alignment");
+    static_assert(WARP_BYTES % 256 == 0 && (16 * HS * 2) % 256 == 0 && STAGE_BYTES % 1024 == 0,
+                  "dZ1 staging tiles on 256-byte boundaries (32-byte swizzle atoms)");
     static_assert(SMEM <= SMEM_LIMIT, "shared memory");
 };
 
@@ -106,8 +109,6 @@ struct FusedArgs {
     float ca, cb;
     const int32_t* Y;
     const uint8_t* img;     // [J][IMG_BYTES] particle images
-    __nv_bfloat16* dZT;     // [J*H][ldz]
-    int64_t ldz;
     float* part_w;          // [slot][J][C*H + C]
     double* part_l;         // [slot][J][2]
     int slot_base, nseg;
@@ -139,7 +140,7 @@ __device__ __forceinline__ void raise_abort(const FusedArgs& a, volatile int* ab
 template <int KT, int ACT>
 __global__ void __launch_bounds__(THREADS, 1)
 fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                      const FusedArgs a) {
+                      const __grid_constant__ CUtensorMap tmZ, const FusedArgs a) {
     using F = FCfg<KT>;
     constexpr int HP = F::HP, HS = F::HS, NT2 = 2 * KT, STAGES = F::STAGES;
     extern __shared__ uint8_t smem_raw[];
@@ -307,6 +308,9 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                 const int tile0 = tm * BM + wq * 32;       // first row of this warp (chunk-relative)
                 const bool work = active && tile0 < a.M;
                 if (work) {
+                    // the previous unit's dZ1 stores have read the staging tiles this overwrites
+                    if (lane == 0) bulk_wait_read0();
+                    __syncwarp();
                     // ---- 1. accumulator -> bias + activation -> BF16 H tile (row = lane)
                     const uint32_t tb = tbase + (uint32_t)acc * ACC_COLS + (uint32_t)(grp * HP) +
                                         ((uint32_t)(wq * 32) << 16);
@@ -465,25 +469,13 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                         stsm_x4_t(Zm + hid * 16 + hsw * 8, zp[0], zp[1], zp[2], zp[3]);
                     }
                     __syncwarp();
-                    // dZ1 -> HBM transposed: 16 hidden rows x 16 samples (32 bytes each) per instruction
-                    {
-                        const int h = lane & 1;
-                        const int m = r0 + 8 * h;
-                        const bool fullrow = m + 8 <= a.M;
-                        for (int p0 = 0; p0 < a.H; p0 += 16) {
-                            const int hid = p0 + (lane >> 1);
-                            if (hid < a.H && m < a.M) {
-                                const int hsw = h ^ ((hid >> 2) & 1);
-                                const uint4 v = *reinterpret_cast<const uint4*>(Zm + hid * 16 + hsw * 8);
-                                __nv_bfloat16* dst = a.dZT + ((int64_t)j * a.H + hid) * a.ldz + m;
-                                if (fullrow) {
-                                    *reinterpret_cast<uint4*>(dst) = v;
-                                } else {
-                                    const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
-                                    for (int i = 0; i < 8 && m + i < a.M; ++i) dst[i] = e[i];
-                                }
-                            }
-                        }
+                    // dZ1 -> HBM transposed: one TMA box {16 samples, HP hidden rows} of
+                    // particle j; rows past H and samples past the chunk are not written
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_3d(&tmZ, Zm, r0, 0, j);
+                        bulk_commit();
                     }
                     __syncwarp();
                 }
@@ -540,6 +532,8 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
             ++segk;
         }
         if (!ok) raise_abort(a, abort_flag, ERR_EPILOGUE);
+        if (lane == 0) bulk_wait_all();   // dZ1 stores complete before the CTA exits
+        __syncwarp();
     }
     tc_fence_before();
     __syncthreads();
@@ -598,7 +592,8 @@ static int nseg_of(int64_t tiles_m, int64_t npairs, int G) {
 static int grid_of(const smc_ctx* c, int64_t T) { return (int)std::max<int64_t>(1, std::min<int64_t>(T, c->num_sms)); }
 
 template <int KT, int ACT>
-static cudaError_t launch_t(smc_ctx* c, const FusedArgs& a, const CUtensorMap& ta, const CUtensorMap& tb, int G) {
+static cudaError_t launch_t(smc_ctx* c, const FusedArgs& a, const CUtensorMap& ta, const CUtensorMap& tb,
+                            const CUtensorMap& tz, int G) {
     using F = FCfg<KT>;
     auto kern = fused_fwd_head_kernel<KT, ACT>;
     static bool attr_set = false;
@@ -607,16 +602,16 @@ static cudaError_t launch_t(smc_ctx* c, const FusedArgs& a, const CUtensorMap& t
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    SMC_LAUNCH(c, kern<<<G, THREADS, F::SMEM, c->stream>>>(ta, tb, a));
+    SMC_LAUNCH(c, kern<<<G, THREADS, F::SMEM, c->stream>>>(ta, tb, tz, a));
     return cudaGetLastError();
 }
 
 template <int KT>
 static cudaError_t launch_k(smc_ctx* c, int act, const FusedArgs& a, const CUtensorMap& ta, const CUtensorMap& tb,
-                            int G) {
-    if (act == SMC_ACT_RELU) return launch_t<KT, SMC_ACT_RELU>(c, a, ta, tb, G);
-    if (act == SMC_ACT_TANH) return launch_t<KT, SMC_ACT_TANH>(c, a, ta, tb, G);
-    return launch_t<KT, SMC_ACT_IDENTITY>(c, a, ta, tb, G);
+                            const CUtensorMap& tz, int G) {
+    if (act == SMC_ACT_RELU) return launch_t<KT, SMC_ACT_RELU>(c, a, ta, tb, tz, G);
+    if (act == SMC_ACT_TANH) return launch_t<KT, SMC_ACT_TANH>(c, a, ta, tb, tz, G);
+    return launch_t<KT, SMC_ACT_IDENTITY>(c, a, ta, tb, tz, G);
 }
 
 }  // namespace fz
@@ -661,8 +656,6 @@ cudaError_t launch_fused_fwd_head(smc_ctx* c, const __nv_bfloat16* x, int64_t g0
     a.cb = (float)c->coef_b;
     a.Y = c->Y;
     a.img = c->fimg;
-    a.dZT = c->dZT;
-    a.ldz = c->chunk;
     a.part_w = c->head_part;
     a.part_l = c->head_ll;
     a.slot_base = slot_base;
@@ -670,14 +663,19 @@ cudaError_t launch_fused_fwd_head(smc_ctx* c, const __nv_bfloat16* x, int64_t g0
     a.nseg = nseg_of(a.tiles_m, a.npairs, G);
     a.err = c->err_dev;
     *nslots = 4 * a.nseg;
-    CUtensorMap ta, tb;
+    CUtensorMap ta, tb, tz;
     const uint64_t din = (uint64_t)c->in_feat;
     if (!make_tmap(&ta, x, din, (uint64_t)mc, din * 2, BM)) return cudaErrorInvalidValue;
     if (!make_tmap_3d(&tb, c->shadow, din, (uint64_t)H, (uint64_t)c->J, din * 2, din * 2 * (uint64_t)H, HP, 2))
         return cudaErrorInvalidValue;
-    if (kt == 7) return launch_k<7>(c, L0.act, a, ta, tb, G);
-    if (kt == 3) return launch_k<3>(c, L0.act, a, ta, tb, G);
-    return launch_k<8>(c, L0.act, a, ta, tb, G);
+    // dZ1^T [J][H][ldz]: box {16 samples, HP hidden rows} per m-tile
+    const uint64_t ldz = (uint64_t)c->chunk;
+    if (!make_store_tmap_3d_sw32(&tz, c->dZT, (uint64_t)mc, (uint64_t)H, (uint64_t)c->J, ldz * 2, ldz * 2 * H, 16,
+                                 HP))
+        return cudaErrorInvalidValue;
+    if (kt == 7) return launch_k<7>(c, L0.act, a, ta, tb, tz, G);
+    if (kt == 3) return launch_k<3>(c, L0.act, a, ta, tb, tz, G);
+    return launch_k<8>(c, L0.act, a, ta, tb, tz, G);
 }
 
 }  // namespace smc

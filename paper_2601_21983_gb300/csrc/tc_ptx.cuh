@@ -44,18 +44,38 @@ static __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false on timeout or when another role raised the abort flag.
-static __device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
-    if (mbar_try(b, parity)) return true;
+// try_wait that may suspend the thread in hardware for up to `ns` nanoseconds
+// (it resumes as soon as the phase completes), so a waiting role does not take
+// issue slots from the warps sharing its scheduler.
+static __device__ __forceinline__ bool mbar_try_suspend(uint64_t* b, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+constexpr uint32_t kSuspendNs = 100000;   // 0.1 ms per suspended try
+
+// Bounded wait, slow path: false on timeout or when another role raised the abort flag.
+static __device__ __noinline__ bool mbar_wait_slow(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
     const uint64_t t0 = gtimer();
     for (uint32_t it = 1; it < (1u << 26); ++it) {
-        if (mbar_try(b, parity)) return true;
-        if ((it & 127) == 0) {
+        if (mbar_try_suspend(b, parity, kSuspendNs)) return true;
+        if ((it & 7) == 0) {
             if (abort_flag != nullptr && *abort_flag) return false;
             if (gtimer() - t0 > kTimeoutNs) return false;
         }
     }
     return false;
+}
+// Bounded wait: false on timeout or when another role raised the abort flag.
+static __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_try(b, parity)) return true;
+    return mbar_wait_slow(b, parity, abort_flag);
 }
 
 static __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
@@ -99,6 +119,14 @@ static __device__ __forceinline__ void tma_store_2d(const CUtensorMap* tm, const
                  ::"l"((uint64_t)tm), "r"(x), "r"(y), "r"(su32(src))
                  : "memory");
 }
+// TMA store of a 3-D box from shared memory (bulk async-group); coordinates past
+// the tensor's extent are not written.
+static __device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, const void* src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
+                 ::"l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(su32(src))
+                 : "memory");
+}
+static __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 static __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 static __device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 static __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }

@@ -72,5 +72,22 @@ static inline bool make_tmap_3d(CUtensorMap* m, const void* base, uint64_t d0, u
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 3-D BF16 tensor [d2][d1][d0] for TMA stores: box {box0, box1, 1} with 32-byte
+// swizzle (box0 * 2 = 32 bytes: the two 16-byte halves of row r swap when bit 2
+// of r is set); coordinates past d0 or d1 are not written.
+static inline bool make_store_tmap_3d_sw32(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64_t d2,
+                                           uint64_t p1, uint64_t p2, uint32_t box0, uint32_t box1) {
+    auto enc = encode_fn();
+    if (!enc) return false;
+    if (((uintptr_t)base & 15) || (p1 & 15) || (p2 & 15) || box0 * 2 != 32) return false;
+    cuuint64_t dims[3] = {d0, d1, d2};
+    cuuint64_t strides[2] = {p1, p2};
+    cuuint32_t box[3] = {box0, box1, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace tcg
 }  // namespace smc
