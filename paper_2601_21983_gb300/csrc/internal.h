@@ -141,6 +141,7 @@ struct smc_ctx {
     int64_t head_slices_cap = 0;
     uint8_t* fimg = nullptr;         // fused kernel: per-particle W2 / b1 / b2 images
     bool fused = true;               // first-layer GEMM and head in one kernel
+    bool pair_gemm = true;           // weight-gradient GEMM on CTA pairs (cta_group::2)
     float* gemm_part = nullptr;      // split-K partials
     int64_t gemm_part_cap = 0;
 

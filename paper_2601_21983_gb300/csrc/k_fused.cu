@@ -62,7 +62,7 @@ using mm::unpack2;
 
 constexpr int BM = 128;
 constexpr int BK = 64;
-constexpr int DS = 24;                      // dlogits tile / W2^T row stride (elements)
+constexpr int DS = 24;                      // dlogits tile row stride (elements)
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t ACC_COLS = 256;          // TMEM columns between the two accumulators
@@ -77,10 +77,11 @@ struct FCfg {
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = N * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-    // per-particle image: W2 [16][HS] | W2^T [HP][DS] (BF16) | b1 [HP] | b2 [16] (FP32)
-    static constexpr int W2S_ELEMS = 16 * HS;
-    static constexpr int W2T_ELEMS = HP * DS;
-    static constexpr int IMG_RAW = (W2S_ELEMS + W2T_ELEMS) * 2 + HP * 4 + 16 * 4;
+    // per-particle image, W2 in mma.sync B-fragment order (one 16-byte load per lane
+    // gives two fragments): logits fragments [KT][32 lanes] | dH fragments
+    // [KT][32 lanes] (BF16) | b1 [HP] | b2 [16] (FP32)
+    static constexpr int FRAG_BYTES = KT * 32 * 16;
+    static constexpr int IMG_RAW = 2 * FRAG_BYTES + HP * 4 + 16 * 4;
     static constexpr int IMG_BYTES = (IMG_RAW + 255) / 256 * 256;   // keeps the staging tiles 256-byte aligned
     // per epilogue warp: H tile [32][HS] + dlogits [32][DS]; each 16-row half of the H
     // tile is reused as that m-tile's dZ1 staging [HP][16]
@@ -130,6 +131,19 @@ __device__ __forceinline__ float act_bwd(float d, float h) {
     if (ACT == SMC_ACT_TANH) return d * (1.0f - h * h);
     if (ACT == SMC_ACT_RELU) return h > 0.0f ? d : 0.0f;
     return d;
+}
+
+// dZ1 for two adjacent hidden units as packed BF16: (d0, d1) * act'(h) with h the
+// packed BF16 activations.  ReLU keeps d where h > 0 through a bf16x2 compare
+// mask, bit-identical to selecting in FP32 and rounding.
+template <int ACT>
+__device__ __forceinline__ uint32_t act_bwd2(float d0, float d1, uint32_t h) {
+    if (ACT == SMC_ACT_RELU) {
+        const __nv_bfloat162 hv = *reinterpret_cast<const __nv_bfloat162*>(&h);
+        return pack2(d0, d1) & __hgt2_mask(hv, __float2bfloat162_rn(0.0f));
+    }
+    const float2 hf = unpack2(h);
+    return pack2(act_bwd<ACT>(d0, hf.x), act_bwd<ACT>(d1, hf.y));
 }
 
 __device__ __forceinline__ void raise_abort(const FusedArgs& a, volatile int* abort_flag, int code) {
@@ -257,9 +271,9 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
         const int wq = warp & 3;            // TMEM lane quarter: rows 32 wq .. 32 wq + 31 of the unit
         const int g = lane >> 2, q4 = lane & 3;
         uint8_t* myimg = imgs + grp * F::IMG_BYTES;
-        const __nv_bfloat16* W2s = reinterpret_cast<const __nv_bfloat16*>(myimg);   // [16][HS]
-        const __nv_bfloat16* W2Ts = W2s + F::W2S_ELEMS;                               // [HP][DS]
-        const float* b1s = reinterpret_cast<const float*>(W2Ts + F::W2T_ELEMS);       // [HP]
+        const uint4* W2F = reinterpret_cast<const uint4*>(myimg);                     // logits B fragments
+        const uint4* W2TF = W2F + KT * 32;                                            // dH B fragments
+        const float* b1s = reinterpret_cast<const float*>(W2TF + KT * 32);            // [HP]
         const float* b2s = b1s + HP;                                                  // [16]
         __nv_bfloat16* Hs = reinterpret_cast<__nv_bfloat16*>(wbase + ew * F::WARP_BYTES);   // [32][HS]
         __nv_bfloat16* Dl = Hs + 32 * HS;                                                    // [32][DS]
@@ -299,6 +313,9 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
             __syncwarp();
             if (lane == 0) mbar_arrive(img_full + grp);
             if (!mbar_wait(img_full + grp, (uint32_t)(segk & 1), abort_flag)) { ok = false; break; }
+            float b2r[4];     // b2 of this thread's logit columns
+#pragma unroll
+            for (int e = 0; e < 4; ++e) b2r[e] = b2s[cls[e]];
 
             int lo, hi;
             m_range(p, lo, hi);
@@ -367,18 +384,15 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                         const int m = r0 + g + 8 * half;
                         ylab[half] = (m < a.M) ? a.Y[a.g0 + m] : -1;
                     }
-                    // logits = H W2^T
+                    // logits = H W2^T (even and odd k-tiles in separate accumulators)
                     uint32_t af[KT][4];
-                    float cz[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+                    float cz[2][2][4] = {};
 #pragma unroll
                     for (int kt = 0; kt < KT; ++kt) {
                         ldsm_x4(af[kt], Hm + (lane & 15) * HS + 16 * kt + (lane >> 4) * 8);
-#pragma unroll
-                        for (int nt = 0; nt < 2; ++nt) {
-                            const __nv_bfloat16* w = W2s + (8 * nt + g) * HS + 16 * kt + 2 * q4;
-                            mma16816(cz[nt], af[kt], *reinterpret_cast<const uint32_t*>(w),
-                                     *reinterpret_cast<const uint32_t*>(w + 8));
-                        }
+                        const uint4 bf = W2F[kt * 32 + lane];
+                        mma16816(cz[kt & 1][0], af[kt], bf.x, bf.y);
+                        mma16816(cz[kt & 1][1], af[kt], bf.z, bf.w);
                     }
                     // log-softmax, log-likelihood, dlogits (rows g and g+8)
                     float dl[2][4];
@@ -387,10 +401,10 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                         const int m = r0 + g + 8 * half;
                         const bool valid = m < a.M;
                         float z[4];
-                        z[0] = cz[0][2 * half] + b2s[cls[0]];
-                        z[1] = cz[0][2 * half + 1] + b2s[cls[1]];
-                        z[2] = cz[1][2 * half] + b2s[cls[2]];
-                        z[3] = cz[1][2 * half + 1] + b2s[cls[3]];
+                        z[0] = (cz[0][0][2 * half] + cz[1][0][2 * half]) + b2r[0];
+                        z[1] = (cz[0][0][2 * half + 1] + cz[1][0][2 * half + 1]) + b2r[1];
+                        z[2] = (cz[0][1][2 * half] + cz[1][1][2 * half]) + b2r[2];
+                        z[3] = (cz[0][1][2 * half + 1] + cz[1][1][2 * half + 1]) + b2r[3];
                         float mx = -INFINITY;
 #pragma unroll
                         for (int e = 0; e < 4; ++e)
@@ -450,17 +464,16 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
 #pragma unroll
                     for (int n2 = 0; n2 < NT2; n2 += 2) {
                         uint32_t zp[4];
+                        const uint4 bt = W2TF[(n2 >> 1) * 32 + lane];
 #pragma unroll
                         for (int u = 0; u < 2; ++u) {
                             const int n = n2 + u;
-                            const __nv_bfloat16* w = W2Ts + (8 * n + g) * DS + 2 * q4;
                             float d[4] = {0.f, 0.f, 0.f, 0.f};
-                            mma16816(d, adl, *reinterpret_cast<const uint32_t*>(w),
-                                     *reinterpret_cast<const uint32_t*>(w + 8));
-                            const float2 hA = unpack2((n & 1) ? af[n >> 1][2] : af[n >> 1][0]);   // row g
-                            const float2 hB = unpack2((n & 1) ? af[n >> 1][3] : af[n >> 1][1]);   // row g+8
-                            zp[2 * u] = pack2(act_bwd<ACT>(d[0], hA.x), act_bwd<ACT>(d[1], hA.y));
-                            zp[2 * u + 1] = pack2(act_bwd<ACT>(d[2], hB.x), act_bwd<ACT>(d[3], hB.y));
+                            mma16816(d, adl, u ? bt.z : bt.x, u ? bt.w : bt.y);
+                            const uint32_t hA = (n & 1) ? af[n >> 1][2] : af[n >> 1][0];   // row g
+                            const uint32_t hB = (n & 1) ? af[n >> 1][3] : af[n >> 1][1];   // row g+8
+                            zp[2 * u] = act_bwd2<ACT>(d[0], d[1], hA);
+                            zp[2 * u + 1] = act_bwd2<ACT>(d[2], d[3], hB);
                         }
                         // matrix mi: hidden block n2 + mi/2, sample half mi%2; row i of it = hidden unit
                         const int mi = lane >> 3, i = lane & 7;
@@ -543,26 +556,32 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
     }
 }
 
-// Per-particle images: W2 and W2^T in BF16 with zero padding, b1 and b2 in FP32.
+// Per-particle images: W2 in mma.sync B-fragment order (BF16, zero padded), b1 and
+// b2 in FP32.  Lane (g, q4) of the logits product H . W2^T over hidden k-tile kt
+// needs W2[c][16 kt + 2 q4 + {0,1}] and W2[c][16 kt + 8 + 2 q4 + {0,1}] for classes
+// c = g and 8 + g; of dH = dl . W2 over hidden tile n it needs W2[2 q4 + {0,1}][8 n + g]
+// and W2[8 + 2 q4 + {0,1}][8 n + g].
 template <int KT>
 __global__ void fused_image_kernel(const float* __restrict__ W2, const float* __restrict__ b2,
                                    const float* __restrict__ b1, int H, int C, uint8_t* __restrict__ img) {
     using F = FCfg<KT>;
-    constexpr int HP = F::HP, HS = F::HS;
+    constexpr int HP = F::HP;
     const int j = blockIdx.x;
     uint8_t* base = img + (int64_t)j * F::IMG_BYTES;
-    __nv_bfloat16* W2s = reinterpret_cast<__nv_bfloat16*>(base);
-    __nv_bfloat16* W2Ts = W2s + F::W2S_ELEMS;
-    float* b1s = reinterpret_cast<float*>(W2Ts + F::W2T_ELEMS);
+    uint4* W2F = reinterpret_cast<uint4*>(base);
+    uint4* W2TF = W2F + KT * 32;
+    float* b1s = reinterpret_cast<float*>(W2TF + KT * 32);
     float* b2s = b1s + HP;
     const float* W2j = W2 + (int64_t)j * C * H;
-    for (int i = threadIdx.x; i < F::W2S_ELEMS; i += blockDim.x) {
-        const int c = i / HS, k = i % HS;
-        W2s[i] = __float2bfloat16_rn((c < C && k < H) ? W2j[c * H + k] : 0.0f);
-    }
-    for (int i = threadIdx.x; i < F::W2T_ELEMS; i += blockDim.x) {
-        const int k = i / DS, c = i % DS;
-        W2Ts[i] = __float2bfloat16_rn((c < C && k < H) ? W2j[c * H + k] : 0.0f);
+    auto w = [&](int c, int k) { return (c < C && k < H) ? W2j[c * H + k] : 0.0f; };
+    for (int i = threadIdx.x; i < KT * 32; i += blockDim.x) {
+        const int kt = i / 32, lane = i % 32, g = lane >> 2, q4 = lane & 3;
+        const int k0 = 16 * kt + 2 * q4;
+        W2F[i] = make_uint4(pack2(w(g, k0), w(g, k0 + 1)), pack2(w(g, k0 + 8), w(g, k0 + 9)),
+                            pack2(w(8 + g, k0), w(8 + g, k0 + 1)), pack2(w(8 + g, k0 + 8), w(8 + g, k0 + 9)));
+        const int n0 = 8 * (2 * kt) + g, n1 = n0 + 8, c0 = 2 * q4;
+        W2TF[i] = make_uint4(pack2(w(c0, n0), w(c0 + 1, n0)), pack2(w(c0 + 8, n0), w(c0 + 9, n0)),
+                             pack2(w(c0, n1), w(c0 + 1, n1)), pack2(w(c0 + 8, n1), w(c0 + 9, n1)));
     }
     for (int i = threadIdx.x; i < HP; i += blockDim.x) b1s[i] = (i < H) ? b1[(int64_t)j * H + i] : 0.0f;
     for (int i = threadIdx.x; i < 16; i += blockDim.x) b2s[i] = (i < C) ? b2[(int64_t)j * C + i] : 0.0f;

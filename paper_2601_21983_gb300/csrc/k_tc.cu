@@ -351,6 +351,192 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
 }
 
+// CTA-pair GEMM with FP32 output (EPI_F32): the two CTAs of a cluster compute a
+// 256 x 2 NHALF tile with tcgen05.mma.cta_group::2 (M = 256).  CTA r stages the
+// A rows of m-tile 2 q + r and B rows [tn 2 NHALF + r NHALF, + NHALF), so each SM
+// holds half of the B tile: per K step an SM reads its A tile and NHALF B rows,
+// which balances shared-memory traffic against the tensor rate.  The even CTA
+// issues the MMAs: per 16-wide K step one N = 2 N1 instruction (B rows [0, N1) of
+// each CTA) and one N = 2 N2 instruction (rows [N1, NHALF)); both CTAs' TMA loads
+// complete on the even CTA's stage barrier, MMA completion is multicast to both
+// CTAs' stage and accumulator barriers, and each CTA's epilogue drains its own
+// TMEM rows and releases the accumulator on the even CTA's barrier.
+template <int NHALF, int STAGES>
+struct PairCfg {
+    static constexpr int N1 = NHALF > 128 ? 128 : NHALF;
+    static constexpr int N2 = NHALF - N1;
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = NHALF * BK * 2;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr uint32_t TCOLS = 512;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+    static_assert(NHALF % 8 == 0 && N1 % 8 == 0 && N2 % 8 == 0, "B slices in whole 8-row atoms");
+    static_assert(2 * N1 <= 256 && 2 * N2 <= 256, "MMA N");
+    static_assert(2 * NHALF <= (int)TCOLS, "TMEM columns");
+    static_assert(STAGE_BYTES % 1024 == 0 && (N1 * 128) % 1024 == 0, "swizzle atoms");
+    static_assert(SMEM <= 232448, "shared memory");
+};
+
+// Tile column of TMEM accumulator column t (see PairCfg: the two MMAs interleave
+// the CTAs' B slices).
+template <int NHALF>
+__device__ __forceinline__ int pair_col(int t) {
+    constexpr int N1 = PairCfg<NHALF, 1>::N1, N2 = PairCfg<NHALF, 1>::N2;
+    if (t < N1) return t;
+    if (t < 2 * N1) return NHALF + (t - N1);
+    if (t < 2 * N1 + N2) return N1 + (t - 2 * N1);
+    return NHALF + N1 + (t - 2 * N1 - N2);
+}
+
+template <int NHALF, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs g) {
+    using C = PairCfg<NHALF, STAGES>;
+    const int rank = (int)cluster_rank();
+    const int cid = blockIdx.x / 2, ncl = gridDim.x / 2;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + STAGES * C::STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* tfull = empty + STAGES;
+    uint64_t* tempty = tfull + 1;
+    uint64_t* drain = tempty + 1;
+    uint32_t* tslot = (uint32_t*)(drain + 1);
+    volatile int* abort_flag = (volatile int*)(tslot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
+        mbar_init(tfull, 1);
+        mbar_init(tempty, 8);   // the four epilogue warps of both CTAs (used on the even CTA)
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) tmem_alloc_pair(tslot, C::TCOLS);
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();   // both CTAs' barriers exist before any remote signal
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------------------------ TMA producer (both CTAs)
+            int stage = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (int u = cid; u < g.num_units && ok; u += ncl) {
+                int tm, tn, ks;
+                decode(g, u, rank, tm, tn, ks);
+                const int kb0 = ks * g.kb_per_slice, kb1 = min(g.kb_total, kb0 + g.kb_per_slice);
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    if (!mbar_wait(empty + stage, ph ^ 1, abort_flag)) { ok = false; break; }
+                    if (rank == 0) mbar_expect_tx(full + stage, 2 * C::STAGE_BYTES);   // both CTAs' bytes
+                    const uint32_t fb = mapa_shared(full + stage, 0);
+                    uint8_t* sa = smem + stage * C::STAGE_BYTES;
+                    tma_load_2d_pair(sa, &tmA, kb * BK, tm * BM, fb);
+                    tma_load_2d_pair(sa + C::A_BYTES, &tmB, kb * BK, tn * 2 * NHALF + rank * NHALF, fb);
+                    if (++stage == STAGES) { stage = 0; ph ^= 1; }
+                }
+            }
+            if (!ok) {
+                raise_abort(g, abort_flag, ERR_PRODUCER);
+                // copies already issued land within microseconds; keep this CTA's
+                // shared memory alive well past that before leaving
+                const uint64_t t0 = gtimer();
+                while (gtimer() - t0 < 2000000ull) {
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) {
+            // ------------------------------------------------ MMA issuer (even CTA)
+            constexpr uint32_t ID1 = idesc_bf16(2 * BM, 2 * C::N1);
+            constexpr uint32_t ID2 = idesc_bf16(2 * BM, C::N2 > 0 ? 2 * C::N2 : 16);
+            int stage = 0;
+            uint32_t ph = 0, aph = 0;
+            bool ok = true;
+            for (int u = cid; u < g.num_units && ok; u += ncl) {
+                int tm, tn, ks;
+                decode(g, u, rank, tm, tn, ks);
+                const int kb0 = ks * g.kb_per_slice, kb1 = min(g.kb_total, kb0 + g.kb_per_slice);
+                if (!mbar_wait(tempty, aph ^ 1, abort_flag)) { ok = false; break; }
+                tc_fence_after();
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    if (!mbar_wait(full + stage, ph, abort_flag)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t sa = su32(smem + stage * C::STAGE_BYTES);
+                    const uint32_t sb = sa + C::A_BYTES;
+                    const int krem = g.K - kb * BK;
+                    const int nk = krem >= BK ? BK / 16 : (krem + 15) / 16;
+                    for (int k = 0; k < nk; ++k) {
+                        const uint64_t ad = sdesc(sa + k * 32);
+                        const uint32_t accum = (kb > kb0 || k > 0) ? 1u : 0u;
+                        umma_bf16_pair(tbase, ad, sdesc(sb + k * 32), ID1, accum);
+                        if (C::N2 > 0)
+                            umma_bf16_pair(tbase + 2 * C::N1, ad, sdesc(sb + C::N1 * 128 + k * 32), ID2, accum);
+                    }
+                    umma_commit_pair_mc(empty + stage, 0x3);   // frees the stage in both CTAs
+                    if (++stage == STAGES) { stage = 0; ph ^= 1; }
+                }
+                if (!ok) break;
+                umma_commit_pair_mc(tfull, 0x3);
+                aph ^= 1;
+            }
+            if (!ok) raise_abort(g, abort_flag, ERR_MMA);
+            umma_commit_pair_mc(drain, 0x1);
+            mbar_wait(drain, 0, nullptr);
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------- epilogue (warps 2..5, both CTAs)
+        const int wq = warp & 3;
+        const uint32_t tempty_even = mapa_shared(tempty, 0);
+        uint32_t aph = 0;
+        for (int u = cid; u < g.num_units; u += ncl) {
+            int tm, tn, ks;
+            decode(g, u, rank, tm, tn, ks);
+            if (!mbar_wait(tfull, aph, abort_flag)) {
+                raise_abort(g, abort_flag, ERR_EPILOGUE);
+                break;
+            }
+            tc_fence_after();
+            const int row = tm * BM + wq * 32 + lane;
+            const uint32_t tb = tbase + ((uint32_t)(wq * 32) << 16);
+#pragma unroll 1
+            for (int c0 = 0; c0 < 2 * NHALF; c0 += 32) {
+                uint32_t r[32];
+                const int n8 = min(4, (2 * NHALF - c0) / 8);
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (q < n8) {
+                        uint32_t* rq = r + 8 * q;
+                        TMEM_LD8(tb + (uint32_t)(c0 + 8 * q), rq);
+                    }
+                }
+                tmem_ld_wait();
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q < n8) epi_store(g, row, tn * 2 * NHALF + pair_col<NHALF>(c0 + 8 * q), 8, ks, r + 8 * q);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_remote(tempty_even);
+            aph ^= 1;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();   // the even CTA's MMAs into this CTA's TMEM and smem are complete
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(tbase, C::TCOLS);
+    }
+}
+
 // ------------------------------------------------------------- host side
 template <int BN, int BNBOX, int STAGES, int CS>
 static cudaError_t launch_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, GemmArgs g, cudaStream_t s,
@@ -393,6 +579,45 @@ static cudaError_t launch_gemm(const void* A, int64_t lda, const void* B, int64_
     const int clusters = std::max(1, std::min(g.num_units, max_clusters));
     cfg.gridDim = dim3((unsigned)(clusters * CS), 1, 1);
     cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ta, tb, tc, g);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+template <int NHALF, int STAGES>
+static cudaError_t launch_gemm_pair(const void* A, int64_t lda, const void* B, int64_t ldb, GemmArgs g,
+                                    cudaStream_t s, int num_sms) {
+    using C = PairCfg<NHALF, STAGES>;
+    CUtensorMap ta, tb;
+    if (g.cs != 2 || g.epi != EPI_F32) return cudaErrorInvalidValue;
+    if (!make_tmap(&ta, A, (uint64_t)g.K, (uint64_t)g.M, (uint64_t)lda * 2, BM)) return cudaErrorInvalidValue;
+    if (!make_tmap(&tb, B, (uint64_t)g.K, (uint64_t)g.N, (uint64_t)ldb * 2, NHALF)) return cudaErrorInvalidValue;
+    auto kern = gemm_pair_kernel<NHALF, STAGES>;
+    static int max_clusters = -1;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(192, 1, 1);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (max_clusters < 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e != cudaSuccess) return e;
+        cfg.gridDim = dim3((unsigned)(num_sms - num_sms % 2), 1, 1);
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            n = num_sms / 2;
+        }
+        max_clusters = std::min(n, num_sms / 2);
+    }
+    const int clusters = std::max(1, std::min(g.num_units, max_clusters));
+    cfg.gridDim = dim3((unsigned)(clusters * 2), 1, 1);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ta, tb, g);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -521,6 +746,8 @@ smc_status tc_alloc(smc_ctx* c) {
     const int64_t per = (int64_t)c->n_out * H + c->n_out + H;
     const char* env = getenv("SMC_FUSED_HEAD");
     c->fused = !(env != nullptr && env[0] == '0');
+    const char* envp = getenv("SMC_PAIR_GEMM");
+    c->pair_gemm = !(envp != nullptr && envp[0] == '0');
     c->head_slices_cap = (c->N + 1023) / 1024 + 2 * (c->N / chunk + 2);
     if (c->fused) {
         // partial slots of the fused kernel, summed over the chunks of a full pass
@@ -598,7 +825,9 @@ static cudaError_t launch_wgrad(smc_ctx* c, int64_t g0, int64_t mc, bool with_b1
         g.aug_out = gb1;
     }
     fam_begin(c, F_WGRAD_GEMM);
-    cudaError_t e = launch_gemm<400, 200, 3, 2>(c->dZT, c->chunk, c->XTa + g0, c->Npad, g, c->stream, c->num_sms);
+    cudaError_t e = c->pair_gemm
+                        ? launch_gemm_pair<200, 5>(c->dZT, c->chunk, c->XTa + g0, c->Npad, g, c->stream, c->num_sms)
+                        : launch_gemm<400, 200, 3, 2>(c->dZT, c->chunk, c->XTa + g0, c->Npad, g, c->stream, c->num_sms);
     c->launches++;
     if (e == cudaSuccess && g.kslices > 1) {
         const int64_t n = JH * ncol;
@@ -704,7 +933,7 @@ cudaError_t tc_gemm_public(const void* A, int64_t lda, const void* B, int64_t ld
     g.err = err_dev;
     if (N > 256) {
         plan(g, 400, 1, 2);
-        return launch_gemm<400, 200, 3, 2>(A, lda, B, ldb, g, s, num_sms);
+        return launch_gemm_pair<200, 5>(A, lda, B, ldb, g, s, num_sms);
     }
     plan(g, 256, 1, 2);
     return launch_gemm<256, 128, 4, 2>(A, lda, B, ldb, g, s, num_sms);
