@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import datetime
 import os
 import subprocess
 import sys
@@ -56,50 +57,63 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi samples during the timed region."""
+    """nvidia-smi samples (every 100 ms, host-timestamped) kept for the timed
+    region only: start() before the warm-up, mark(t0, t1) with the host times
+    around the timed loop, stop() after it."""
+
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, idx):
         self.proc = None
+        self.window = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(idx), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+                ["nvidia-smi", "-i", str(idx), "--query-gpu=timestamp,clocks.sm,clocks.max.sm,power.draw,"
                  "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
                  "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
+
     def stop(self):
         if self.proc is None:
             return None
+        time.sleep(0.15)          # let the sampler write the sample that closes the window
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             parts = [t.strip() for t in line.split(",")]
-            if len(parts) < 8:
+            if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[4:8]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
+        if not rows:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        t0, t1 = self.window if self.window else (rows[0][0], rows[-1][0])
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        note = "samples inside the timed region"
+        if not inside:       # a region shorter than the sampling period: the sample closest to it
+            inside = [min(rows, key=lambda r: abs(r[0] - 0.5 * (t0 + t1)))]
+            note = "timed region shorter than the 100 ms sampling period: nearest sample"
+        reasons = sorted({nm for r in inside for nm, v in zip(self.NAMES, r[4]) if v.lower().startswith("active")})
+        return {"sm_mhz": float(np.median([r[1] for r in inside])), "sm_max_mhz": float(max(r[2] for r in inside)),
+                "reasons": reasons, "samples": len(inside), "power_w": float(np.median([r[3] for r in inside])),
+                "note": note}
 
 
 def make_data(n, seed=0):
@@ -258,7 +272,7 @@ def run_tta(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--J", type=int, default=J_DEFAULT)
@@ -310,23 +324,27 @@ def main():
         evals[0] += st["grad_evals"] * st["rows"] * args.J
         return st
 
+    clocks = Clocks(local) if rank == 0 else None
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clocks = Clocks(local) if rank == 0 else None
     n0, _, _ = S.smc_get_counters(ctx)
     evals[0] = 0
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    h0 = time.time()
     ev0.record(stream)
     for _ in range(args.steps):
         one_step()
     ev1.record(stream)
     torch.cuda.synchronize()
+    h1 = time.time()
     ms = ev0.elapsed_time(ev1)
     n1, _, _ = S.smc_get_counters(ctx)
+    if clocks:
+        clocks.mark(h0, h1)
     clk = clocks.stop() if clocks else None
     my_evals = evals[0]
     t = torch.tensor([ms], dtype=torch.float64, device="cuda")

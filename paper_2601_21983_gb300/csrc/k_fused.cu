@@ -10,15 +10,20 @@
 // particle) for the weight-gradient GEMM (K5), which also yields db1 through the
 // ones row of the transposed input.
 //
-// Work unit: 128 rows x one particle pair.  The pair's first-layer rows are one
-// TMA box {64, HP, 2} of the [J][H][Din] weights (rows past H and particles past
-// J read as zeros), so the tcgen05.mma has N = 2 HP with particle 0 in TMEM
-// columns [0, HP) and particle 1 in [HP, 2 HP); HP = 16 KT keeps both blocks on
-// 16-column boundaries.  The accumulator is double-buffered in TMEM (columns
-// 0 and 256).
+// Work unit: 256 rows x one particle pair on a 2-CTA cluster.  CTA r of the pair
+// stages the 128 rows of m-tile 2 q + r and the first-layer rows of particle
+// 2 p + r (a TMA box {64, HP, 1} of the [J][H][Din] weights; rows past H and
+// particles past J read as zeros), and the even CTA issues tcgen05.mma.cta_group::2
+// with M = 256, N = 2 HP: the B operand is split between the CTAs, so each SM
+// reads its own A rows and one particle's W1 rows per K step, and every CTA's
+// TMEM receives its 128 rows with particle 0 in columns [0, HP) and particle 1 in
+// [HP, 2 HP); HP = 16 KT keeps both blocks on 16-column boundaries.  The
+// accumulator is double-buffered in TMEM (columns 0 and 256).
 //
-// Roles (320 threads, one CTA per SM): warp 0 issues TMA, warp 1 issues MMAs,
-// warps 2..9 run the head.  Epilogue warp w serves particle (w-2)/4 of the pair
+// Roles (320 threads per CTA, one CTA per SM): warp 0 issues TMA (both CTAs'
+// copies complete on the even CTA's stage barrier), warp 1 of the even CTA
+// issues the MMAs (completion multicast to both CTAs), warps 2..9 run the head
+// and release the accumulator on the even CTA's barrier.  Epilogue warp w serves particle (w-2)/4 of the pair
 // and TMEM lane quarter w%4 (32 rows): it moves its 32 x HP block from TMEM
 // through bias + activation into a BF16 tile in shared memory, releases the
 // accumulator, and then runs the head on mma.sync m16n8k16 fragments:
@@ -28,12 +33,12 @@
 // while the MMA warp already computes the next unit into the other buffer.
 //
 // Scheduling: the units, ordered pair-major, are split into one contiguous range
-// per CTA; a CTA visits the pairs of its range from last to first, each over
-// ascending rows, so all CTAs sweep the rows together and the input rows in use
-// at any time stay in L2.  dW2 / db2 and the log-likelihood sums accumulate in
-// registers over a pair's units and are written once per (pair segment, warp)
-// to fixed partial slots; the reduce kernel sums the slots in order, so the
-// result does not depend on timing.
+// per cluster; a cluster visits the pairs of its range from last to first, each
+// over ascending rows, so all clusters sweep the rows together and the input rows
+// in use at any time stay in L2.  dW2 / db2 and the log-likelihood sums
+// accumulate in registers over a pair's units and are written once per (pair
+// segment, CTA, warp) to fixed partial slots; the reduce kernel sums the slots in
+// order, so the result does not depend on timing.
 //
 // Every wait is a bounded mbarrier wait; on timeout the kernel raises the error
 // flag, drains its own copies and MMAs, frees TMEM and returns.  The epilogue
@@ -48,6 +53,7 @@
 #include "mma_ptx.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace smc {
 namespace fz {
@@ -75,7 +81,7 @@ struct FCfg {
     static constexpr int N = 2 * HP;        // MMA N: two particles
     static constexpr int HS = HP + 8;       // H tile row stride (elements)
     static constexpr int A_BYTES = BM * BK * 2;
-    static constexpr int B_BYTES = N * BK * 2;
+    static constexpr int B_BYTES = HP * BK * 2;     // this CTA's particle (half of the MMA's B)
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     // per-particle image, W2 in mma.sync B-fragment order (one 16-byte load per lane
     // gives two fragments): logits fragments [KT][32 lanes] | dH fragments
@@ -102,8 +108,10 @@ struct FusedArgs {
     int M;                  // rows of this chunk
     int K;                  // input features
     int J, H, C;
-    int tiles_m, npairs;
-    int64_t T;              // units = npairs * tiles_m
+    int tiles_m;            // 128-row m-tiles
+    int tiles_q;            // m-tile pairs (one per cluster unit)
+    int npairs;
+    int64_t T;              // units = npairs * tiles_q
     int kb_total;
     int64_t g0;             // global row of the chunk's first row
     int64_t rows_a;         // rows < rows_a carry coefficient ca, the rest cb
@@ -116,7 +124,7 @@ struct FusedArgs {
     int* err;
 };
 
-// CTA owning unit t when T units are split into G contiguous ranges
+// Cluster owning unit t when T units are split into G contiguous ranges
 // [floor(c T / G), floor((c+1) T / G)).
 __host__ __device__ inline int owner_of(int64_t t, int64_t T, int G) { return (int)(((t + 1) * G - 1) / T); }
 
@@ -159,6 +167,7 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
     constexpr int HP = F::HP, HS = F::HS, NT2 = 2 * KT, STAGES = F::STAGES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int rank = (int)cluster_rank();   // 0: the CTA that issues the MMAs
     uint8_t* imgs = smem + STAGES * F::STAGE_BYTES;
     uint8_t* wbase = imgs + 2 * F::IMG_BYTES;
     uint64_t* full = (uint64_t*)(wbase + EPI_WARPS * F::WARP_BYTES);
@@ -176,7 +185,7 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
         for (int s = 0; s < STAGES; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
         for (int b = 0; b < 2; ++b) {
             mbar_init(tfull + b, 1);
-            mbar_init(tempty + b, EPI_WARPS);
+            mbar_init(tempty + b, 2 * EPI_WARPS);   // both CTAs' epilogue warps (used on the even CTA)
             mbar_init(img_full + b, 4);
             mbar_init(img_free + b, 4);
         }
@@ -184,61 +193,66 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
         *abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == 1) tmem_alloc(tslot, 512);
+    if (warp == 1) tmem_alloc_pair(tslot, 512);
     tc_fence_before();
     __syncthreads();
+    cluster_sync();   // both CTAs' barriers exist before any remote signal
     tc_fence_after();
     const uint32_t tbase = *tslot;
 
-    // this CTA's units [t0, t1): pairs p_last down to p_first, rows ascending
-    const int G = gridDim.x, cta = blockIdx.x;
-    const int64_t t0 = (int64_t)cta * a.T / G, t1 = (int64_t)(cta + 1) * a.T / G;
-    const int p_first = (int)(t0 / a.tiles_m);
-    const int p_last = t1 > t0 ? (int)((t1 - 1) / a.tiles_m) : p_first - 1;
+    // this cluster's units [t0, t1): pairs p_last down to p_first, m-tile pairs ascending
+    const int G = gridDim.x / 2, cid = blockIdx.x / 2;
+    const int64_t t0 = (int64_t)cid * a.T / G, t1 = (int64_t)(cid + 1) * a.T / G;
+    const int p_first = (int)(t0 / a.tiles_q);
+    const int p_last = t1 > t0 ? (int)((t1 - 1) / a.tiles_q) : p_first - 1;
     auto m_range = [&](int p, int& lo, int& hi) {
-        lo = (p == p_first) ? (int)(t0 - (int64_t)p * a.tiles_m) : 0;
-        hi = (p == p_last) ? (int)(t1 - (int64_t)p * a.tiles_m) : a.tiles_m;
+        lo = (p == p_first) ? (int)(t0 - (int64_t)p * a.tiles_q) : 0;
+        hi = (p == p_last) ? (int)(t1 - (int64_t)p * a.tiles_q) : a.tiles_q;
     };
 
     if (warp == 0) {
         if (lane == 0) {
             // ---------------------------------------------------- TMA producer
-            int stage = 0, issued = 0;
+            int stage = 0;
             uint32_t ph = 0;
             bool ok = true;
             for (int p = p_last; p >= p_first && ok; --p) {
                 int lo, hi;
                 m_range(p, lo, hi);
-                for (int tm = lo; tm < hi && ok; ++tm) {
+                for (int tq = lo; tq < hi && ok; ++tq) {
+                    const int tm = 2 * tq + rank;
                     for (int kb = 0; kb < a.kb_total; ++kb) {
                         if (!mbar_wait(empty + stage, ph ^ 1, abort_flag)) { ok = false; break; }
-                        mbar_expect_tx(full + stage, F::STAGE_BYTES);
+                        if (rank == 0) mbar_expect_tx(full + stage, 2 * F::STAGE_BYTES);   // both CTAs' bytes
+                        const uint32_t fb = mapa_shared(full + stage, 0);
                         uint8_t* sa = smem + stage * F::STAGE_BYTES;
-                        tma_load_2d(sa, &tmA, kb * BK, tm * BM, full + stage);
-                        tma_load_3d(sa + F::A_BYTES, &tmB, kb * BK, 0, 2 * p, full + stage);
-                        ++issued;
+                        tma_load_2d_pair(sa, &tmA, kb * BK, tm * BM, fb);
+                        tma_load_3d_pair(sa + F::A_BYTES, &tmB, kb * BK, 0, 2 * p + rank, fb);
                         if (++stage == STAGES) { stage = 0; ph ^= 1; }
                     }
                 }
             }
             if (!ok) {
                 raise_abort(a, abort_flag, ERR_PRODUCER);
-                for (int f = max(0, issued - STAGES); f < issued; ++f)
-                    mbar_wait(full + (f % STAGES), (uint32_t)((f / STAGES) & 1), nullptr);
+                // copies already issued land within microseconds; keep this CTA's
+                // shared memory alive well past that before leaving
+                const uint64_t tw = gtimer();
+                while (gtimer() - tw < 2000000ull) {
+                }
             }
         }
         __syncwarp();
     } else if (warp == 1) {
-        if (lane == 0) {
-            // ---------------------------------------------------- MMA issuer
-            constexpr uint32_t ID = idesc_bf16(BM, F::N);
+        if (lane == 0 && rank == 0) {
+            // ---------------------------------------------------- MMA issuer (even CTA)
+            constexpr uint32_t ID = idesc_bf16(2 * BM, F::N);
             int stage = 0, acc = 0;
             uint32_t ph = 0, aph = 0;
             bool ok = true;
             for (int p = p_last; p >= p_first && ok; --p) {
                 int lo, hi;
                 m_range(p, lo, hi);
-                for (int tm = lo; tm < hi && ok; ++tm) {
+                for (int tq = lo; tq < hi && ok; ++tq) {
                     if (!mbar_wait(tempty + acc, aph ^ 1, abort_flag)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t dt = tbase + (uint32_t)acc * ACC_COLS;
@@ -250,17 +264,17 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                         const int krem = a.K - kb * BK;
                         const int nk = krem >= BK ? BK / 16 : (krem + 15) / 16;
                         for (int k = 0; k < nk; ++k)
-                            umma_bf16(dt, sdesc(sa + k * 32), sdesc(sb + k * 32), ID, (kb > 0 || k > 0) ? 1u : 0u);
-                        umma_commit(empty + stage);
+                            umma_bf16_pair(dt, sdesc(sa + k * 32), sdesc(sb + k * 32), ID, (kb > 0 || k > 0) ? 1u : 0u);
+                        umma_commit_pair_mc(empty + stage, 0x3);   // frees the stage in both CTAs
                         if (++stage == STAGES) { stage = 0; ph ^= 1; }
                     }
                     if (!ok) break;
-                    umma_commit(tfull + acc);
+                    umma_commit_pair_mc(tfull + acc, 0x3);
                     if (++acc == 2) { acc = 0; aph ^= 1; }
                 }
             }
             if (!ok) raise_abort(a, abort_flag, ERR_MMA);
-            umma_commit(drain);
+            umma_commit_pair_mc(drain, 0x1);
             mbar_wait(drain, 0, nullptr);
         }
         __syncwarp();
@@ -319,10 +333,21 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
 
             int lo, hi;
             m_range(p, lo, hi);
-            for (int tm = lo; tm < hi; ++tm) {
+            for (int tq = lo; tq < hi; ++tq) {
+                const int tm = 2 * tq + rank;
+                const int tile0 = tm * BM + wq * 32;       // first row of this warp (chunk-relative)
+                // class labels of this warp's rows (m-tile mt, row g + 8 half), fetched while
+                // the accumulator is still being computed
+                int ylab[2][2];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        const int m = tile0 + 16 * mt + g + 8 * half;
+                        ylab[mt][half] = (active && m < a.M) ? a.Y[a.g0 + m] : -1;
+                    }
                 if (!mbar_wait(tfull + acc, aph, abort_flag)) { ok = false; break; }
                 tc_fence_after();
-                const int tile0 = tm * BM + wq * 32;       // first row of this warp (chunk-relative)
                 const bool work = active && tile0 < a.M;
                 if (work) {
                     // the previous unit's dZ1 stores have read the staging tiles this overwrites
@@ -363,10 +388,10 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                         }
                     }
                 }
-                // the accumulator buffer is free for the MMA warp
+                // the accumulator buffer is free for the MMA warp (on the even CTA)
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(tempty + acc);
+                if (lane == 0) mbar_arrive_remote(mapa_shared(tempty + acc, 0));
                 if (++acc == 2) { acc = 0; aph ^= 1; }
                 if (!work) continue;
 
@@ -378,12 +403,6 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                     __nv_bfloat16* Hm = Hs + 16 * mt * HS;     // [16][HS]
                     __nv_bfloat16* Dm = Dl + 16 * mt * DS;     // [16][DS]
                     __nv_bfloat16* Zm = Hm;                    // [HP][16], 16-byte halves XOR-swizzled
-                    int ylab[2];
-#pragma unroll
-                    for (int half = 0; half < 2; ++half) {
-                        const int m = r0 + g + 8 * half;
-                        ylab[half] = (m < a.M) ? a.Y[a.g0 + m] : -1;
-                    }
                     // logits = H W2^T (even and odd k-tiles in separate accumulators)
                     uint32_t af[KT][4];
                     float cz[2][2][4] = {};
@@ -422,7 +441,7 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                         const float inv_se = __frcp_rn(se);
                         const float lse = mx + __logf(se);
                         const int64_t gr = a.g0 + m;
-                        const int yy = ylab[half];
+                        const int yy = ylab[mt][half];
                         const bool in_a = gr < a.rows_a;
                         const float coef = in_a ? a.ca : a.cb;
 #pragma unroll
@@ -482,24 +501,27 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                         stsm_x4_t(Zm + hid * 16 + hsw * 8, zp[0], zp[1], zp[2], zp[3]);
                     }
                     __syncwarp();
-                    // dZ1 -> HBM transposed: one TMA box {16 samples, HP hidden rows} of
-                    // particle j; rows past H and samples past the chunk are not written
-                    fence_proxy_async_smem();
-                    __syncwarp();
-                    if (lane == 0) {
-                        tma_store_3d(&tmZ, Zm, r0, 0, j);
-                        bulk_commit();
-                    }
-                    __syncwarp();
                 }
+                // dZ1 -> HBM transposed: per m-tile one TMA box {16 samples, HP hidden rows}
+                // of particle j (one proxy fence for both); rows past H and samples past
+                // the chunk are not written
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt)
+                        if (tile0 + 16 * mt < a.M) tma_store_3d(&tmZ, Hs + 16 * mt * HS, tile0 + 16 * mt, 0, j);
+                    bulk_commit();
+                }
+                __syncwarp();
             }
             if (!ok) break;
 
             // ---- 6. this warp's partial for the pair segment: dW2 [C][H] | db2 [C], LL sums
             if (active) {
-                const int seg = cta - owner_of((int64_t)p * a.tiles_m, a.T, G);
-                const bool last = cta == owner_of((int64_t)(p + 1) * a.tiles_m - 1, a.T, G);
-                const int64_t slot = a.slot_base + seg * 4 + wq;
+                const int seg = cid - owner_of((int64_t)p * a.tiles_q, a.T, G);
+                const bool last = cid == owner_of((int64_t)(p + 1) * a.tiles_q - 1, a.T, G);
+                const int64_t slot = a.slot_base + seg * 8 + rank * 4 + wq;
                 float* pw = a.part_w + (slot * a.J + j) * (int64_t)per;
 #pragma unroll
                 for (int mh = 0; mh < KT; ++mh)
@@ -532,7 +554,7 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                 // the last segment of the pair clears the slots no CTA owns for it
                 if (last) {
                     for (int s2 = seg + 1; s2 < a.nseg; ++s2) {
-                        const int64_t sl2 = a.slot_base + s2 * 4 + wq;
+                        const int64_t sl2 = a.slot_base + s2 * 8 + rank * 4 + wq;
                         float* pz = a.part_w + (sl2 * a.J + j) * (int64_t)per;
                         for (int i = lane; i < per; i += 32) pz[i] = 0.0f;
                         if (lane < 2) a.part_l[(sl2 * a.J + j) * 2 + lane] = 0.0;
@@ -550,9 +572,10 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
     }
     tc_fence_before();
     __syncthreads();
+    cluster_sync();   // the even CTA's MMAs into this CTA's TMEM and shared memory are complete
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tbase, 512);
+        tmem_dealloc_pair(tbase, 512);
     }
 }
 
@@ -597,18 +620,65 @@ static int img_bytes_for(int H) {
     return kt == 7 ? img_bytes<7>() : (kt == 3 ? img_bytes<3>() : img_bytes<8>());
 }
 
-// Pair segments: the largest number of CTAs any pair's units are split over.
-static int nseg_of(int64_t tiles_m, int64_t npairs, int G) {
-    const int64_t T = tiles_m * npairs;
+// Pair segments: the largest number of clusters any pair's units are split over.
+static int nseg_of(int64_t tiles_q, int64_t npairs, int G) {
+    const int64_t T = tiles_q * npairs;
     int best = 1;
     for (int64_t p = 0; p < npairs; ++p) {
-        const int s = owner_of((p + 1) * tiles_m - 1, T, G) - owner_of(p * tiles_m, T, G) + 1;
+        const int s = owner_of((p + 1) * tiles_q - 1, T, G) - owner_of(p * tiles_q, T, G) + 1;
         best = std::max(best, s);
     }
     return best;
 }
 
-static int grid_of(const smc_ctx* c, int64_t T) { return (int)std::max<int64_t>(1, std::min<int64_t>(T, c->num_sms)); }
+// Clusters of two CTAs that can be resident at once (one CTA per SM; the GPC
+// layout can leave SMs unpaired), so that every cluster's range runs in one wave.
+template <int KT, int ACT>
+static int max_clusters_t(int num_sms) {
+    using F = FCfg<KT>;
+    static int cached = -1;
+    if (cached < 0) {
+        auto kern = fused_fwd_head_kernel<KT, ACT>;
+        int n = 0;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, F::SMEM) == cudaSuccess) {
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 2;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)(num_sms - num_sms % 2), 1, 1);
+            cfg.blockDim = dim3(THREADS, 1, 1);
+            cfg.dynamicSmemBytes = F::SMEM;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) n = 0;
+        }
+        cudaGetLastError();
+        cached = (n >= 1) ? std::min(n, num_sms / 2) : std::max(1, num_sms / 2);
+    }
+    return cached;
+}
+
+
+static int max_clusters(const smc_ctx* c) {
+    const int kt = kt_for((int)c->layers[0].out_feat()), act = c->layers[0].act;
+    auto pick = [&](auto kt_tag) {
+        constexpr int K = decltype(kt_tag)::value;
+        if (act == SMC_ACT_RELU) return max_clusters_t<K, SMC_ACT_RELU>(c->num_sms);
+        if (act == SMC_ACT_TANH) return max_clusters_t<K, SMC_ACT_TANH>(c->num_sms);
+        return max_clusters_t<K, SMC_ACT_IDENTITY>(c->num_sms);
+    };
+    if (kt == 7) return pick(std::integral_constant<int, 7>{});
+    if (kt == 3) return pick(std::integral_constant<int, 3>{});
+    return pick(std::integral_constant<int, 8>{});
+}
+
+static int grid_of(const smc_ctx* c, int64_t T) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(T, max_clusters(c)));
+}
+
+static int64_t tiles_q_of(int64_t mc) { return ((mc + BM - 1) / BM + 1) / 2; }
 
 template <int KT, int ACT>
 static cudaError_t launch_t(smc_ctx* c, const FusedArgs& a, const CUtensorMap& ta, const CUtensorMap& tb,
@@ -621,7 +691,22 @@ static cudaError_t launch_t(smc_ctx* c, const FusedArgs& a, const CUtensorMap& t
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    SMC_LAUNCH(c, kern<<<G, THREADS, F::SMEM, c->stream>>>(ta, tb, tz, a));
+    if (G > max_clusters_t<KT, ACT>(c->num_sms)) return cudaErrorInvalidValue;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(2 * G), 1, 1);
+    cfg.blockDim = dim3(THREADS, 1, 1);
+    cfg.dynamicSmemBytes = F::SMEM;
+    cfg.stream = c->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ta, tb, tz, a);
+    c->launches++;
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -640,8 +725,8 @@ using namespace fz;
 int64_t fused_image_bytes(const smc_ctx* c) { return (int64_t)c->J * img_bytes_for((int)c->layers[0].out_feat()); }
 
 int64_t fused_slots(const smc_ctx* c, int64_t mc) {
-    const int64_t tiles_m = (mc + BM - 1) / BM, npairs = (c->J + 1) / 2;
-    return 4 * (int64_t)nseg_of(tiles_m, npairs, grid_of(c, tiles_m * npairs));
+    const int64_t tiles_q = tiles_q_of(mc), npairs = (c->J + 1) / 2;
+    return 8 * (int64_t)nseg_of(tiles_q, npairs, grid_of(c, tiles_q * npairs));
 }
 
 cudaError_t launch_fused_images(smc_ctx* c) {
@@ -666,8 +751,9 @@ cudaError_t launch_fused_fwd_head(smc_ctx* c, const __nv_bfloat16* x, int64_t g0
     a.K = (int)c->in_feat;
     a.J = c->J; a.H = H; a.C = c->n_out;
     a.tiles_m = (int)((mc + BM - 1) / BM);
+    a.tiles_q = (int)tiles_q_of(mc);
     a.npairs = (c->J + 1) / 2;
-    a.T = (int64_t)a.tiles_m * a.npairs;
+    a.T = (int64_t)a.tiles_q * a.npairs;
     a.kb_total = (int)((c->in_feat + BK - 1) / BK);
     a.g0 = g0;
     a.rows_a = c->rows_a;
@@ -679,13 +765,13 @@ cudaError_t launch_fused_fwd_head(smc_ctx* c, const __nv_bfloat16* x, int64_t g0
     a.part_l = c->head_ll;
     a.slot_base = slot_base;
     const int G = grid_of(c, a.T);
-    a.nseg = nseg_of(a.tiles_m, a.npairs, G);
+    a.nseg = nseg_of(a.tiles_q, a.npairs, G);
     a.err = c->err_dev;
-    *nslots = 4 * a.nseg;
+    *nslots = 8 * a.nseg;
     CUtensorMap ta, tb, tz;
     const uint64_t din = (uint64_t)c->in_feat;
     if (!make_tmap(&ta, x, din, (uint64_t)mc, din * 2, BM)) return cudaErrorInvalidValue;
-    if (!make_tmap_3d(&tb, c->shadow, din, (uint64_t)H, (uint64_t)c->J, din * 2, din * 2 * (uint64_t)H, HP, 2))
+    if (!make_tmap_3d(&tb, c->shadow, din, (uint64_t)H, (uint64_t)c->J, din * 2, din * 2 * (uint64_t)H, HP, 1))
         return cudaErrorInvalidValue;
     // dZ1^T [J][H][ldz]: box {16 samples, HP hidden rows} per m-tile
     const uint64_t ldz = (uint64_t)c->chunk;

@@ -215,6 +215,16 @@ static __device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtenso
         : "memory");
 }
 
+// 3-D form of tma_load_2d_pair.
+static __device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* tm, int x, int y, int z,
+                                                        uint32_t bar_cluster) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cta.global.tile.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%2, "
+        "%3, %4}], [%5];"
+        ::"r"(su32(dst)), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(bar_cluster)
+        : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
 // 128 bytes, 8-row groups 1024 bytes apart (stride byte offset), version 1.
 static __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
