@@ -279,6 +279,24 @@ smc_status smc_set_noise(smc_ctx* ctx, const float* z);
  * J values (multinomial), host, each in [0, 1). */
 smc_status smc_set_uniforms(smc_ctx* ctx, const double* u, int32_t n);
 
+/* Checkpoint (the paper has no counterpart: run infrastructure).  Writes the
+ * sampler's dynamic state to the file `path`: particles, raw and normalised
+ * log-weights, cached log pi and its two log-likelihood sums, last ancestors,
+ * the cached gradient (if valid), the schedule position and target (k, row
+ * regions, coefficients, beta), the step counter that positions the momentum
+ * stream, the host resampling-uniform stream, and the learned proposal
+ * (parameters, Adam moments, collected training rows).  Model, data and
+ * configuration are not stored; noise or uniforms injected but not yet
+ * consumed are dropped.  SMC_EINVAL if the file cannot be written. */
+smc_status smc_checkpoint(smc_ctx* ctx, const char* path);
+
+/* Restore a checkpoint into a context created with the same model, data, J,
+ * seed and precision (checked; SMC_EINVAL on a mismatch, another library
+ * version or a truncated file; the context is unchanged when a header check
+ * fails).  Continuing from the restored state reproduces the original run bit
+ * for bit. */
+smc_status smc_restore(smc_ctx* ctx, const char* path);
+
 /* Evaluate, at the current particles and under the current target, log pi [J],
  * the gradient of the log-likelihood part sum_i c_i grad log p(y_i|theta)
  * [J][D] (canonical order, prior excluded) and the unweighted log-likelihood

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 
 using namespace smc;
@@ -181,6 +182,41 @@ void seg_to_canon(const smc_ctx* c, const std::vector<float>& seg, float* canon)
 }
 int64_t flat_size(const smc_ctx* c) { return c->segs.back().off + (int64_t)c->J * c->segs.back().size; }
 
+}  // namespace
+
+// ---------------------------------------------------------------- checkpoint file
+// File: a fixed header (identity of the run + every scalar that carries state
+// from one iteration to the next), then the device arrays in a fixed order.
+namespace {
+constexpr char kCkptMagic[8] = {'S', 'M', 'C', 'C', 'K', 'P', 'T', '1'};
+
+struct CkptHeader {
+    char magic[8];
+    int32_t abi, precision, J, scheduled;
+    int64_t D, N, flat, k, rows_a, rows_b, step_index, resample_count, lp_rows;
+    uint64_t seed, target_id, split_state;
+    double coef_a, coef_b, beta, ess, lp_last_h;
+    int32_t grad_valid, lp_fallback, lp_train_steps, has_learned, n_lp_params, n_segs;
+    smc_schedule sched;
+};
+
+bool put(FILE* f, const void* p, size_t n) { return n == 0 || fwrite(p, 1, n, f) == n; }
+bool get(FILE* f, void* p, size_t n) { return n == 0 || fread(p, 1, n, f) == n; }
+
+// device array <-> file through a host staging buffer
+template <typename T>
+cudaError_t dev_to_file(FILE* f, const T* d, int64_t n, bool* io_ok) {
+    std::vector<T> h((size_t)n);
+    cudaError_t e = n ? cudaMemcpy(h.data(), d, (size_t)n * sizeof(T), cudaMemcpyDeviceToHost) : cudaSuccess;
+    if (e == cudaSuccess && !put(f, h.data(), (size_t)n * sizeof(T))) *io_ok = false;
+    return e;
+}
+template <typename T>
+cudaError_t file_to_dev(FILE* f, T* d, int64_t n, bool* io_ok) {
+    std::vector<T> h((size_t)n);
+    if (!get(f, h.data(), (size_t)n * sizeof(T))) { *io_ok = false; return cudaSuccess; }
+    return n ? cudaMemcpy(d, h.data(), (size_t)n * sizeof(T), cudaMemcpyHostToDevice) : cudaSuccess;
+}
 }  // namespace
 
 extern "C" {
@@ -643,6 +679,113 @@ smc_status smc_upload_rows(smc_ctx* c, int64_t row0, int64_t n, const float* x, 
     if (e == cudaSuccess && yv) e = cudaMemcpyAsync(c->Yv + row0, yv, n * 4, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && c->precision == SMC_PREC_BF16) e = launch_bf16_data(c);
     if (e != cudaSuccess) return cuda_check(c, e, "upload rows");
+    return SMC_OK;
+}
+
+// ---------------------------------------------------------------- checkpoints
+
+smc_status smc_checkpoint(smc_ctx* c, const char* path) {
+    if (!c || !path) return SMC_EINVAL;
+    if (!ok_ctx(c)) return SMC_ESTATE;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "checkpoint");
+    CkptHeader h{};
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.abi = SMC_ABI_VERSION;
+    h.precision = c->precision;
+    h.J = c->J;
+    h.scheduled = c->scheduled ? 1 : 0;
+    h.D = c->D; h.N = c->N; h.flat = flat_size(c);
+    h.k = c->k; h.rows_a = c->rows_a; h.rows_b = c->rows_b;
+    h.step_index = c->step_index; h.resample_count = c->resample_count; h.lp_rows = c->lp_rows;
+    h.seed = c->seed; h.target_id = c->target_id; h.split_state = c->split_state;
+    h.coef_a = c->coef_a; h.coef_b = c->coef_b; h.beta = c->beta; h.ess = c->ess; h.lp_last_h = c->lp_last_h;
+    h.grad_valid = c->grad_target_id == c->target_id ? 1 : 0;
+    h.lp_fallback = c->lp_fallback ? 1 : 0;
+    h.lp_train_steps = c->lp_train_steps;
+    h.has_learned = c->lp_params ? 1 : 0;
+    h.n_lp_params = learned_num_params();
+    h.n_segs = (int32_t)c->segs.size();
+    h.sched = c->sched;
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(c, SMC_EINVAL, std::string("cannot open checkpoint for writing: ") + path);
+    bool io = put(f, &h, sizeof(h));
+    const int64_t J = c->J;
+    if (io && e == cudaSuccess) e = dev_to_file(f, c->theta, h.flat, &io);
+    if (io && e == cudaSuccess) e = dev_to_file(f, c->logw, J, &io);
+    if (io && e == cudaSuccess) e = dev_to_file(f, c->wn, J, &io);
+    if (io && e == cudaSuccess) e = dev_to_file(f, c->logpi, J, &io);
+    if (io && e == cudaSuccess) e = dev_to_file(f, c->la, J, &io);
+    if (io && e == cudaSuccess) e = dev_to_file(f, c->lb, J, &io);
+    if (io && e == cudaSuccess) e = dev_to_file(f, c->anc, J, &io);
+    if (io && e == cudaSuccess && h.grad_valid) e = dev_to_file(f, c->grad, h.flat, &io);
+    if (io && e == cudaSuccess && h.has_learned) {
+        e = dev_to_file(f, c->lp_params, h.n_lp_params, &io);
+        if (io && e == cudaSuccess) e = dev_to_file(f, c->lp_adam, 2 * (int64_t)h.n_lp_params, &io);
+        if (io && e == cudaSuccess) e = dev_to_file(f, c->lp_dataF, c->lp_rows * 8, &io);
+        if (io && e == cudaSuccess) e = dev_to_file(f, c->lp_dataT, c->lp_rows * 2, &io);
+    }
+    io = (fclose(f) == 0) && io;
+    if (e != cudaSuccess) return cuda_check(c, e, "checkpoint");
+    if (!io) return fail(c, SMC_EINVAL, std::string("checkpoint write failed: ") + path);
+    return SMC_OK;
+}
+
+smc_status smc_restore(smc_ctx* c, const char* path) {
+    if (!c || !path) return SMC_EINVAL;
+    if (!ok_ctx(c)) return SMC_ESTATE;
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(c, SMC_EINVAL, std::string("cannot open checkpoint: ") + path);
+    CkptHeader h{};
+    if (!get(f, &h, sizeof(h)) || std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.abi != SMC_ABI_VERSION) {
+        fclose(f);
+        return fail(c, SMC_EINVAL, "not a checkpoint of this library version");
+    }
+    if (h.J != c->J || h.D != c->D || h.N != c->N || h.flat != flat_size(c) || h.precision != c->precision ||
+        h.seed != c->seed || h.n_segs != (int32_t)c->segs.size() || h.n_lp_params != learned_num_params() ||
+        (h.has_learned && !c->lp_params) || h.lp_rows < 0 || h.lp_rows > c->lp_cap) {
+        fclose(f);
+        return fail(c, SMC_EINVAL, "checkpoint was written by a context with another J, model, data, seed or precision");
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    bool io = true;
+    const int64_t J = c->J;
+    if (e == cudaSuccess) e = file_to_dev(f, c->theta, h.flat, &io);
+    if (io && e == cudaSuccess) e = file_to_dev(f, c->logw, J, &io);
+    if (io && e == cudaSuccess) e = file_to_dev(f, c->wn, J, &io);
+    if (io && e == cudaSuccess) e = file_to_dev(f, c->logpi, J, &io);
+    if (io && e == cudaSuccess) e = file_to_dev(f, c->la, J, &io);
+    if (io && e == cudaSuccess) e = file_to_dev(f, c->lb, J, &io);
+    if (io && e == cudaSuccess) e = file_to_dev(f, c->anc, J, &io);
+    if (io && e == cudaSuccess && h.grad_valid) e = file_to_dev(f, c->grad, h.flat, &io);
+    if (io && e == cudaSuccess && h.has_learned) {
+        e = file_to_dev(f, c->lp_params, h.n_lp_params, &io);
+        if (io && e == cudaSuccess) e = file_to_dev(f, c->lp_adam, 2 * (int64_t)h.n_lp_params, &io);
+        if (io && e == cudaSuccess) e = file_to_dev(f, c->lp_dataF, h.lp_rows * 8, &io);
+        if (io && e == cudaSuccess) e = file_to_dev(f, c->lp_dataT, h.lp_rows * 2, &io);
+    }
+    fclose(f);
+    if (e == cudaSuccess) e = launch_shadow(c);   // BF16 copy of the first layer's weights
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "restore");
+    if (!io) return fail(c, SMC_EINVAL, "truncated checkpoint");
+    c->scheduled = h.scheduled != 0;
+    c->sched = h.sched;
+    c->k = (int)h.k;
+    c->rows_a = h.rows_a; c->rows_b = h.rows_b;
+    c->coef_a = h.coef_a; c->coef_b = h.coef_b; c->beta = h.beta;
+    c->target_id = h.target_id;
+    c->grad_target_id = h.grad_valid ? h.target_id : ~0ull;
+    c->ess = h.ess;
+    c->step_index = (int)h.step_index;
+    c->resample_count = (int)h.resample_count;
+    c->split_state = h.split_state;
+    c->lp_rows = h.lp_rows;
+    c->lp_fallback = h.lp_fallback != 0;
+    c->lp_last_h = h.lp_last_h;
+    c->lp_train_steps = h.lp_train_steps;
+    c->pending_u.clear();
+    c->pending_noise = false;
     return SMC_OK;
 }
 

@@ -107,6 +107,8 @@ _SIGS = {
     "smc_get_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smc_get_permutation": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smc_get_ancestors": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "smc_checkpoint": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "smc_restore": (C.c_int, [C.c_void_p, C.c_char_p]),
     "smc_get_counters": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_void_p, C.c_int32, C.c_void_p]),
     "smc_reset_counters": (C.c_int, [C.c_void_p]),
     "smc_learned_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -364,6 +366,17 @@ def smc_get_ancestors(ctx, J):
     a = np.empty(J, np.int32)
     _check(load().smc_get_ancestors(ctx, _ptr(a)), "smc_get_ancestors", ctx)
     return a
+
+
+def smc_checkpoint(ctx, path):
+    """Write the sampler's dynamic state to `path` (see include/smc.h)."""
+    _check(load().smc_checkpoint(ctx, os.fsencode(path)), "smc_checkpoint", ctx)
+
+
+def smc_restore(ctx, path):
+    """Load a checkpoint into a context built with the same model, data, J, seed
+    and precision."""
+    _check(load().smc_restore(ctx, os.fsencode(path)), "smc_restore", ctx)
 
 
 def smc_get_counters(ctx):
