@@ -279,6 +279,38 @@ smc_status smc_set_noise(smc_ctx* ctx, const float* z);
  * J values (multinomial), host, each in [0, 1). */
 smc_status smc_set_uniforms(smc_ctx* ctx, const double* u, int32_t n);
 
+/* ---- particle-sharded runs (several contexts, one per GPU, holding
+ * consecutive particle ranges of one sampler; the normalisation and
+ * resampling of Sec. 2 need all J weights, so a driver exchanges them between
+ * the calls below).  The paper runs on one device and has no counterpart. */
+
+/* Global index of this context's particle 0.  The prior and momentum draws of
+ * particle j then use the Philox stream positions of global particle
+ * first_particle + j, so G contexts with consecutive ranges draw exactly what
+ * one context with all particles draws.  Redraws theta_0 (eq. init_weight) with
+ * those positions; call before smc_set_schedule. */
+smc_status smc_set_shard(smc_ctx* ctx, int64_t first_particle);
+
+/* Draw n uniforms in [0, 1) from the context's resampling stream (host
+ * SplitMix64; the stream smc_resample consumes; injected uniforms first).
+ * Contexts with equal seeds draw equal values. */
+smc_status smc_draw_uniforms(smc_ctx* ctx, int32_t n, double* u);
+
+/* Install normalised weights w~ [J] (host; this context's slice of the global
+ * weights, eq. normalise) and the global ESS (eq. jeff).  Used by SDA moments,
+ * prediction and the next resampling decision. */
+smc_status smc_set_weights(smc_ctx* ctx, const double* wn, double ess);
+
+/* This context's partial SDA moments under its current weights (Sec. 3.1):
+ * out[0..3] = sum_j w~_j Omega^_j, sum_j w~_j Omega^_j^2, sum_j w~_j Omega_j,
+ * sum_j w~_j Omega_j Omega^_j, with Omega^ = -L_b and Omega = -L_a. */
+smc_status smc_sda_partials(smc_ctx* ctx, double* out);
+
+/* smc_anneal_next with the four SDA moments supplied (summed over all shards)
+ * instead of computed from this context's particles; identical to
+ * smc_anneal_next for the fixed schedules. */
+smc_status smc_anneal_next_moments(smc_ctx* ctx, const double* moments, smc_anneal_info* info);
+
 /* Checkpoint (the paper has no counterpart: run infrastructure).  Writes the
  * sampler's dynamic state to the file `path`: particles, raw and normalised
  * log-weights, cached log pi and its two log-likelihood sums, last ancestors,

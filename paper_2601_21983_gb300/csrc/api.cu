@@ -540,7 +540,16 @@ smc_status smc_step(smc_ctx* c, const smc_step_params* p, smc_step_stats* stats)
     return st;
 }
 
-smc_status smc_anneal_next(smc_ctx* c, smc_anneal_info* info) {
+static smc_status anneal_impl(smc_ctx* c, const double* given, smc_anneal_info* info);
+
+smc_status smc_anneal_next(smc_ctx* c, smc_anneal_info* info) { return anneal_impl(c, nullptr, info); }
+
+smc_status smc_anneal_next_moments(smc_ctx* c, const double* moments, smc_anneal_info* info) {
+    if (!moments) return SMC_EINVAL;
+    return anneal_impl(c, moments, info);
+}
+
+static smc_status anneal_impl(smc_ctx* c, const double* given, smc_anneal_info* info) {
     if (!c) return SMC_EINVAL;
     if (!ok_ctx(c) || !c->scheduled) return SMC_ESTATE;
     const int64_t before = c->rows_a + c->rows_b;
@@ -569,13 +578,17 @@ smc_status smc_anneal_next(smc_ctx* c, smc_anneal_info* info) {
         c->target_id++;
     } else {
         // eqs. beta_initial_data_k / beta_annealed_k with the weighted moments
-        cudaError_t e = launch_sda_moments(c);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(c->stats_host + 8, c->stats_dev + 8, 4 * sizeof(double), cudaMemcpyDeviceToHost,
-                                c->stream);
-        if (e != cudaSuccess) return cuda_check(c, e, "sda moments");
-        smc_status st = sync_and_check(c, "sda moments");
-        if (st != SMC_OK) return st;
+        if (given) {
+            std::memcpy(c->stats_host + 8, given, 4 * sizeof(double));
+        } else {
+            cudaError_t e = launch_sda_moments(c);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c->stats_host + 8, c->stats_dev + 8, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream);
+            if (e != cudaSuccess) return cuda_check(c, e, "sda moments");
+            smc_status st = sync_and_check(c, "sda moments");
+            if (st != SMC_OK) return st;
+        }
         const double e_oh = c->stats_host[8], e_oh2 = c->stats_host[9], e_o = c->stats_host[10],
                      e_ooh = c->stats_host[11];
         const double var = e_oh2 - e_oh * e_oh;
@@ -679,6 +692,50 @@ smc_status smc_upload_rows(smc_ctx* c, int64_t row0, int64_t n, const float* x, 
     if (e == cudaSuccess && yv) e = cudaMemcpyAsync(c->Yv + row0, yv, n * 4, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && c->precision == SMC_PREC_BF16) e = launch_bf16_data(c);
     if (e != cudaSuccess) return cuda_check(c, e, "upload rows");
+    return SMC_OK;
+}
+
+// ---------------------------------------------------------------- sharded runs
+smc_status smc_set_shard(smc_ctx* c, int64_t first_particle) {
+    if (!c || first_particle < 0) return SMC_EINVAL;
+    if (!ok_ctx(c)) return SMC_ESTATE;
+    c->particle_offset = first_particle;
+    // theta_0 ~ q_0 again, now from the global particles' stream positions
+    cudaError_t e = launch_prior_draw(c);
+    if (e == cudaSuccess) e = launch_shadow(c);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    c->grad_target_id = ~0ull;
+    return cuda_check(c, e, "set_shard");
+}
+
+smc_status smc_draw_uniforms(smc_ctx* c, int32_t n, double* u) {
+    if (!c || !u || n < 1) return SMC_EINVAL;
+    for (int i = 0; i < n; ++i)
+        u[i] = (i < (int)c->pending_u.size()) ? c->pending_u[i] : splitmix_double(c->split_state);
+    c->pending_u.clear();
+    return SMC_OK;
+}
+
+smc_status smc_set_weights(smc_ctx* c, const double* wn, double ess) {
+    if (!c || !wn || !(ess >= 0.0)) return SMC_EINVAL;
+    if (!ok_ctx(c)) return SMC_ESTATE;
+    cudaError_t e = cudaMemcpyAsync(c->wn, wn, c->J * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "set_weights");
+    c->ess = ess;
+    return SMC_OK;
+}
+
+smc_status smc_sda_partials(smc_ctx* c, double* out) {
+    if (!c || !out) return SMC_EINVAL;
+    if (!ok_ctx(c) || !c->scheduled) return SMC_ESTATE;
+    cudaError_t e = launch_sda_moments(c);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->stats_host + 8, c->stats_dev + 8, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "sda partials");
+    smc_status st = sync_and_check(c, "sda partials");
+    if (st != SMC_OK) return st;
+    std::memcpy(out, c->stats_host + 8, 4 * sizeof(double));
     return SMC_OK;
 }
 

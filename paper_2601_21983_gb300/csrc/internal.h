@@ -65,6 +65,7 @@ struct smc_ctx {
     uint64_t seed = 0;
     cudaStream_t stream = nullptr;
     int device = 0, num_sms = 148;
+    int64_t particle_offset = 0;     // global index of particle 0 (sharded runs: Philox streams)
     bool timing = false;
     bool failed = false;
     std::string last_error;

@@ -61,16 +61,22 @@ __global__ void philox_u32_kernel(uint32_t k0, uint32_t k1, uint32_t c2, uint32_
 
 // Normals in canonical order scattered to the segment-major layout, times scale.
 // z_src != nullptr: injected draws (canonical order) instead of Philox.
-__global__ void canon_normals_kernel(float* dst, SegTable t, int64_t D, int64_t total, uint64_t seed,
+// Element e of this context's [J][D] canonical block is element base + e of the
+// stream (base = first particle's global index * D), so ranks holding
+// consecutive particle ranges draw exactly what one context holding all of them
+// would.  One thread per stream quad overlapping [base, base + total).
+__global__ void canon_normals_kernel(float* dst, SegTable t, int64_t D, int64_t total, int64_t base, uint64_t seed,
                                      uint32_t sid, uint32_t it, float scale, const float* z_src) {
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q * 4 >= total) return;
+    const int64_t q = base / 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q * 4 >= base + total) return;
     float z[4];
     if (z_src == nullptr) normals4(seed, sid, it, (uint64_t)q, z);
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        const int64_t e = q * 4 + r;
-        if (e < total) dst[canon_to_addr(t, D, e)] = scale * (z_src ? z_src[e] : z[r]);
+        const int64_t eg = q * 4 + r;
+        if (eg < base || eg >= base + total) continue;
+        const int64_t e = eg - base;
+        dst[canon_to_addr(t, D, e)] = scale * (z_src ? z_src[e] : z[r]);
     }
 }
 
@@ -488,19 +494,22 @@ static int part_chunks_for(const smc_ctx* c) {
     return (int)n;
 }
 
+static int64_t stream_quads(int64_t base, int64_t total) { return (base + total + 3) / 4 - base / 4; }
+
 cudaError_t launch_prior_draw(smc_ctx* c) {
-    const int64_t total = (int64_t)c->J * c->D;
-    const int64_t quads = (total + 3) / 4;
+    const int64_t total = (int64_t)c->J * c->D, base = c->particle_offset * c->D;
+    const int64_t quads = stream_quads(base, total);
     SMC_LAUNCH(c, canon_normals_kernel<<<(unsigned)((quads + 255) / 256), 256, 0, c->stream>>>(
-                      c->theta, seg_table(c), c->D, total, c->seed, RNG_PRIOR, 0u, (float)c->prior_sigma, nullptr));
+                      c->theta, seg_table(c), c->D, total, base, c->seed, RNG_PRIOR, 0u, (float)c->prior_sigma,
+                      nullptr));
     return cudaGetLastError();
 }
 
 cudaError_t launch_momentum(smc_ctx* c, bool injected) {
-    const int64_t total = (int64_t)c->J * c->D;
-    const int64_t quads = (total + 3) / 4;
+    const int64_t total = (int64_t)c->J * c->D, base = c->particle_offset * c->D;
+    const int64_t quads = stream_quads(base, total);
     SMC_LAUNCH(c, canon_normals_kernel<<<(unsigned)((quads + 255) / 256), 256, 0, c->stream>>>(
-                      c->mom, seg_table(c), c->D, total, c->seed, RNG_MOMENTUM, (uint32_t)c->step_index, 1.0f,
+                      c->mom, seg_table(c), c->D, total, base, c->seed, RNG_MOMENTUM, (uint32_t)c->step_index, 1.0f,
                       injected ? c->z_inject : nullptr));
     return cudaGetLastError();
 }

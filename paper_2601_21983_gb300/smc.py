@@ -107,6 +107,11 @@ _SIGS = {
     "smc_get_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smc_get_permutation": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smc_get_ancestors": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "smc_set_shard": (C.c_int, [C.c_void_p, C.c_int64]),
+    "smc_draw_uniforms": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "smc_set_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double]),
+    "smc_sda_partials": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "smc_anneal_next_moments": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(smc_anneal_info)]),
     "smc_checkpoint": (C.c_int, [C.c_void_p, C.c_char_p]),
     "smc_restore": (C.c_int, [C.c_void_p, C.c_char_p]),
     "smc_get_counters": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_void_p, C.c_int32, C.c_void_p]),
@@ -243,6 +248,35 @@ def smc_anneal_next(ctx):
     return info.as_dict()
 
 
+def smc_anneal_next_moments(ctx, moments):
+    m = np.ascontiguousarray(moments, np.float64)
+    assert m.shape == (4,)
+    info = smc_anneal_info()
+    _check(load().smc_anneal_next_moments(ctx, _ptr(m), C.byref(info)), "smc_anneal_next_moments", ctx)
+    return info.as_dict()
+
+
+def smc_set_shard(ctx, first_particle):
+    _check(load().smc_set_shard(ctx, int(first_particle)), "smc_set_shard", ctx)
+
+
+def smc_draw_uniforms(ctx, n):
+    u = np.empty(int(n), np.float64)
+    _check(load().smc_draw_uniforms(ctx, int(n), _ptr(u)), "smc_draw_uniforms", ctx)
+    return u
+
+
+def smc_set_weights(ctx, wn, ess):
+    w = np.ascontiguousarray(wn, np.float64)
+    _check(load().smc_set_weights(ctx, _ptr(w), float(ess)), "smc_set_weights", ctx)
+
+
+def smc_sda_partials(ctx):
+    out = np.empty(4, np.float64)
+    _check(load().smc_sda_partials(ctx, _ptr(out)), "smc_sda_partials", ctx)
+    return out
+
+
 def smc_resample(ctx, force=False):
     did = C.c_int32(0)
     _check(load().smc_resample(ctx, 1 if force else 0, C.byref(did)), "smc_resample", ctx)
@@ -260,8 +294,8 @@ def smc_upload_rows(ctx, row0, x, y_class=None, y_value=None):
            "smc_upload_rows", ctx)
 
 
-def smc_get_state(ctx, J, D):
-    th = np.empty((J, D), np.float32)
+def smc_get_state(ctx, J, D, theta=True):
+    th = np.empty((J, D), np.float32) if theta else None
     lw = np.empty(J, np.float64)
     lp = np.empty(J, np.float64)
     _check(load().smc_get_state(ctx, _ptr(th), _ptr(lw), _ptr(lp)), "smc_get_state", ctx)
