@@ -508,9 +508,13 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) {
+                    // dZ1^T streams through L2 once: evict it first so it does not push out
+                    // the input rows and first-layer weights the next units read
+                    const uint64_t pol = policy_evict_first();
 #pragma unroll
                     for (int mt = 0; mt < 2; ++mt)
-                        if (tile0 + 16 * mt < a.M) tma_store_3d(&tmZ, Hs + 16 * mt * HS, tile0 + 16 * mt, 0, j);
+                        if (tile0 + 16 * mt < a.M)
+                            tma_store_3d_hint(&tmZ, Hs + 16 * mt * HS, tile0 + 16 * mt, 0, j, pol);
                     bulk_commit();
                 }
                 __syncwarp();

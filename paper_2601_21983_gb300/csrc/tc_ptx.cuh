@@ -126,6 +126,19 @@ static __device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, const
                  ::"l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(su32(src))
                  : "memory");
 }
+// L2 policy for data written once and not read again by this kernel.
+static __device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// tma_store_3d with an L2 cache policy.
+static __device__ __forceinline__ void tma_store_3d_hint(const CUtensorMap* tm, const void* src, int x, int y, int z,
+                                                         uint64_t policy) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%1, %2, %3}], [%4], %5;"
+                 ::"l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(su32(src)), "l"(policy)
+                 : "memory");
+}
 static __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 static __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 static __device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
