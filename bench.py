@@ -302,6 +302,56 @@ def run_tta(args):
     print(json.dumps(line), flush=True)
 
 
+def run_grid(args):
+    """The scheme grid of Sec. 4 (Table 1) on the MNIST-shaped stand-in: every
+    data-annealing scheme (Sec. 3.1: Constant, FB, CTR, Linear, Automated, SDA)
+    x {LD (S = 1), HMC (S = 3)} from the same seed for K iterations, C = kappa =
+    the mini-batch size.  Runtime = GPU-synchronous wall time over the
+    iterations (test evaluation excluded); then the posterior-predictive
+    accuracy and NLL on a separate test draw."""
+    import torch
+    from paper_2601_21983_gb300 import smc as S
+    S.load()
+    stream = torch.cuda.current_stream()
+    import synthetic
+    X, y = make_data(args.n, seed=0)
+    Xt, yt = synthetic.template_images(10000, seed=0, test=True)
+    Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    Xtd = torch.from_numpy(Xt).cuda()
+    probs = torch.empty((10000, NCLS), device="cuda", dtype=torch.float32)
+    model = S.make_model([("dense", DIN, H), ("dense", H, NCLS)], (DIN,), S.ACT_RELU)
+    K, mb = args.grid_iters, args.grid_mb
+    rows = []
+    for kernel, steps in [("LD", 1), ("HMC", S_LF)]:
+        for scheme in ["constant", "fb", "ctr", "linear", "automated", "sda"]:
+            ctx = S.smc_init(model, Xd, y_class=yd, cfg=S.make_config(args.J, 7, S.PREC_BF16, stream=stream))
+            S.smc_set_schedule(ctx, S.make_schedule(scheme, mb, mb, K, delta_s=1.0))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rows_seen = 0
+            for _ in range(1, K):
+                info = S.smc_anneal_next(ctx)
+                S.smc_resample(ctx)
+                S.smc_step(ctx, STEP_H, steps)
+                rows_seen += info["rows"]
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            S.smc_posterior_predict(ctx, Xtd, probs)
+            p = probs.double().cpu().numpy()
+            acc = float((p.argmax(axis=1) == yt).mean())
+            nll = float(-np.mean(np.log(np.maximum(p[np.arange(len(yt)), yt], 1e-300))))
+            S.smc_destroy(ctx)
+            rows.append({"kernel": kernel, "scheme": scheme, "seconds": secs, "test_acc": acc, "test_nll": nll,
+                         "mean_subset_rows": rows_seen / (K - 1)})
+    for r in rows:
+        fb = next(q for q in rows if q["kernel"] == r["kernel"] and q["scheme"] == "fb")
+        r["speedup_vs_fb"] = fb["seconds"] / r["seconds"]
+    print(json.dumps({"metric": "scheme grid (Sec. 4 Table 1 on synthetic stand-ins)", "rows": rows,
+                      "config": {"workload": f"MLP {DIN}-{H}-{NCLS} ReLU, J={args.J}, {args.n} synthetic images, "
+                                             f"C=kappa={mb}, K={K}, h={STEP_H}, BF16, seed 7",
+                                 "test_rows": 10000}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -314,6 +364,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline", action="store_true")
     ap.add_argument("--tta", action="store_true", help="time-to-test-accuracy, learned vs plain proposal")
+    ap.add_argument("--grid", action="store_true", help="every DA scheme x {LD, HMC}: runtime and test accuracy")
+    ap.add_argument("--grid-iters", type=int, default=200)
+    ap.add_argument("--grid-mb", type=int, default=500)
     ap.add_argument("--tta-iters", type=int, default=80)
     ap.add_argument("--tta-explore", type=int, default=30)
     ap.add_argument("--tta-every", type=int, default=4)
@@ -323,6 +376,8 @@ def main():
         return run_reference(args)
     if args.tta:
         return run_tta(args)
+    if args.grid:
+        return run_grid(args)
 
     import torch
     from paper_2601_21983_gb300 import smc as S

@@ -472,3 +472,33 @@ def test_bf16_fused_and_unfused_heads_agree(monkeypatch, J, N, chunk):
     assert np.allclose(la1, la0, rtol=1e-5) and np.allclose(lb1, lb0, rtol=1e-5, atol=1e-6)
     assert np.allclose(lp1, lp0, rtol=1e-5)
     assert _per_particle_rel(g1, g0) < 2e-3
+
+
+LENET5 = [("conv", 1, 6, 5), ("pool2",), ("conv", 6, 16, 5), ("pool2",), ("dense", 400, 120), ("dense", 120, 84),
+          ("dense", 84, 10)]
+
+
+@pytest.mark.parametrize("act", [nn.TANH, nn.RELU])
+def test_lenet5_eval_parity(act):
+    """LeNet-5 (Sec. 4's model family; D = 61,706) as a model description:
+    28x28 images zero-padded to 32x32 (the first convolution's padding of 2),
+    two 5x5 valid convolutions with 2x2 max pooling, dense 400-120-84-10;
+    log-likelihoods and whole gradients against the FP64 oracle."""
+    spec = nn.Spec(LENET5, (1, 32, 32), act)
+    assert spec.n_params == 61706
+    N, J = 48, 2
+    X, y = _images(N, 23)
+    X = np.pad(X.reshape(N, 1, 28, 28), ((0, 0), (0, 0), (2, 2), (2, 2))).reshape(N, 1024)
+    ctx, orc, _ = make_pair(spec, X, y, J, seed=23, chunk=20)
+    try:
+        th0 = synthetic.particles(J, spec.n_params, 23, std=0.1)
+        S.smc_set_state(ctx, th0)
+        S.smc_set_schedule(ctx, S.make_schedule("fb", N, N, 5))
+        orc.set_schedule("fb", N, N, 5, th0)
+        lp, g, la, lb = S.smc_eval(ctx, J, spec.n_params)
+        rlp, rg, rla, rlb = oracle_eval(orc)
+        assert np.allclose(la, rla, rtol=1e-5)
+        assert np.allclose(lp, rlp, rtol=1e-5)
+        assert _per_particle_rel(g, rg) < 1e-5
+    finally:
+        S.smc_destroy(ctx)
