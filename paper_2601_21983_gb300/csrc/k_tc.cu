@@ -635,13 +635,23 @@ static void plan(GemmArgs& g, int BN, int kslices, int cs) {
     g.num_units = ((g.tiles_m + cs - 1) / cs) * g.tiles_n * g.kslices;
 }
 
-// Choose a split-K factor that evens out the last wave of persistent CTAs.
-static int choose_kslices(int tiles, int kb_total, int num_sms, int max_s) {
+// Split-K factor for the weight-gradient GEMM.  Candidate s costs
+// ceil(units * s / workers) waves of units that each run ceil(kb / s) K blocks
+// and store one 128 x 400 FP32 tile per CTA, plus, for s > 1, the reduction
+// that reads s partial slices and writes the result.  Constants are GB300
+// measurements of the CTA-pair kernel: 0.68 us per K block of a unit, about
+// 3 us per tile store, 6.5 TB/s for the reduction.  A short K (small subsets)
+// therefore gets no split: slices of one or two K blocks would spend their time
+// storing and re-reading partial tiles.
+static int choose_kslices(int64_t units, int kb_total, int workers, int max_s, double out_bytes) {
+    constexpr double kKbUs = 0.68, kStoreUs = 3.0, kBytesPerUs = 6.5e6;
     int best = 1;
-    double best_cost = 1e30;
+    double best_cost = 1e300;
     for (int s = 1; s <= max_s && s <= kb_total; ++s) {
-        const double waves = std::ceil((double)tiles * s / num_sms) / s;
-        const double cost = waves * (1.0 + 0.01 * (s - 1));
+        const double waves = std::ceil((double)units * s / std::max(workers, 1));
+        const int kbs = (kb_total + s - 1) / s;
+        double cost = waves * (kbs * kKbUs + kStoreUs);
+        if (s > 1) cost += (s + 1) * out_bytes / kBytesPerUs;
         if (cost < best_cost - 1e-9) { best_cost = cost; best = s; }
     }
     return best;
@@ -810,9 +820,9 @@ static cudaError_t launch_wgrad(smc_ctx* c, int64_t g0, int64_t mc, bool with_b1
     g.epi = EPI_F32;
     g.err = c->err_dev;
     plan(g, 400, 1, 2);
-    const int ks = choose_kslices(g.tiles_m * g.tiles_n, g.kb_total, c->num_sms, 8);
     const int64_t ldp = rup(ncol, 4);
     const int64_t slice = JH * ldp;
+    const int ks = choose_kslices(g.num_units, g.kb_total, c->num_sms / 2, 8, (double)slice * 4);
     const int use_ks = (ks > 1 && (int64_t)ks * slice <= c->gemm_part_cap) ? ks : 1;
     plan(g, 400, use_ks, 2);
     float* gW1 = c->grad + c->segs[L0.seg_w].off;
