@@ -120,6 +120,34 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
 // hscale[g] (the learned proposal; plain: G = 1, all ones).  With theta_old
 // given, phase 0 saves the starting particles and phase 2 accumulates the
 // squared jump |theta_k - theta_{k-1}|^2 per particle.
+// One leapfrog phase on element i of a particle (eqs. mom_first / pos_update /
+// mom_second with M = diag(1 / im)), accumulating this thread's kinetic energy,
+// |theta|^2 and squared jump shares.
+template <int PHASE>
+__device__ __forceinline__ void leap_elem(float& th, float& p, float g0, float* told, float im, float sqrt_m, float hk,
+                                          float hd, float inv_sig2, float& ke, float& sq, float& jump) {
+    if (PHASE == 0) {
+        if (told) *told = th;
+        p *= sqrt_m;
+        ke = fmaf(0.5f * im * p, p, ke);
+    }
+    const float g = g0 - th * inv_sig2;
+    p = fmaf(hk, g, p);
+    if (PHASE != 2) {
+        th = fmaf(hd * im, p, th);
+        sq = fmaf(th, th, sq);
+    } else {
+        ke = fmaf(0.5f * im * p, p, ke);
+        if (told) {
+            const float d = th - *told;
+            jump = fmaf(d, d, jump);
+        }
+    }
+}
+
+// Block (ch, j): chunk ch of every segment of particle j.  Segments whose
+// per-particle size is a multiple of 4 move 16 bytes per access (their starts
+// are 64-element aligned, so every particle row is 16-byte aligned).
 template <int PHASE>
 __global__ void __launch_bounds__(256) leapfrog_kernel(float* __restrict__ theta, float* __restrict__ mom,
                                                        const float* __restrict__ grad,
@@ -137,35 +165,54 @@ __global__ void __launch_bounds__(256) leapfrog_kernel(float* __restrict__ theta
     float ke = 0.0f, sq = 0.0f, jump = 0.0f;          // per-thread shares, widened to FP64 in the block sum
     for (int s = 0; s < t.n; ++s) {
         const int64_t size = t.size[s];
-        const int64_t lo = size * ch / nchunks, hi = size * (ch + 1) / nchunks;
         const int64_t base = t.off[s] + (int64_t)j * size;
         const float im = inv_mass ? inv_mass[grp * t.n + s] : 1.0f;
         const float sqrt_m = rsqrtf(im);
         const bool has_shadow = t.tc[s] != 0;
-        for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
-            const int64_t idx = base + e;
-            float th = theta[idx];
-            float p = mom[idx];
-            if (PHASE == 0) {
-                if (theta_old) theta_old[idx] = th;
-                p *= sqrt_m;
-                ke = fmaf(0.5f * im * p, p, ke);
-            }
-            const float g = grad[idx] - th * inv_sig2;
-            p = fmaf(hk, g, p);
-            if (PHASE != 2) {
-                th = fmaf(hd * im, p, th);
-                theta[idx] = th;
-                sq = fmaf(th, th, sq);
-                if (has_shadow) shadow[(int64_t)j * size + e] = __float2bfloat16_rn(th);
-            } else {
-                ke = fmaf(0.5f * im * p, p, ke);
-                if (theta_old) {
-                    const float d = th - theta_old[idx];
-                    jump = fmaf(d, d, jump);
+        if ((size & 3) == 0) {
+            const int64_t nq = size >> 2;
+            const int64_t lo = nq * ch / nchunks, hi = nq * (ch + 1) / nchunks;
+            float4* th4 = reinterpret_cast<float4*>(theta + base);
+            float4* p4 = reinterpret_cast<float4*>(mom + base);
+            const float4* g4 = reinterpret_cast<const float4*>(grad + base);
+            float4* to4 = theta_old ? reinterpret_cast<float4*>(theta_old + base) : nullptr;
+            for (int64_t q = lo + threadIdx.x; q < hi; q += blockDim.x) {
+                float4 th = th4[q], p = p4[q];
+                const float4 g = g4[q];
+                float4 to = (to4 && PHASE == 2) ? to4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                float* tp = (to4 && PHASE != 1) ? &to.x : nullptr;
+                leap_elem<PHASE>(th.x, p.x, g.x, tp, im, sqrt_m, hk, hd, inv_sig2, ke, sq, jump);
+                leap_elem<PHASE>(th.y, p.y, g.y, tp ? tp + 1 : nullptr, im, sqrt_m, hk, hd, inv_sig2, ke, sq, jump);
+                leap_elem<PHASE>(th.z, p.z, g.z, tp ? tp + 2 : nullptr, im, sqrt_m, hk, hd, inv_sig2, ke, sq, jump);
+                leap_elem<PHASE>(th.w, p.w, g.w, tp ? tp + 3 : nullptr, im, sqrt_m, hk, hd, inv_sig2, ke, sq, jump);
+                if (PHASE == 0 && to4) to4[q] = to;
+                if (PHASE != 2) {
+                    th4[q] = th;
+                    if (has_shadow) {
+                        __nv_bfloat162 lo2 = __floats2bfloat162_rn(th.x, th.y), hi2 = __floats2bfloat162_rn(th.z, th.w);
+                        uint2 v;
+                        v.x = *reinterpret_cast<uint32_t*>(&lo2);
+                        v.y = *reinterpret_cast<uint32_t*>(&hi2);
+                        *reinterpret_cast<uint2*>(shadow + (int64_t)j * size + 4 * q) = v;
+                    }
                 }
+                p4[q] = p;
             }
-            mom[idx] = p;
+        } else {
+            const int64_t lo = size * ch / nchunks, hi = size * (ch + 1) / nchunks;
+            for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+                const int64_t idx = base + e;
+                float th = theta[idx], p = mom[idx];
+                float to = (theta_old && PHASE == 2) ? theta_old[idx] : 0.0f;
+                leap_elem<PHASE>(th, p, grad[idx], (theta_old && PHASE != 1) ? &to : nullptr, im, sqrt_m, hk, hd,
+                                 inv_sig2, ke, sq, jump);
+                if (PHASE == 0 && theta_old) theta_old[idx] = to;
+                if (PHASE != 2) {
+                    theta[idx] = th;
+                    if (has_shadow) shadow[(int64_t)j * size + e] = __float2bfloat16_rn(th);
+                }
+                mom[idx] = p;
+            }
         }
     }
     const double ked = block_sum((double)ke, sh);
@@ -487,7 +534,7 @@ __global__ void predict_reduce_kernel(const float* __restrict__ logits, int64_t 
 
 // ----------------------------------------------------------------- launchers
 static int part_chunks_for(const smc_ctx* c) {
-    int64_t per = 256 * 8;
+    int64_t per = 256 * 32;   // elements per block: a few 16-byte accesses per thread per segment
     int64_t n = (c->D + per - 1) / per;
     if (n < 1) n = 1;
     if (n > kMaxPartChunks) n = kMaxPartChunks;
