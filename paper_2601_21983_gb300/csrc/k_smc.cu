@@ -29,14 +29,6 @@ SegTable seg_table(const smc_ctx* c) {
     return t;
 }
 
-// canonical element e = j*D + d  ->  segment-major address
-__device__ __forceinline__ int64_t canon_to_addr(const SegTable& t, int64_t D, int64_t e) {
-    const int64_t j = e / D, d = e - j * D;
-    int s = 0;
-    while (s + 1 < t.n && d >= t.canon[s + 1]) ++s;
-    return t.off[s] + j * t.size[s] + (d - t.canon[s]);
-}
-
 __global__ void philox_normals_kernel(uint64_t seed, uint32_t sid, uint32_t it, uint64_t off, int64_t n,
                                       float* out) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -71,12 +63,25 @@ __global__ void canon_normals_kernel(float* dst, SegTable t, int64_t D, int64_t 
     if (q * 4 >= base + total) return;
     float z[4];
     if (z_src == nullptr) normals4(seed, sid, it, (uint64_t)q, z);
+    // (particle, parameter, segment) of the quad's first element in this block,
+    // found once and stepped across the quad's elements
+    const int64_t e0 = max(q * 4, base) - base;
+    int64_t j = e0 / D, d = e0 - j * D;
+    int sg = 0;
+    while (sg + 1 < t.n && d >= t.canon[sg + 1]) ++sg;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int64_t eg = q * 4 + r;
         if (eg < base || eg >= base + total) continue;
         const int64_t e = eg - base;
-        dst[canon_to_addr(t, D, e)] = scale * (z_src ? z_src[e] : z[r]);
+        dst[t.off[sg] + j * t.size[sg] + (d - t.canon[sg])] = scale * (z_src ? z_src[e] : z[r]);
+        if (++d == D) {
+            d = 0;
+            ++j;
+            sg = 0;
+        } else if (sg + 1 < t.n && d >= t.canon[sg + 1]) {
+            ++sg;
+        }
     }
 }
 
