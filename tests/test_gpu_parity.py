@@ -502,3 +502,24 @@ def test_lenet5_eval_parity(act):
         assert _per_particle_rel(g, rg) < 1e-5
     finally:
         S.smc_destroy(ctx)
+
+
+def test_bf16_split_k_across_chunks():
+    """Subsets long enough for the weight-gradient GEMM to split K (here eight
+    slices, summed inside the CTA-pair kernel) and processed in two chunks
+    whose gradients accumulate: whole gradients and log-likelihoods against
+    the FP64 oracle."""
+    N, J, chunk = 20000, 8, 10000
+    X, y = _images(N, 29)
+    ctx, orc, _ = make_pair(MLP1, X, y, J, seed=29, precision=S.PREC_BF16, chunk=chunk)
+    try:
+        th0 = synthetic.particles(J, MLP1.n_params, 29, std=0.1)
+        S.smc_set_state(ctx, th0)
+        S.smc_set_schedule(ctx, S.make_schedule("fb", N, N, 5))
+        lp, g, la, lb = S.smc_eval(ctx, J, MLP1.n_params)
+        for j in range(J):
+            ll, gg = nn.loglik_grad(MLP1, th0[j], orc.X, orc.y, 1.0)
+            assert abs(la[j] - ll.sum()) <= 2e-2 * abs(ll.sum()), j
+            assert rel_err(g[j], gg) < 2e-2, j
+    finally:
+        S.smc_destroy(ctx)
