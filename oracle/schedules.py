@@ -15,7 +15,9 @@ from __future__ import annotations
 import math
 
 CONSTANT, FULL_BATCH, CTR, LINEAR, AUTOMATED, SDA = "constant", "fb", "ctr", "linear", "automated", "sda"
-FIXED_KINDS = (CONSTANT, FULL_BATCH, CTR, LINEAR, AUTOMATED)
+CONSTANT_FRESH, CTR_FRESH = "constant_fresh", "ctr_fresh"
+FIXED_KINDS = (CONSTANT, FULL_BATCH, CTR, LINEAR, AUTOMATED, CONSTANT_FRESH, CTR_FRESH)
+FRESH_KINDS = (CONSTANT_FRESH, CTR_FRESH)
 
 
 def _late(k: int, K: int) -> bool:
@@ -40,11 +42,11 @@ def subset_size(kind: str, k: int, N: int, C: int, kappa: int, K: int) -> int:
                are appended in whole mini-batches, then kept within [C, N].
     """
     C = min(C, N)
-    if kind == CONSTANT:
+    if kind in (CONSTANT, CONSTANT_FRESH):
         return C
     if kind == FULL_BATCH:
         return N
-    if kind == CTR:
+    if kind in (CTR, CTR_FRESH):
         return N if _late(k, K) else C
     if kind == LINEAR:
         return N if _late(k, K) else min(N, kappa * k + C)
@@ -55,6 +57,20 @@ def subset_size(kind: str, k: int, N: int, C: int, kappa: int, K: int) -> int:
         m = ((2 * m + kappa) // (2 * kappa)) * kappa     # nearest multiple, ties up
         return max(C, min(N, m))
     raise ValueError(f"unknown fixed schedule {kind!r}")
+
+
+def subset_start(kind: str, k: int, N: int, M: int) -> int:
+    """First row (in the annealed order) of iteration k's subset.
+
+    The cumulative schedules of Sec. 3 use a prefix (start 0).  The fresh
+    variants of Constant and CTR read the mini-batch of Sec. 3 as a
+    stochastic-gradient batch: iteration k uses the M rows starting at
+    (k M) mod N, wrapping past N to row 0, so consecutive iterations take
+    consecutive disjoint batches through the permuted data; the full-batch
+    refinement of CTR starts at 0."""
+    if kind in FRESH_KINDS and M < N:
+        return (k * M) % N
+    return 0
 
 
 def sda_next_beta(beta: float, wn, omega, omega_hat, delta_s: float = 1.0) -> float:

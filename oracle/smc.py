@@ -123,13 +123,23 @@ class Sampler:
         M = self.M
         return M, (self.N / M if self.scaled else 1.0), 0, 0.0
 
+    def rows(self):
+        """Indices (annealed order) of the current subset: a prefix, or for the
+        fresh schedules M consecutive rows from `schedules.subset_start`,
+        wrapping past N."""
+        ra, _, rb, _ = self.regions()
+        n = ra + rb
+        start = 0 if self.kind == schedules.SDA else schedules.subset_start(self.kind, self.k, self.N, n)
+        return (start + np.arange(n)) % self.N
+
     def target(self, theta):
         """log pi_k(theta), its gradient, and the unweighted log-likelihood sums
         over the two row regions (L_a, L_b)."""
         ra, ca, rb, cb = self.regions()
         n = ra + rb
         coef = np.concatenate([np.full(ra, ca), np.full(rb, cb)])
-        ll, g = nn.loglik_grad(self.spec, theta, self.X[:n], self.y[:n], coef)
+        idx = self.rows()
+        ll, g = nn.loglik_grad(self.spec, theta, self.X[idx], self.y[idx], coef)
         la, lb = float(ll[:ra].sum()), float(ll[ra:n].sum())
         logpi = -0.5 * float(theta @ theta) / self.sigma ** 2 + ca * la + cb * lb
         return logpi, g - theta / self.sigma ** 2, la, lb

@@ -73,7 +73,7 @@ def test_schedule_invariants(kind):
         assert all(min(C, N) <= m <= N for m in seq)
         assert all(b >= a for a, b in zip(seq, seq[1:])), "subset never shrinks"
         late = [m for k, m in enumerate(seq) if 10 * k >= 9 * K]
-        if kind != schedules.CONSTANT:
+        if kind not in (schedules.CONSTANT, schedules.CONSTANT_FRESH):
             assert all(m == N for m in late), "full data from 0.9K on"
         if kind == schedules.AUTOMATED:
             assert all(m % kappa == 0 or m == N for m in seq)
@@ -113,3 +113,21 @@ def test_sda_state_machine():
     assert (s.m_full, s.block, s.beta) == (10, 0, 1.0)
     # degenerate denominator -> beta jumps to one (reading r10)
     assert schedules.sda_next_beta(0.3, [1.0], [0.0], [5.0]) == 1.0
+
+
+def test_fresh_batches_walk_the_data_once_per_epoch():
+    """Fresh Constant batches: consecutive iterations take consecutive disjoint
+    blocks, so N / C iterations use every row exactly once (N = 60000, C = 500);
+    with N not a multiple of M the window wraps to row 0 (hand-listed)."""
+    N, C = 60000, 500
+    seen = np.zeros(N, np.int64)
+    for k in range(N // C):
+        s = schedules.subset_start(schedules.CONSTANT_FRESH, k, N, C)
+        seen[(s + np.arange(C)) % N] += 1
+    assert np.all(seen == 1)
+    windows = [list((schedules.subset_start("constant_fresh", k, 10, 4) + np.arange(4)) % 10) for k in range(4)]
+    assert windows == [[0, 1, 2, 3], [4, 5, 6, 7], [8, 9, 0, 1], [2, 3, 4, 5]]
+    # cumulative schedules and the refinement phase of fresh CTR use the prefix
+    assert schedules.subset_start(schedules.LINEAR, 5, N, 5500) == 0
+    assert schedules.subset_start(schedules.CTR_FRESH, 7, N, C) == 3500
+    assert schedules.subset_start(schedules.CTR_FRESH, 190, N, N) == 0

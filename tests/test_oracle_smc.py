@@ -230,3 +230,23 @@ def test_weight_increment_is_energy_error_under_fixed_target():
         s.step(h, int(round(0.2 / h)), z)
         incs.append(np.max(np.abs(s.logw - before)))
     assert 3.0 < incs[0] / incs[1] < 5.0 and 3.0 < incs[1] / incs[2] < 5.0, incs
+
+
+def test_fresh_batch_target_is_the_prefix_target_of_rotated_data():
+    """The fresh-batch target at iteration k equals the ordinary prefix target on
+    the same data rotated so that the batch starts at row 0 (the window is the
+    only difference between the two readings of Constant)."""
+    spec = nn.Spec([("dense", 4, 3), ("dense", 3, 2)], (4,), nn.TANH)
+    X, y = synthetic.gaussian_mixture(37, d=4, n_classes=2, seed=3)
+    perm = np.arange(37)
+    th = synthetic.particles(1, spec.n_params, 3, std=0.5)
+    fresh = smc.Sampler(spec, X, y, 1, perm)
+    fresh.set_schedule("constant_fresh", 10, 10, 20, th)
+    for _ in range(4):
+        fresh.anneal_next()                      # k = 4: rows 40..49 mod 37 = 3..12
+    start = 40 % 37
+    plain = smc.Sampler(spec, np.roll(X, -start, axis=0), np.roll(y, -start), 1, perm)
+    plain.set_schedule("constant", 10, 10, 20, th)
+    a, b = fresh.target(th[0]), plain.target(th[0])
+    assert np.isclose(a[0], b[0], rtol=1e-13) and np.allclose(a[1], b[1], rtol=1e-12, atol=1e-14)
+    assert list(fresh.rows()) == list(range(3, 13))
