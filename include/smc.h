@@ -60,7 +60,13 @@ enum { SMC_PREC_FP32 = 0, SMC_PREC_BF16 = 1 };
 enum { SMC_RESAMPLE_SYSTEMATIC = 0, SMC_RESAMPLE_MULTINOMIAL = 1 };
 enum {
     SMC_SCHED_CONSTANT = 0, SMC_SCHED_FB = 1, SMC_SCHED_CTR = 2,
-    SMC_SCHED_LINEAR = 3, SMC_SCHED_AUTOMATED = 4, SMC_SCHED_SDA = 5
+    SMC_SCHED_LINEAR = 3, SMC_SCHED_AUTOMATED = 4, SMC_SCHED_SDA = 5,
+    /* Constant and CTR drawing a fresh mini-batch each iteration (Sec. 3.1
+     * names this variant beside the cumulative ones): M_k rows starting at
+     * row (k M_k) mod N of the annealed order, wrapping past N, so that
+     * consecutive iterations walk through the data; once M_k = N the subset
+     * is all rows from row 0. */
+    SMC_SCHED_CONSTANT_FRESH = 6, SMC_SCHED_CTR_FRESH = 7
 };
 enum { SMC_PROPOSAL_PLAIN = 0, SMC_PROPOSAL_LEARNED = 1, SMC_PROPOSAL_EXPLORE = 2 };
 #define SMC_LEARNED_NUM_PARAMS 706   /* 8-64-2 network: W1 [64][8], b1 [64], W2 [2][64], b2 [2] */
@@ -187,7 +193,10 @@ int64_t smc_num_params(const smc_ctx* ctx);
  * particles and set log w_0 = log pi_0(theta) - log q_0(theta), i.e. the
  * coefficient-weighted log-likelihood (eq. init_weight); then normalise
  * (eq. normalise) and compute the ESS (eq. jeff).  `stats` may be NULL.
- * Errors: SMC_EINVAL (C < 1, kappa < 1, K < 1), SMC_ENUMERIC. */
+ * Errors: SMC_EINVAL (C < 1, kappa < 1, K < 1; a fresh mini-batch kind on
+ * the BF16 engine with C < N unless C and N are multiples of 8, since the
+ * weight-gradient GEMM reads its rows from a 16-byte aligned offset),
+ * SMC_ENUMERIC. */
 smc_status smc_set_schedule(smc_ctx* ctx, const smc_schedule* sched, smc_step_stats* stats);
 
 /* One move + reweight under the current target pi_k (Sec. 2.1):

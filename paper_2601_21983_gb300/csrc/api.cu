@@ -77,9 +77,11 @@ int64_t subset_size(int kind, int64_t k, int64_t N, int64_t C, int64_t kappa, in
     C = std::min(C, N);
     const bool late = 10 * k >= 9 * K;
     switch (kind) {
-        case SMC_SCHED_CONSTANT: return C;
+        case SMC_SCHED_CONSTANT:
+        case SMC_SCHED_CONSTANT_FRESH: return C;
         case SMC_SCHED_FB: return N;
-        case SMC_SCHED_CTR: return late ? N : C;
+        case SMC_SCHED_CTR:
+        case SMC_SCHED_CTR_FRESH: return late ? N : C;
         case SMC_SCHED_LINEAR: return late ? N : std::min(N, kappa * k + C);
         case SMC_SCHED_AUTOMATED: {
             if (late) return N;
@@ -109,10 +111,18 @@ smc_status sync_and_check(smc_ctx* c, const char* what) {
 struct SdaHost { int64_t m_full = 0, block = 0; };
 SdaHost g_unused;
 
+// First row of iteration k's subset: the cumulative schedules take a prefix;
+// the fresh kinds move an M-row window by M rows per iteration, wrapping.
+int64_t subset_start(int kind, int64_t k, int64_t N, int64_t M) {
+    const bool fresh = kind == SMC_SCHED_CONSTANT_FRESH || kind == SMC_SCHED_CTR_FRESH;
+    return (fresh && M < N) ? (int64_t)(((unsigned __int128)k * (uint64_t)M) % (uint64_t)N) : 0;
+}
+
 void set_regions_fixed(smc_ctx* c) {
     const smc_schedule& s = c->sched;
     const int64_t M = subset_size(s.kind, c->k, c->N, s.C, s.kappa, s.K);
     c->rows_a = M;
+    c->row_start = subset_start(s.kind, c->k, c->N, M);
     c->coef_a = c->scaled ? (double)c->N / (double)M : 1.0;
     c->rows_b = 0;
     c->coef_b = 0.0;
@@ -435,9 +445,12 @@ void smc_destroy(smc_ctx* c) {
 smc_status smc_set_schedule(smc_ctx* c, const smc_schedule* s, smc_step_stats* stats) {
     if (!c || !s) return SMC_EINVAL;
     if (!ok_ctx(c)) return SMC_ESTATE;
-    if (s->kind < SMC_SCHED_CONSTANT || s->kind > SMC_SCHED_SDA || s->C < 1 || s->kappa < 1 || s->K < 1 ||
+    if (s->kind < SMC_SCHED_CONSTANT || s->kind > SMC_SCHED_CTR_FRESH || s->C < 1 || s->kappa < 1 || s->K < 1 ||
         s->k_start < 0)
         return fail(c, SMC_EINVAL, "schedule arguments");
+    if ((s->kind == SMC_SCHED_CONSTANT_FRESH || s->kind == SMC_SCHED_CTR_FRESH) && c->precision == SMC_PREC_BF16 &&
+        s->C < c->N && (s->C % 8 != 0 || c->N % 8 != 0))
+        return fail(c, SMC_EINVAL, "fresh mini-batches on the BF16 engine need C and N multiples of 8");
     c->sched = *s;
     c->k = s->k_start;
     if (s->kind == SMC_SCHED_SDA) {
@@ -445,6 +458,7 @@ smc_status smc_set_schedule(smc_ctx* c, const smc_schedule* s, smc_step_stats* s
         c->rows_a = 0;
         c->coef_a = 1.0;
         c->rows_b = std::min<int64_t>(s->C, c->N);
+        c->row_start = 0;
         c->beta = s->beta0 > 0 ? s->beta0 : 0.1;
         c->coef_b = c->beta;
     } else {
@@ -556,10 +570,10 @@ static smc_status anneal_impl(smc_ctx* c, const double* given, smc_anneal_info* 
     int appended = 0;
     c->k++;
     if (c->sched.kind != SMC_SCHED_SDA) {
-        const int64_t old_a = c->rows_a;
+        const int64_t old_a = c->rows_a, old_s = c->row_start;
         const double old_c = c->coef_a;
         set_regions_fixed(c);
-        if (c->rows_a != old_a || c->coef_a != old_c) c->target_id++;
+        if (c->rows_a != old_a || c->coef_a != old_c || c->row_start != old_s) c->target_id++;
         appended = c->rows_a > old_a;
     } else if (c->beta >= 1.0) {
         // "append an additional MB and reinitialise beta" (Sec. 3.1)
@@ -830,6 +844,7 @@ smc_status smc_restore(smc_ctx* c, const char* path) {
     c->sched = h.sched;
     c->k = (int)h.k;
     c->rows_a = h.rows_a; c->rows_b = h.rows_b;
+    c->row_start = c->sched.kind == SMC_SCHED_SDA ? 0 : subset_start(c->sched.kind, c->k, c->N, c->rows_a);
     c->coef_a = h.coef_a; c->coef_b = h.coef_b; c->beta = h.beta;
     c->target_id = h.target_id;
     c->grad_target_id = h.grad_valid ? h.target_id : ~0ull;

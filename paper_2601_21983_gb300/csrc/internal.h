@@ -151,6 +151,7 @@ struct smc_ctx {
     smc_schedule sched{};
     int k = 0;
     int64_t rows_a = 0, rows_b = 0;  // fully weighted rows, tempered block rows
+    int64_t row_start = 0;           // first row of the subset (fresh mini-batches); it wraps past N
     double coef_a = 1.0, coef_b = 0.0, beta = 1.0;
     uint64_t target_id = 0, grad_target_id = ~0ull;  // cached gradient validity
     double ess = 0.0;
@@ -168,6 +169,23 @@ struct smc_ctx {
 };
 
 namespace smc {
+
+// Rows g < split_row(c) of the current target carry coef_a, the rest coef_b:
+// SDA's fully included prefix (Sec. 3.1), or every row of a fixed schedule's
+// subset (which may start anywhere for the fresh mini-batch kinds).
+inline int64_t split_row(const smc_ctx* c) { return c->sched.kind == SMC_SCHED_SDA ? c->rows_a : c->N; }
+
+// The current subset as at most two contiguous ranges of rows: rows_a + rows_b
+// rows from row_start, wrapping past N.
+struct RowRange { int64_t first, count; };
+inline int subset_ranges(const smc_ctx* c, RowRange r[2]) {
+    const int64_t M = c->rows_a + c->rows_b;
+    const int64_t tail = M < c->N - c->row_start ? M : c->N - c->row_start;
+    int n = 0;
+    if (tail > 0) r[n++] = RowRange{c->row_start, tail};
+    if (M - tail > 0) r[n++] = RowRange{0, M - tail};
+    return n;
+}
 
 constexpr int kMaxPartChunks = 64;
 

@@ -760,7 +760,7 @@ cudaError_t launch_fused_fwd_head(smc_ctx* c, const __nv_bfloat16* x, int64_t g0
     a.T = (int64_t)a.tiles_q * a.npairs;
     a.kb_total = (int)((c->in_feat + BK - 1) / BK);
     a.g0 = g0;
-    a.rows_a = c->rows_a;
+    a.rows_a = split_row(c);
     a.ca = (float)c->coef_a;
     a.cb = (float)c->coef_b;
     a.Y = c->Y;

@@ -318,7 +318,7 @@ static cudaError_t launch_head_mma_t(smc_ctx* c, int H, int C, int mc, int64_t g
         set = smem;
     }
     SMC_LAUNCH(c, head_mma_kernel<KT, ACT><<<dim3(nsl, c->J), 128, smem, c->stream>>>(
-                      H1, ldh, H, C, mc, g0, c->rows_a, (float)c->coef_a, (float)c->coef_b, c->Y, W2, b2, act, c->dZT,
+                      H1, ldh, H, C, mc, g0, split_row(c), (float)c->coef_a, (float)c->coef_b, c->Y, W2, b2, act, c->dZT,
                       c->chunk, c->head_part, c->head_ll, slot, c->J, rows_per_slice));
     return cudaGetLastError();
 }

@@ -384,24 +384,27 @@ static void simt_forward(smc_ctx* c, const float* x, int rows) {
 smc_status simt_eval(smc_ctx* c) {
     const int J = c->J;
     const int64_t ch = c->chunk;
-    const int64_t M = c->rows_a + c->rows_b;
     cudaMemsetAsync(c->grad, 0, (size_t)c->flat * sizeof(float), c->stream);
     cudaMemsetAsync(c->la, 0, J * sizeof(double), c->stream);
     cudaMemsetAsync(c->lb, 0, J * sizeof(double), c->stream);
     const int nl = (int)c->layers.size();
     fam_begin(c, F_SIMT_NET);
-    for (int64_t g0 = 0; g0 < M; g0 += ch) {
-        const int rows = (int)std::min<int64_t>(ch, M - g0);
+    RowRange rr[2];
+    const int nr = subset_ranges(c, rr);
+    const int64_t split = split_row(c);
+    for (int r = 0; r < nr; ++r)
+    for (int64_t g0 = rr[r].first; g0 < rr[r].first + rr[r].count; g0 += ch) {
+        const int rows = (int)std::min<int64_t>(ch, rr[r].first + rr[r].count - g0);
         const float* x = c->X + g0 * c->in_feat;
         simt_forward(c, x, rows);
         // head on the last layer's outputs
         const int C = c->n_out;
         float* dl = c->delta[0];
         SMC_LAUNCH(c, head_kernel<<<nblk((int64_t)J * rows), 256, 0, c->stream>>>(
-                          c->act[nl - 1], ch * C, C, rows, J, g0, c->rows_a, (float)c->coef_a, (float)c->coef_b,
+                          c->act[nl - 1], ch * C, C, rows, J, g0, split, (float)c->coef_a, (float)c->coef_b,
                           c->Y, c->Yv, c->likelihood, (float)(1.0 / (c->noise_sigma * c->noise_sigma)),
                           (float)(0.5 * log(2.0 * M_PI * c->noise_sigma * c->noise_sigma)), c->rowll, ch, dl));
-        SMC_LAUNCH(c, region_sum_kernel<<<J, 256, 0, c->stream>>>(c->rowll, ch, rows, g0, c->rows_a, c->la, c->lb));
+        SMC_LAUNCH(c, region_sum_kernel<<<J, 256, 0, c->stream>>>(c->rowll, ch, rows, g0, split, c->la, c->lb));
         // backward: cur holds d/d(pre-activation) of layer l (parametric) or
         // d/d(output) of a pool layer
         int cur = 0;

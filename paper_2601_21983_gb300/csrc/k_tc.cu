@@ -760,9 +760,12 @@ smc_status tc_alloc(smc_ctx* c) {
     c->pair_gemm = !(envp != nullptr && envp[0] == '0');
     c->head_slices_cap = (c->N + 1023) / 1024 + 2 * (c->N / chunk + 2);
     if (c->fused) {
-        // partial slots of the fused kernel, summed over the chunks of a full pass
-        int64_t need = 0;
+        // partial slots of the fused kernel, summed over the chunks of a full
+        // pass, plus two short chunks for a subset that wraps past row N
+        int64_t need = 0, most = 0;
         for (int64_t g0 = 0; g0 < c->N; g0 += chunk) need += fused_slots(c, std::min(chunk, c->N - g0));
+        for (int64_t m = 256; m < chunk + 256; m += 256) most = std::max(most, fused_slots(c, std::min(m, chunk)));
+        need += 2 * most;
         c->head_slices_cap = std::max(c->head_slices_cap, need);
         if (cudaMalloc(&c->fimg, (size_t)fused_image_bytes(c)) != cudaSuccess) return SMC_ENOMEM;
     }
@@ -811,7 +814,8 @@ static cudaError_t launch_head(smc_ctx* c, int H, int C, int mc, int64_t g0, int
 
 // K5: dW1 (J*H x Din) = dZ1^T X over the chunk's rows (K = mc); with_b1 adds the
 // ones row of the transposed input as column Din, which yields db1 = sum dZ1.
-static cudaError_t launch_wgrad(smc_ctx* c, int64_t g0, int64_t mc, bool with_b1) {
+// first: this chunk opens the sum over the subset's rows (overwrite, not accumulate)
+static cudaError_t launch_wgrad(smc_ctx* c, int64_t g0, int64_t mc, bool with_b1, bool first) {
     const Layer& L0 = c->layers[0];
     const int64_t JH = (int64_t)c->J * L0.out_feat(), Din = c->in_feat;
     const int64_t ncol = with_b1 ? Din + 1 : Din;
@@ -830,7 +834,7 @@ static cudaError_t launch_wgrad(smc_ctx* c, int64_t g0, int64_t mc, bool with_b1
     if (g.kslices > 1) {
         g.out = c->gemm_part; g.ldo = ldp; g.slice_stride = slice; g.aug_col = -1;
     } else {
-        g.out = gW1; g.ldo = Din; g.accumulate = g0 > 0;
+        g.out = gW1; g.ldo = Din; g.accumulate = !first;
         g.aug_col = with_b1 ? (int)Din : -1;
         g.aug_out = gb1;
     }
@@ -842,7 +846,7 @@ static cudaError_t launch_wgrad(smc_ctx* c, int64_t g0, int64_t mc, bool with_b1
     if (e == cudaSuccess && g.kslices > 1) {
         const int64_t n = JH * ncol;
         SMC_LAUNCH(c, splitk_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
-                          c->gemm_part, g.kslices, slice, JH, (int)ncol, ldp, (int)Din, gW1, gb1, g0 > 0));
+                          c->gemm_part, g.kslices, slice, JH, (int)ncol, ldp, (int)Din, gW1, gb1, !first));
         e = cudaGetLastError();
     }
     fam_end(c, F_WGRAD_GEMM);
@@ -854,7 +858,6 @@ smc_status tc_eval(smc_ctx* c) {
     const Layer& L1 = c->layers[1];
     const int H = (int)L0.out_feat(), C = c->n_out;
     const int64_t Din = c->in_feat;
-    const int64_t M = c->rows_a + c->rows_b;
     const int64_t ch = c->chunk;
     const int rows_per_slice = 4096;
     int slot = 0;
@@ -865,8 +868,12 @@ smc_status tc_eval(smc_ctx* c) {
         fam_end(c, F_HEAD);
         if (e != cudaSuccess) return cuda_check(c, e, "particle images");
     }
-    for (int64_t g0 = 0; g0 < M; g0 += ch) {
-        const int64_t mc = std::min<int64_t>(ch, M - g0);
+    RowRange rr[2];
+    const int nr = subset_ranges(c, rr);
+    bool first = true;
+    for (int r = 0; r < nr; ++r)
+    for (int64_t g0 = rr[r].first; g0 < rr[r].first + rr[r].count; g0 += ch) {
+        const int64_t mc = std::min<int64_t>(ch, rr[r].first + rr[r].count - g0);
         if (c->fused) {
             // K1 + K3 in one kernel
             if (slot + fused_slots(c, mc) > c->head_slices_cap) return fail(c, SMC_EINVAL, "head partial buffer too small");
@@ -887,7 +894,8 @@ smc_status tc_eval(smc_ctx* c) {
             if (e != cudaSuccess) return cuda_check(c, e, "head kernel");
             slot += nsl;
         }
-        e = launch_wgrad(c, g0, mc, c->fused);
+        e = launch_wgrad(c, g0, mc, c->fused, first);
+        first = false;
         if (e != cudaSuccess) return cuda_check(c, e, "tcgen05 weight-gradient GEMM");
     }
     // W2 / b2 (/ b1) gradients and log-likelihood sums

@@ -19,7 +19,8 @@ ACT_TANH, ACT_RELU, ACT_IDENTITY = 0, 1, 2
 LIK_CATEGORICAL, LIK_GAUSSIAN = 0, 1
 PREC_FP32, PREC_BF16 = 0, 1
 RESAMPLE_SYSTEMATIC, RESAMPLE_MULTINOMIAL = 0, 1
-SCHED = {"constant": 0, "fb": 1, "ctr": 2, "linear": 3, "automated": 4, "sda": 5}
+SCHED = {"constant": 0, "fb": 1, "ctr": 2, "linear": 3, "automated": 4, "sda": 5, "constant_fresh": 6,
+         "ctr_fresh": 7}
 PROPOSAL_PLAIN, PROPOSAL_LEARNED, PROPOSAL_EXPLORE = 0, 1, 2
 LEARNED_NUM_PARAMS = 706
 STATUS = {0: "SMC_OK", 1: "SMC_EINVAL", 2: "SMC_ENOMEM", 3: "SMC_ECUDA", 4: "SMC_ESTATE",

@@ -120,3 +120,10 @@ def test_restore_refuses_other_runs(tmp_path):
         assert e.value.status == 1
     finally:
         S.smc_destroy(ctx)
+
+
+def test_fresh_minibatch_roundtrip(tmp_path):
+    """The window start of a fresh-mini-batch schedule follows from k, which
+    the checkpoint restores (N = 500, C = 160: the restored run wraps)."""
+    X, y = synthetic.gaussian_mixture(500, seed=36)
+    _roundtrip(tmp_path, MLP0, X, y, 16, 36, S.make_schedule("constant_fresh", 160, 160, 10), 2, 4)

@@ -523,3 +523,106 @@ def test_bf16_split_k_across_chunks():
             assert rel_err(g[j], gg) < 2e-2, j
     finally:
         S.smc_destroy(ctx)
+
+
+# ------------------------------------------------ fresh mini-batch schedules
+def _fresh_window_eval(spec, X, y, J, seed, precision, kind, C, K, n_iter, chunk, tol, std):
+    """Anneal through n_iter targets of a fresh-mini-batch schedule and compare
+    each target's evaluation (log pi, L_a, whole gradient) with the oracle."""
+    N = X.shape[0]
+    ctx, orc, _ = make_pair(spec, X, y, J, seed=seed, precision=precision, chunk=chunk)
+    wrapped = False
+    try:
+        th0 = synthetic.particles(J, spec.n_params, seed, std=std)
+        S.smc_set_state(ctx, th0)
+        S.smc_set_schedule(ctx, S.make_schedule(kind, C, C, K))
+        orc.set_schedule(kind, C, C, K, th0)
+        for k in range(n_iter):
+            if k:
+                info = S.smc_anneal_next(ctx)
+                orc.anneal_next()
+                assert info["rows"] == orc.subset_rows
+            rows = orc.rows()
+            wrapped = wrapped or bool(rows[0] > rows[-1])
+            lp, g, la, lb = S.smc_eval(ctx, J, spec.n_params)
+            rlp, rg, rla, rlb = oracle_eval(orc)
+            assert np.allclose(la, rla, rtol=tol), k
+            assert np.allclose(lp, rlp, rtol=tol), k
+            assert np.all(lb == 0.0)
+            assert _per_particle_rel(g, rg) < tol, k
+    finally:
+        S.smc_destroy(ctx)
+    return wrapped
+
+
+@pytest.mark.parametrize("kind,chunk", [("constant_fresh", 0), ("constant_fresh", 64), ("ctr_fresh", 0)])
+def test_fp32_fresh_minibatch_eval_parity(kind, chunk):
+    """N = 500 rows, C = 160: the window starts at 0, 160, 320, 480 (wrapping
+    to rows 0..139), 140, ...; CTR's late switch (k >= 0.9 K) takes all rows."""
+    X, y = _mixture(500, 37)
+    assert _fresh_window_eval(MLP0, X, y, 8, 37, S.PREC_FP32, kind, 160, 10, 10 if kind == "ctr_fresh" else 6,
+                              chunk, 1e-5, 0.3)
+
+
+@pytest.mark.parametrize("chunk", [0, 128])
+def test_bf16_fresh_minibatch_eval_parity(chunk):
+    """BF16 engine, N = 1000, C = 256: the fourth window runs from row 768 to
+    999 and wraps to rows 0..23, so the weight-gradient GEMM's first chunk is
+    not the chunk of row 0."""
+    X, y = _images(1000, 38)
+    assert _fresh_window_eval(MLP1, X, y, 8, 38, S.PREC_BF16, "constant_fresh", 256, 10, 5, chunk, 2e-2, 0.1)
+
+
+def test_fresh_minibatch_trajectory_parity():
+    """Constant with a fresh mini-batch every iteration, J = 16, 12 moves with
+    injected momenta and resampling uniforms: ESS, ancestors, particles and
+    log pi against the oracle."""
+    N, J, K, C, h, S_ = 600, 16, 12, 128, 0.01, 2
+    X, y = _mixture(N, 39)
+    ctx, orc, _ = make_pair(MLP0, X, y, J, seed=39)
+    try:
+        th0 = synthetic.particles(J, MLP0.n_params, 39)
+        S.smc_set_state(ctx, th0)
+        S.smc_set_schedule(ctx, S.make_schedule("constant_fresh", C, C, K))
+        orc.set_schedule("constant_fresh", C, C, K, th0)
+        g = rng.SplitMix64(39)
+        for k in range(1, K):
+            S.smc_anneal_next(ctx)
+            orc.anneal_next()
+            u = g.next_double()
+            S.smc_set_uniforms(ctx, [u])
+            near_tie = abs(orc.ess - J / 2) < 1e-6 * J
+            did = S.smc_resample(ctx)
+            odid = orc.resample(u=u)
+            if near_tie:
+                pytest.skip(f"ESS within 1e-6 J of J/2 at k={k}")
+            assert did == odid, k
+            if did:
+                assert np.array_equal(S.smc_get_ancestors(ctx, J), orc.ancestors), k
+            z = synthetic.normals((J, MLP0.n_params), 3900 + k)
+            S.smc_set_noise(ctx, z)
+            st = S.smc_step(ctx, h, S_)
+            orc.step(h, S_, z)
+            assert st["rows"] == C
+            assert abs(st["ess"] - orc.ess) <= 1e-4 * J, (k, st["ess"], orc.ess)
+        th, lw, lp = S.smc_get_state(ctx, J, MLP0.n_params)
+        assert _per_particle_rel(th, orc.theta) < 1e-4
+        assert np.allclose(lp, orc.logpi, rtol=1e-4)
+    finally:
+        S.smc_destroy(ctx)
+
+
+def test_bf16_fresh_minibatch_needs_aligned_sizes():
+    X, y = _images(1000, 40)
+    ctx, _, _ = make_pair(MLP1, X, y, 4, seed=40, precision=S.PREC_BF16)
+    try:
+        with pytest.raises(S.SMCError) as e:
+            S.smc_set_schedule(ctx, S.make_schedule("constant_fresh", 100, 100, 10))
+        assert e.value.status == 1
+    finally:
+        S.smc_destroy(ctx)
+    ctx, _, _ = make_pair(MLP1, X, y, 4, seed=40, precision=S.PREC_BF16)
+    try:
+        S.smc_set_schedule(ctx, S.make_schedule("constant_fresh", 1000, 1000, 10))   # M = N: no window
+    finally:
+        S.smc_destroy(ctx)
