@@ -345,6 +345,20 @@ smc_status smc_restore(smc_ctx* ctx, const char* path);
  * outputs, each may be NULL. */
 smc_status smc_eval(smc_ctx* ctx, double* logpi, float* grad_ll, double* la, double* lb);
 
+/* Device-pointer forms for callers that keep the particles on the GPU (the
+ * binding's torch.autograd.Function around the adjoint).  theta and grad are
+ * [J][D] float32 in canonical order, logpi is [J] float64, all device memory
+ * of the context's device; both calls only enqueue work on the context's
+ * stream (no host synchronisation).  smc_set_state_device overwrites the
+ * particles (log-weights and cached log pi unchanged) and invalidates the
+ * cached gradient.  smc_eval_device evaluates, under the current target,
+ * log pi(theta) (eq. approx-grad's estimate plus the prior, as in smc_eval) and
+ * its full gradient grad log pi = sum_i c_i grad log p(y_i|theta) - theta /
+ * sigma^2; either output may be NULL.  Errors: SMC_EINVAL (NULL context or
+ * theta), SMC_ESTATE (before smc_set_schedule or after a failure), SMC_ECUDA. */
+smc_status smc_set_state_device(smc_ctx* ctx, const float* theta_dev);
+smc_status smc_eval_device(smc_ctx* ctx, double* logpi_dev, float* grad_dev);
+
 /* The annealed row order (Sec. 3: mini-batches drawn without replacement):
  * perm[r] = index of the training row stored at position r, [n] int32 host. */
 smc_status smc_get_permutation(smc_ctx* ctx, int32_t* perm);

@@ -935,6 +935,26 @@ smc_status smc_eval(smc_ctx* c, double* logpi, float* grad_ll, double* la, doubl
     return cuda_check(c, e, "eval copy");
 }
 
+smc_status smc_set_state_device(smc_ctx* c, const float* theta) {
+    if (!c || !theta) return SMC_EINVAL;
+    if (!ok_ctx(c)) return SMC_ESTATE;
+    cudaError_t e = launch_canon_to_seg(c, theta, c->theta);
+    if (e == cudaSuccess) e = launch_shadow(c);
+    c->grad_target_id = ~0ull;
+    return cuda_check(c, e, "set_state_device");
+}
+
+smc_status smc_eval_device(smc_ctx* c, double* logpi, float* grad) {
+    if (!c) return SMC_EINVAL;
+    if (!ok_ctx(c) || !c->scheduled) return SMC_ESTATE;
+    smc_status st = engine_eval(c);
+    if (st != SMC_OK) return st;
+    cudaError_t e = launch_sqnorm(c, 0);
+    if (e == cudaSuccess && logpi) e = launch_eval_logpi(c, logpi);
+    if (e == cudaSuccess && grad) e = launch_grad_to_canon(c, grad);
+    return cuda_check(c, e, "eval_device");
+}
+
 smc_status smc_get_permutation(smc_ctx* c, int32_t* perm) {
     if (!c || !perm) return SMC_EINVAL;
     std::memcpy(perm, c->perm.data(), c->perm.size() * sizeof(int32_t));

@@ -217,6 +217,9 @@ cudaError_t launch_sda_moments(smc_ctx* c);
 cudaError_t launch_resample(smc_ctx* c, int kind, int nu);
 cudaError_t launch_gather(smc_ctx* c);
 cudaError_t launch_shadow(smc_ctx* c);
+cudaError_t launch_eval_logpi(smc_ctx* c, double* out);            // log pi [J] (device) at the current particles
+cudaError_t launch_canon_to_seg(smc_ctx* c, const float* canon, float* seg);
+cudaError_t launch_grad_to_canon(smc_ctx* c, float* canon);        // grad log pi, canonical [J][D] (device)
 cudaError_t launch_permute_rows(smc_ctx* c, const float* src, const int32_t* srcy, const float* srcyv,
                                 const int32_t* perm_dev);
 cudaError_t launch_bf16_data(smc_ctx* c);

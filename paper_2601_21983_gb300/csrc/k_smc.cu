@@ -607,6 +607,46 @@ cudaError_t launch_weights(smc_ctx* c, int mode) {
 
 cudaError_t launch_normalise_only(smc_ctx* c) { return launch_weights(c, 2); }
 
+cudaError_t launch_eval_logpi(smc_ctx* c, double* out) {
+    const double inv_sig2 = 1.0 / (c->prior_sigma * c->prior_sigma);
+    SMC_LAUNCH(c, weights_kernel<<<1, 1024, 0, c->stream>>>(3, c->J, c->part_chunks, c->part, c->la, c->lb,
+                                                            c->coef_a, c->coef_b, inv_sig2, c->logw, c->logpi,
+                                                            c->wn, c->stats_dev, out));
+    return cudaGetLastError();
+}
+
+// Canonical [J][D] <-> segment-major particle arrays on the device.  Block row
+// y is segment y; element i of segment s is particle i / size, parameter
+// canon[s] + i % size, stored at off[s] + i.  to_seg: seg[off + i] = canon[...].
+// Otherwise canon[...] = seg[off + i] - prior_coef * theta[off + i] (the
+// gradient of log pi from the log-likelihood gradient and the prior's term).
+__global__ void canon_seg_kernel(float* __restrict__ seg, const float* __restrict__ theta, float* __restrict__ canon,
+                                 SegTable t, int64_t D, int J, int to_seg, float prior_coef) {
+    const int s = blockIdx.y;
+    const int64_t n = (int64_t)J * t.size[s];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = i / t.size[s], k = i - j * t.size[s];
+        const int64_t ci = j * D + t.canon[s] + k, si = t.off[s] + i;
+        if (to_seg) seg[si] = canon[ci];
+        else canon[ci] = seg[si] - prior_coef * theta[si];
+    }
+}
+
+cudaError_t launch_canon_to_seg(smc_ctx* c, const float* canon, float* seg) {
+    const SegTable t = seg_table(c);
+    SMC_LAUNCH(c, canon_seg_kernel<<<dim3(c->num_sms * 4, t.n), 256, 0, c->stream>>>(
+                      seg, nullptr, const_cast<float*>(canon), t, c->D, c->J, 1, 0.0f));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_to_canon(smc_ctx* c, float* canon) {
+    const SegTable t = seg_table(c);
+    const float coef = (float)(1.0 / (c->prior_sigma * c->prior_sigma));
+    SMC_LAUNCH(c, canon_seg_kernel<<<dim3(c->num_sms * 4, t.n), 256, 0, c->stream>>>(
+                      c->grad, c->theta, canon, t, c->D, c->J, 0, coef));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sda_moments(smc_ctx* c) {
     SMC_LAUNCH(c, sda_moments_kernel<<<1, 1024, 0, c->stream>>>(c->J, c->wn, c->la, c->lb, c->stats_dev));
     return cudaGetLastError();

@@ -213,9 +213,15 @@ static __device__ __forceinline__ uint32_t mapa_shared(const void* p, uint32_t r
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(su32(p)), "r"(rank));
     return r;
 }
-// Arrive (release, cluster scope) on an mbarrier given by its shared::cluster address.
+// Arrive on an mbarrier given by its shared::cluster address, with the default
+// (CTA-scope release) semantics.  Its one use is an epilogue handing a TMEM
+// accumulator back to the MMA issuer of the pair: the tcgen05.ld reads it
+// protects have completed (tcgen05.wait::ld) and are ordered before the arrive
+// by tcgen05.fence::before_thread_sync, and no generic memory the waiter reads
+// is published through it, so a cluster-scope release (a fence that stalls the
+// warp for hundreds of cycles) orders nothing more.
 static __device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 // 2-D tiled TMA load into this CTA's shared memory whose completion is signalled
 // on an mbarrier of either CTA of the pair (shared::cluster address).

@@ -105,6 +105,8 @@ _SIGS = {
     "smc_set_noise": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smc_set_uniforms": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "smc_eval": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "smc_set_state_device": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "smc_eval_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "smc_get_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smc_get_permutation": (C.c_int, [C.c_void_p, C.c_void_p]),
     "smc_get_ancestors": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -327,6 +329,17 @@ def smc_eval(ctx, J, D):
     lb = np.empty(J, np.float64)
     _check(load().smc_eval(ctx, _ptr(lp), _ptr(g), _ptr(la), _ptr(lb)), "smc_eval", ctx)
     return lp, g, la, lb
+
+
+def smc_set_state_device(ctx, theta):
+    """Overwrite the particles from a contiguous float32 CUDA tensor [J, D]."""
+    _check(load().smc_set_state_device(ctx, _ptr(theta)), "smc_set_state_device", ctx)
+
+
+def smc_eval_device(ctx, logpi=None, grad=None):
+    """Enqueue log pi [J] (float64) and grad log pi [J, D] (float32) of the
+    current target into CUDA tensors (either may be None)."""
+    _check(load().smc_eval_device(ctx, _ptr(logpi), _ptr(grad)), "smc_eval_device", ctx)
 
 
 def smc_get_weights(ctx, J):

@@ -626,3 +626,50 @@ def test_bf16_fresh_minibatch_needs_aligned_sizes():
         S.smc_set_schedule(ctx, S.make_schedule("constant_fresh", 1000, 1000, 10))   # M = N: no window
     finally:
         S.smc_destroy(ctx)
+
+
+def test_multinomial_unscaled_trajectory_parity():
+    """The paper-faithful variants as configuration: multinomial resampling
+    (J injected uniforms) and c_i = 1 instead of N / M_k, on a Constant
+    schedule (M_k < N, so the scale matters), 10 moves with injected momenta
+    and resampling forced every third iteration: ancestors, ESS, particles
+    and log pi against the oracle."""
+    N, J, K, h, S_ = 600, 16, 10, 0.01, 2
+    X, y = _mixture(N, 55)
+    ctx, orc, _ = make_pair(MLP0, X, y, J, seed=55, scaled=False, resampler=S.RESAMPLE_MULTINOMIAL)
+    try:
+        th0 = synthetic.particles(J, MLP0.n_params, 55)
+        S.smc_set_state(ctx, th0)
+        S.smc_set_schedule(ctx, S.make_schedule("constant", 128, 128, K))
+        orc.set_schedule("constant", 128, 128, K, th0)
+        rlp0 = oracle_eval(orc)[0]
+        lp0 = S.smc_eval(ctx, J, MLP0.n_params)[0]
+        assert np.allclose(lp0, rlp0, rtol=1e-5)
+        g = rng.SplitMix64(55)
+        resampled = 0
+        for k in range(1, K):
+            S.smc_anneal_next(ctx)
+            orc.anneal_next()
+            u = [g.next_double() for _ in range(J)]
+            force = k % 3 == 0
+            S.smc_set_uniforms(ctx, u)
+            near_tie = not force and abs(orc.ess - J / 2) < 1e-6 * J
+            did = S.smc_resample(ctx, force=force)
+            odid = orc.resample(uniforms=np.array(u), kind="multinomial", force=force)
+            if near_tie:
+                pytest.skip(f"ESS within 1e-6 J of J/2 at k={k}")
+            assert did == odid, k
+            if did:
+                resampled += 1
+                assert np.array_equal(S.smc_get_ancestors(ctx, J), orc.ancestors), k
+            z = synthetic.normals((J, MLP0.n_params), 5500 + k)
+            S.smc_set_noise(ctx, z)
+            st = S.smc_step(ctx, h, S_)
+            orc.step(h, S_, z)
+            assert abs(st["ess"] - orc.ess) <= 1e-4 * J, (k, st["ess"], orc.ess)
+        assert resampled >= 3
+        th, lw, lp = S.smc_get_state(ctx, J, MLP0.n_params)
+        assert _per_particle_rel(th, orc.theta) < 1e-4
+        assert np.allclose(lp, orc.logpi, rtol=1e-4)
+    finally:
+        S.smc_destroy(ctx)
