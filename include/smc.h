@@ -234,6 +234,21 @@ smc_status smc_posterior_predict(smc_ctx* ctx, const float* x_test, int64_t n,
 smc_status smc_upload_rows(smc_ctx* ctx, int64_t row0, int64_t n,
                            const float* x, const int32_t* y_class, const float* y_value);
 
+/* smc_upload_rows without a stall: the host-to-device copy is enqueued on the
+ * context's own copy stream into a device staging buffer and the call returns
+ * at once; the rows take effect at the next smc_set_schedule or
+ * smc_anneal_next (in stream order, before that iteration's evaluations), so
+ * a caller can upload iteration k+1's rows while iteration k computes.
+ * x / y_class / y_value must stay valid and unchanged until that call has
+ * returned; pinned memory
+ * makes the copy asynchronous.  Uploads not yet applied apply in call order.
+ * Like smc_upload_rows this moves data and does not change the target: the
+ * rows are expected to carry the training set's values, and a cached
+ * gradient or log pi is kept.  Errors: SMC_EINVAL (range), SMC_ENOMEM (the
+ * first call allocates an N-row staging buffer), SMC_ECUDA. */
+smc_status smc_upload_rows_async(smc_ctx* ctx, int64_t row0, int64_t n,
+                                 const float* x, const int32_t* y_class, const float* y_value);
+
 /* ------------------------------------------ learned proposal (not in the paper) */
 
 /* Get (host out [SMC_LEARNED_NUM_PARAMS]) and/or set (host in) the proposal

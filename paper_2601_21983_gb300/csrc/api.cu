@@ -164,6 +164,15 @@ void free_all(smc_ctx* c) {
                   c->shadow, c->logw, c->wn, c->logpi, c->logpi_alt, c->la, c->lb, c->la_alt, c->lb_alt, c->part,
                   c->stats_dev, c->anc, c->u_dev, c->err_dev, c->z_inject};
     for (void* p : ps) cudaFree(p);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
+    if (c->stage_ready) cudaEventDestroy(c->stage_ready);
+    if (c->stage_free) cudaEventDestroy(c->stage_free);
+    cudaFree(c->Xstage);
+    cudaFree(c->Ystage);
+    cudaFree(c->Yvstage);
     lp_free(c);
     if (c->stats_host) cudaFreeHost(c->stats_host);
     for (auto& t : c->timers) {
@@ -442,6 +451,8 @@ void smc_destroy(smc_ctx* c) {
     delete c;
 }
 
+static cudaError_t apply_staged_rows(smc_ctx* c);
+
 smc_status smc_set_schedule(smc_ctx* c, const smc_schedule* s, smc_step_stats* stats) {
     if (!c || !s) return SMC_EINVAL;
     if (!ok_ctx(c)) return SMC_ESTATE;
@@ -451,6 +462,7 @@ smc_status smc_set_schedule(smc_ctx* c, const smc_schedule* s, smc_step_stats* s
     if ((s->kind == SMC_SCHED_CONSTANT_FRESH || s->kind == SMC_SCHED_CTR_FRESH) && c->precision == SMC_PREC_BF16 &&
         s->C < c->N && (s->C % 8 != 0 || c->N % 8 != 0))
         return fail(c, SMC_EINVAL, "fresh mini-batches on the BF16 engine need C and N multiples of 8");
+    if (cudaError_t e = apply_staged_rows(c); e != cudaSuccess) return cuda_check(c, e, "apply uploaded rows");
     c->sched = *s;
     c->k = s->k_start;
     if (s->kind == SMC_SCHED_SDA) {
@@ -568,6 +580,7 @@ static smc_status anneal_impl(smc_ctx* c, const double* given, smc_anneal_info* 
     if (!ok_ctx(c) || !c->scheduled) return SMC_ESTATE;
     const int64_t before = c->rows_a + c->rows_b;
     int appended = 0;
+    if (cudaError_t e = apply_staged_rows(c); e != cudaSuccess) return cuda_check(c, e, "apply uploaded rows");
     c->k++;
     if (c->sched.kind != SMC_SCHED_SDA) {
         const int64_t old_a = c->rows_a, old_s = c->row_start;
@@ -706,6 +719,62 @@ smc_status smc_upload_rows(smc_ctx* c, int64_t row0, int64_t n, const float* x, 
     if (e == cudaSuccess && yv) e = cudaMemcpyAsync(c->Yv + row0, yv, n * 4, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && c->precision == SMC_PREC_BF16) e = launch_bf16_data(c);
     if (e != cudaSuccess) return cuda_check(c, e, "upload rows");
+    return SMC_OK;
+}
+
+// Rows uploaded by smc_upload_rows_async take effect here, in stream order:
+// the compute stream waits for the staging copy, moves the rows into place
+// (and into the BF16 operands), then releases the staging buffer.
+static cudaError_t apply_staged_rows(smc_ctx* c) {
+    if (!c->stage_pending) return cudaSuccess;
+    c->stage_pending = false;
+    cudaError_t e = cudaStreamWaitEvent(c->stream, c->stage_ready, 0);
+    const int64_t r0 = c->stage_row0, n = c->stage_n;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->X + r0 * c->in_feat, c->Xstage + r0 * c->in_feat, (size_t)n * c->in_feat * 4,
+                            cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && c->stage_y)
+        e = cudaMemcpyAsync(c->Y + r0, c->Ystage + r0, n * 4, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && c->stage_yv)
+        e = cudaMemcpyAsync(c->Yv + r0, c->Yvstage + r0, n * 4, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && c->precision == SMC_PREC_BF16) e = launch_bf16_data(c);
+    if (e == cudaSuccess) e = cudaEventRecord(c->stage_free, c->stream);
+    return e;
+}
+
+smc_status smc_upload_rows_async(smc_ctx* c, int64_t row0, int64_t n, const float* x, const int32_t* y,
+                                 const float* yv) {
+    if (!c || !x || n < 0 || row0 < 0 || row0 + n > c->N) return SMC_EINVAL;
+    if (!ok_ctx(c)) return SMC_ESTATE;
+    if (n == 0) return SMC_OK;
+    cudaError_t e = cudaSuccess;
+    if (!c->copy_stream) {
+        e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_free, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_check(c, e, "upload staging stream");
+        if (!dalloc(c->Xstage, (size_t)c->N * c->in_feat) || !dalloc(c->Ystage, (size_t)c->N) ||
+            !dalloc(c->Yvstage, (size_t)c->N))
+            return fail(c, SMC_ENOMEM, "upload staging buffers");
+    }
+    // an upload not yet applied takes effect first, so uploads apply in call order
+    e = apply_staged_rows(c);
+    // the staging buffer is rewritten only after the last apply has read it
+    if (e == cudaSuccess && c->stage_used) e = cudaStreamWaitEvent(c->copy_stream, c->stage_free, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->Xstage + row0 * c->in_feat, x, (size_t)n * c->in_feat * 4, cudaMemcpyHostToDevice,
+                            c->copy_stream);
+    if (e == cudaSuccess && y) e = cudaMemcpyAsync(c->Ystage + row0, y, n * 4, cudaMemcpyHostToDevice, c->copy_stream);
+    if (e == cudaSuccess && yv)
+        e = cudaMemcpyAsync(c->Yvstage + row0, yv, n * 4, cudaMemcpyHostToDevice, c->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->stage_ready, c->copy_stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "upload rows (async)");
+    c->stage_pending = true;
+    c->stage_used = true;
+    c->stage_row0 = row0;
+    c->stage_n = n;
+    c->stage_y = y != nullptr;
+    c->stage_yv = yv != nullptr;
     return SMC_OK;
 }
 

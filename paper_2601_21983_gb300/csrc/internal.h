@@ -64,6 +64,15 @@ struct smc_ctx {
     double prior_sigma = 1.0, noise_sigma = 1.0;
     uint64_t seed = 0;
     cudaStream_t stream = nullptr;
+    // asynchronous row uploads: H2D copies into staging on their own stream,
+    // applied on `stream` by the next smc_anneal_next
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t stage_ready = nullptr, stage_free = nullptr;
+    float* Xstage = nullptr;
+    int32_t* Ystage = nullptr;
+    float* Yvstage = nullptr;
+    bool stage_pending = false, stage_used = false, stage_y = false, stage_yv = false;
+    int64_t stage_row0 = 0, stage_n = 0;
     int device = 0, num_sms = 148;
     int64_t particle_offset = 0;     // global index of particle 0 (sharded runs: Philox streams)
     bool timing = false;

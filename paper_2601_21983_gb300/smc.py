@@ -100,6 +100,7 @@ _SIGS = {
     "smc_resample": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
     "smc_posterior_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
     "smc_upload_rows": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "smc_upload_rows_async": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "smc_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "smc_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "smc_set_noise": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -295,6 +296,14 @@ def smc_posterior_predict(ctx, x, out):
 def smc_upload_rows(ctx, row0, x, y_class=None, y_value=None):
     _check(load().smc_upload_rows(ctx, row0, x.shape[0], _ptr(x), _ptr(y_class), _ptr(y_value)),
            "smc_upload_rows", ctx)
+
+
+def smc_upload_rows_async(ctx, row0, x, y_class=None, y_value=None):
+    """Enqueue the rows' host-to-device copy and return at once; they take
+    effect at the next smc_set_schedule / smc_anneal_next.  The caller keeps
+    x / y alive (and unchanged) until then; pinned arrays copy asynchronously."""
+    _check(load().smc_upload_rows_async(ctx, row0, x.shape[0], _ptr(x), _ptr(y_class), _ptr(y_value)),
+           "smc_upload_rows_async", ctx)
 
 
 def smc_get_state(ctx, J, D, theta=True):
