@@ -668,8 +668,7 @@ smc_status smc_resample(smc_ctx* c, int32_t force, int32_t* did) {
     std::swap(c->logpi, c->logpi_alt);
     std::swap(c->la, c->la_alt);
     std::swap(c->lb, c->lb_alt);
-    e = launch_shadow(c);
-    if (e != cudaSuccess) return cuda_check(c, e, "shadow");
+    // (the gather has rewritten the BF16 shadow of the first layer's weights)
     smc_status st = sync_and_check(c, "resample");   // u is a stack buffer
     if (st != SMC_OK) return st;
     c->ess = (double)c->J;

@@ -443,18 +443,48 @@ __global__ void __launch_bounds__(1024) resample_kernel(const double* __restrict
 }
 
 // Particle gather by ancestor: theta, cached gradient and per-particle scalars.
+// New particle j takes the arrays of its ancestor anc[j] (theta and the cached
+// gradient), 16 bytes per access where the segment size allows it (segment
+// offsets are 64-element aligned).  With sh != nullptr, segment sh_seg's BF16
+// shadow [J][size] is written from the gathered values on the way (the same
+// round-to-nearest-even conversion as shadow_kernel).
 __global__ void gather_kernel(const float* __restrict__ th_src, float* __restrict__ th_dst,
                               const float* __restrict__ g_src, float* __restrict__ g_dst, SegTable t,
-                              const int32_t* __restrict__ anc, int nchunks) {
+                              const int32_t* __restrict__ anc, int nchunks, __nv_bfloat16* __restrict__ sh,
+                              int sh_seg) {
     const int j = blockIdx.y, ch = blockIdx.x;
     const int a = anc[j];
     for (int s = 0; s < t.n; ++s) {
         const int64_t size = t.size[s];
-        const int64_t lo = size * ch / nchunks, hi = size * (ch + 1) / nchunks;
         const int64_t dst = t.off[s] + (int64_t)j * size, src = t.off[s] + (int64_t)a * size;
-        for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
-            th_dst[dst + e] = th_src[src + e];
-            g_dst[dst + e] = g_src[src + e];
+        __nv_bfloat16* shd = (sh != nullptr && s == sh_seg) ? sh + (int64_t)j * size : nullptr;
+        if ((size & 3) == 0) {
+            const int64_t n4 = size >> 2;
+            const int64_t lo = n4 * ch / nchunks, hi = n4 * (ch + 1) / nchunks;
+            const float4* ts = reinterpret_cast<const float4*>(th_src + src);
+            const float4* gs = reinterpret_cast<const float4*>(g_src + src);
+            float4* td = reinterpret_cast<float4*>(th_dst + dst);
+            float4* gd = reinterpret_cast<float4*>(g_dst + dst);
+            for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+                const float4 v = ts[e];
+                td[e] = v;
+                gd[e] = gs[e];
+                if (shd) {
+                    const __nv_bfloat162 p0 = __floats2bfloat162_rn(v.x, v.y), p1 = __floats2bfloat162_rn(v.z, v.w);
+                    uint2 pk;
+                    pk.x = *reinterpret_cast<const uint32_t*>(&p0);
+                    pk.y = *reinterpret_cast<const uint32_t*>(&p1);
+                    reinterpret_cast<uint2*>(shd)[e] = pk;
+                }
+            }
+        } else {
+            const int64_t lo = size * ch / nchunks, hi = size * (ch + 1) / nchunks;
+            for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+                const float v = th_src[src + e];
+                th_dst[dst + e] = v;
+                g_dst[dst + e] = g_src[src + e];
+                if (shd) shd[e] = __float2bfloat16_rn(v);
+            }
         }
     }
 }
@@ -660,8 +690,12 @@ cudaError_t launch_resample(smc_ctx* c, int kind, int) {
 cudaError_t launch_gather(smc_ctx* c) {
     const int nch = part_chunks_for(c);
     dim3 grid(nch, c->J);
+    // the BF16 engine's first-layer shadow follows the gathered weights
+    const bool shadow = c->precision == SMC_PREC_BF16 && c->shadow != nullptr;
     SMC_LAUNCH(c, gather_kernel<<<grid, 256, 0, c->stream>>>(c->theta, c->theta_alt, c->grad, c->grad_alt,
-                                                             seg_table(c), c->anc, nch));
+                                                             seg_table(c), c->anc, nch,
+                                                             shadow ? c->shadow : nullptr,
+                                                             shadow ? c->layers[0].seg_w : -1));
     SMC_LAUNCH(c, gather_scalars_kernel<<<(c->J + 255) / 256, 256, 0, c->stream>>>(
                       c->J, c->anc, c->logpi, c->logpi_alt, c->la, c->la_alt, c->lb, c->lb_alt, c->logw, c->wn));
     return cudaGetLastError();

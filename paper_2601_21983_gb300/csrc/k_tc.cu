@@ -99,24 +99,39 @@ __device__ __forceinline__ void epi_store(const GemmArgs& g, int row, int col0, 
         }
         return;
     }
-    // EPI_F32
-    if (g.kslices > 1) {
-        float* o = (float*)g.out + (int64_t)ks * g.slice_stride + (int64_t)row * g.ldo;
-        for (int q = 0; q < ncols; ++q) {
-            const int cc = col0 + q;
-            if (cc < g.N) o[cc] = __uint_as_float(r[q]);
-        }
-        return;
-    }
-    float* o = (float*)g.out + (int64_t)row * g.ldo;
-    const int nmain = (g.aug_col >= 0) ? g.aug_col : g.N;
-    for (int q = 0; q < ncols; ++q) {
+    // EPI_F32.  Each thread owns one output row, so a warp's store touches 32
+    // rows: full 8-column groups go out as two 16-byte stores (one whole
+    // 32-byte sector per row) instead of eight 4-byte ones; ragged or
+    // unaligned groups and the augmented column take the scalar path.
+    const bool partial = g.kslices > 1;
+    float* o = (float*)g.out + (partial ? (int64_t)ks * g.slice_stride : 0) + (int64_t)row * g.ldo;
+    const int nmain = partial ? g.N : ((g.aug_col >= 0) ? g.aug_col : g.N);
+    const bool acc = !partial && g.accumulate;
+    for (int q = 0; q < ncols; q += 8) {
         const int cc = col0 + q;
-        const float v = __uint_as_float(r[q]);
-        if (cc < nmain) {
-            o[cc] = g.accumulate ? o[cc] + v : v;
-        } else if (cc == g.aug_col) {
-            g.aug_out[row] = g.accumulate ? g.aug_out[row] + v : v;
+        if (q + 8 <= ncols && cc + 8 <= nmain && ((reinterpret_cast<uintptr_t>(o + cc) & 15) == 0)) {
+            float4 v0 = make_float4(__uint_as_float(r[q]), __uint_as_float(r[q + 1]), __uint_as_float(r[q + 2]),
+                                    __uint_as_float(r[q + 3]));
+            float4 v1 = make_float4(__uint_as_float(r[q + 4]), __uint_as_float(r[q + 5]), __uint_as_float(r[q + 6]),
+                                    __uint_as_float(r[q + 7]));
+            float4* p = reinterpret_cast<float4*>(o + cc);
+            if (acc) {
+                const float4 a0 = p[0], a1 = p[1];
+                v0 = make_float4(a0.x + v0.x, a0.y + v0.y, a0.z + v0.z, a0.w + v0.w);
+                v1 = make_float4(a1.x + v1.x, a1.y + v1.y, a1.z + v1.z, a1.w + v1.w);
+            }
+            p[0] = v0;
+            p[1] = v1;
+            continue;
+        }
+        for (int e = q; e < q + 8 && e < ncols; ++e) {
+            const int c = col0 + e;
+            const float v = __uint_as_float(r[e]);
+            if (c < nmain) {
+                o[c] = acc ? o[c] + v : v;
+            } else if (!partial && c == g.aug_col) {
+                g.aug_out[row] = acc ? g.aug_out[row] + v : v;
+            }
         }
     }
 }
