@@ -305,9 +305,10 @@ def run_tta(args):
 
 def run_grid(args):
     """The scheme grid of Sec. 4 (Table 1) on the MNIST-shaped stand-in: every
-    data-annealing scheme (Sec. 3.1: Constant, FB, CTR, Linear, Automated, SDA)
-    x {LD (S = 1), HMC (S = 3)} from the same seed for K iterations, C = kappa =
-    the mini-batch size.  Runtime = GPU-synchronous wall time over the
+    data-annealing scheme (Sec. 3.1: Constant, FB, CTR, Linear, Automated, SDA,
+    and Constant / CTR with a fresh mini-batch per iteration) x {LD (S = 1),
+    HMC (S = 3)} from the same seed for K iterations, C = kappa = the
+    mini-batch size.  Runtime = GPU-synchronous wall time over the
     iterations (test evaluation excluded); then the posterior-predictive
     accuracy and NLL on a separate test draw."""
     import torch
@@ -324,7 +325,7 @@ def run_grid(args):
     K, mb = args.grid_iters, args.grid_mb
     rows = []
     for kernel, steps in [("LD", 1), ("HMC", S_LF)]:
-        for scheme in ["constant", "fb", "ctr", "linear", "automated", "sda"]:
+        for scheme in ["constant", "fb", "ctr", "linear", "automated", "sda", "constant_fresh", "ctr_fresh"]:
             ctx = S.smc_init(model, Xd, y_class=yd, cfg=S.make_config(args.J, 7, S.PREC_BF16, stream=stream))
             S.smc_set_schedule(ctx, S.make_schedule(scheme, mb, mb, K, delta_s=1.0))
             torch.cuda.synchronize()

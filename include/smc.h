@@ -193,10 +193,7 @@ int64_t smc_num_params(const smc_ctx* ctx);
  * particles and set log w_0 = log pi_0(theta) - log q_0(theta), i.e. the
  * coefficient-weighted log-likelihood (eq. init_weight); then normalise
  * (eq. normalise) and compute the ESS (eq. jeff).  `stats` may be NULL.
- * Errors: SMC_EINVAL (C < 1, kappa < 1, K < 1; a fresh mini-batch kind on
- * the BF16 engine with C < N unless C and N are multiples of 8, since the
- * weight-gradient GEMM reads its rows from a 16-byte aligned offset),
- * SMC_ENUMERIC. */
+ * Errors: SMC_EINVAL (C < 1, kappa < 1, K < 1), SMC_ENUMERIC. */
 smc_status smc_set_schedule(smc_ctx* ctx, const smc_schedule* sched, smc_step_stats* stats);
 
 /* One move + reweight under the current target pi_k (Sec. 2.1):

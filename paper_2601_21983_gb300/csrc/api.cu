@@ -459,9 +459,6 @@ smc_status smc_set_schedule(smc_ctx* c, const smc_schedule* s, smc_step_stats* s
     if (s->kind < SMC_SCHED_CONSTANT || s->kind > SMC_SCHED_CTR_FRESH || s->C < 1 || s->kappa < 1 || s->K < 1 ||
         s->k_start < 0)
         return fail(c, SMC_EINVAL, "schedule arguments");
-    if ((s->kind == SMC_SCHED_CONSTANT_FRESH || s->kind == SMC_SCHED_CTR_FRESH) && c->precision == SMC_PREC_BF16 &&
-        s->C < c->N && (s->C % 8 != 0 || c->N % 8 != 0))
-        return fail(c, SMC_EINVAL, "fresh mini-batches on the BF16 engine need C and N multiples of 8");
     if (cudaError_t e = apply_staged_rows(c); e != cudaSuccess) return cuda_check(c, e, "apply uploaded rows");
     c->sched = *s;
     c->k = s->k_start;

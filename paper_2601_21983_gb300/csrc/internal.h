@@ -161,6 +161,7 @@ struct smc_ctx {
     int k = 0;
     int64_t rows_a = 0, rows_b = 0;  // fully weighted rows, tempered block rows
     int64_t row_start = 0;           // first row of the subset (fresh mini-batches); it wraps past N
+    int chunk_lo = 0;                // BF16 engine: leading rows of the current chunk outside the subset
     double coef_a = 1.0, coef_b = 0.0, beta = 1.0;
     uint64_t target_id = 0, grad_target_id = ~0ull;  // cached gradient validity
     double ess = 0.0;

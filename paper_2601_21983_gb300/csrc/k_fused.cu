@@ -114,6 +114,7 @@ struct FusedArgs {
     int64_t T;              // units = npairs * tiles_q
     int kb_total;
     int64_t g0;             // global row of the chunk's first row
+    int lo;                 // rows [0, lo) of the chunk lie before the subset: zero dlogits, no log-likelihood
     int64_t rows_a;         // rows < rows_a carry coefficient ca, the rest cb
     float ca, cb;
     const int32_t* Y;
@@ -344,7 +345,7 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
 #pragma unroll
                     for (int half = 0; half < 2; ++half) {
                         const int m = tile0 + 16 * mt + g + 8 * half;
-                        ylab[mt][half] = (active && m < a.M) ? a.Y[a.g0 + m] : -1;
+                        ylab[mt][half] = (active && m >= a.lo && m < a.M) ? a.Y[a.g0 + m] : -1;
                     }
                 if (!mbar_wait(tfull + acc, aph, abort_flag)) { ok = false; break; }
                 tc_fence_after();
@@ -418,7 +419,7 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
 #pragma unroll
                     for (int half = 0; half < 2; ++half) {
                         const int m = r0 + g + 8 * half;
-                        const bool valid = m < a.M;
+                        const bool valid = m >= a.lo && m < a.M;
                         float z[4];
                         z[0] = (cz[0][0][2 * half] + cz[1][0][2 * half]) + b2r[0];
                         z[1] = (cz[0][0][2 * half + 1] + cz[1][0][2 * half + 1]) + b2r[1];
@@ -760,6 +761,7 @@ cudaError_t launch_fused_fwd_head(smc_ctx* c, const __nv_bfloat16* x, int64_t g0
     a.T = (int64_t)a.tiles_q * a.npairs;
     a.kb_total = (int)((c->in_feat + BK - 1) / BK);
     a.g0 = g0;
+    a.lo = c->chunk_lo;
     a.rows_a = split_row(c);
     a.ca = (float)c->coef_a;
     a.cb = (float)c->coef_b;

@@ -25,7 +25,7 @@ using namespace mm;
 // ACT: activation of the hidden layer (SMC_ACT_*).
 template <int KT, int ACT>
 __global__ void __launch_bounds__(128) head_mma_kernel(
-    const __nv_bfloat16* __restrict__ H1, int64_t ldh, int H, int C, int rows, int64_t g0, int64_t rows_a,
+    const __nv_bfloat16* __restrict__ H1, int64_t ldh, int H, int C, int rows, int lo, int64_t g0, int64_t rows_a,
     float ca, float cb, const int32_t* __restrict__ Y, const float* __restrict__ W2, const float* __restrict__ b2,
     int act, __nv_bfloat16* __restrict__ dZT, int64_t ldz, float* __restrict__ part_w, double* __restrict__ part_l,
     int slot_base, int J, int rows_per_slice) {
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(128) head_mma_kernel(
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 const int m = tile0 + 16 * mt + g + 8 * half;
-                ylab[mt][half] = (m < r_end) ? Y[g0 + m] : -1;
+                ylab[mt][half] = (m >= lo && m < r_end) ? Y[g0 + m] : -1;
             }
         __syncwarp();
 #pragma unroll
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(128) head_mma_kernel(
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 const int m = tile0 + r0 + g + 8 * half;
-                const bool valid = m < r_end;
+                const bool valid = m >= lo && m < r_end;
                 float z[4];
                 z[0] = cz[0][2 * half] + bs[cls[0]];
                 z[1] = cz[0][2 * half + 1] + bs[cls[1]];
@@ -318,7 +318,7 @@ static cudaError_t launch_head_mma_t(smc_ctx* c, int H, int C, int mc, int64_t g
         set = smem;
     }
     SMC_LAUNCH(c, head_mma_kernel<KT, ACT><<<dim3(nsl, c->J), 128, smem, c->stream>>>(
-                      H1, ldh, H, C, mc, g0, split_row(c), (float)c->coef_a, (float)c->coef_b, c->Y, W2, b2, act, c->dZT,
+                      H1, ldh, H, C, mc, c->chunk_lo, g0, split_row(c), (float)c->coef_a, (float)c->coef_b, c->Y, W2, b2, act, c->dZT,
                       c->chunk, c->head_part, c->head_ll, slot, c->J, rows_per_slice));
     return cudaGetLastError();
 }

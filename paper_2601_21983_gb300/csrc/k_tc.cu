@@ -775,12 +775,12 @@ smc_status tc_alloc(smc_ctx* c) {
     c->pair_gemm = !(envp != nullptr && envp[0] == '0');
     c->head_slices_cap = (c->N + 1023) / 1024 + 2 * (c->N / chunk + 2);
     if (c->fused) {
-        // partial slots of the fused kernel, summed over the chunks of a full
-        // pass, plus two short chunks for a subset that wraps past row N
-        int64_t need = 0, most = 0;
-        for (int64_t g0 = 0; g0 < c->N; g0 += chunk) need += fused_slots(c, std::min(chunk, c->N - g0));
+        // partial slots of the fused kernel: a subset is at most two row ranges
+        // (it wraps past row N), each chunked from at most 7 rows before its
+        // start, so it takes at most ceil(N / chunk) + 2 chunks
+        int64_t most = 0;
         for (int64_t m = 256; m < chunk + 256; m += 256) most = std::max(most, fused_slots(c, std::min(m, chunk)));
-        need += 2 * most;
+        const int64_t need = ((c->N + chunk - 1) / chunk + 2) * most;
         c->head_slices_cap = std::max(c->head_slices_cap, need);
         if (cudaMalloc(&c->fimg, (size_t)fused_image_bytes(c)) != cudaSuccess) return SMC_ENOMEM;
     }
@@ -877,18 +877,25 @@ smc_status tc_eval(smc_ctx* c) {
     const int rows_per_slice = 4096;
     int slot = 0;
     cudaError_t e;
+    c->chunk_lo = 0;
     if (c->fused) {
         fam_begin(c, F_HEAD);
         e = launch_fused_images(c);
         fam_end(c, F_HEAD);
         if (e != cudaSuccess) return cuda_check(c, e, "particle images");
     }
+    // Each range of the subset in chunks of at most ch rows.  The weight-gradient
+    // GEMM reads its rows through TMA from a 16-byte aligned column of the
+    // transposed input, so a range starting off an 8-row boundary begins its
+    // first chunk at the boundary below and marks the rows before the range
+    // invalid (chunk_lo): zero dlogits, hence zero dZ1 rows in the contraction.
     RowRange rr[2];
     const int nr = subset_ranges(c, rr);
     bool first = true;
     for (int r = 0; r < nr; ++r)
-    for (int64_t g0 = rr[r].first; g0 < rr[r].first + rr[r].count; g0 += ch) {
-        const int64_t mc = std::min<int64_t>(ch, rr[r].first + rr[r].count - g0);
+    for (int64_t g0 = rr[r].first & ~(int64_t)7, end = rr[r].first + rr[r].count; g0 < end;) {
+        const int64_t mc = std::min<int64_t>(ch, end - g0);
+        c->chunk_lo = (int)std::max<int64_t>(0, rr[r].first - g0);
         if (c->fused) {
             // K1 + K3 in one kernel
             if (slot + fused_slots(c, mc) > c->head_slices_cap) return fail(c, SMC_EINVAL, "head partial buffer too small");
@@ -912,7 +919,9 @@ smc_status tc_eval(smc_ctx* c) {
         e = launch_wgrad(c, g0, mc, c->fused, first);
         first = false;
         if (e != cudaSuccess) return cuda_check(c, e, "tcgen05 weight-gradient GEMM");
+        g0 += mc;
     }
+    c->chunk_lo = 0;
     // W2 / b2 (/ b1) gradients and log-likelihood sums
     const int nb1 = c->fused ? 0 : H;
     const int per = C * H + C + nb1;

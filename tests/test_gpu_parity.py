@@ -612,20 +612,17 @@ def test_fresh_minibatch_trajectory_parity():
         S.smc_destroy(ctx)
 
 
-def test_bf16_fresh_minibatch_needs_aligned_sizes():
+@pytest.mark.parametrize("fused", [True, False])
+def test_bf16_fresh_minibatch_unaligned_windows(monkeypatch, fused):
+    """BF16 engine, N = 1000, C = 300, chunks of 128 rows: windows start at
+    rows 0, 300, 600 and 900 (wrapping to 0..199), two of them off the 8-row
+    boundary the weight-gradient GEMM's TMA source needs, so their first
+    chunk begins up to 7 rows early with those rows masked out; fused and
+    separate head kernels."""
+    if not fused:
+        monkeypatch.setenv("SMC_FUSED_HEAD", "0")
     X, y = _images(1000, 40)
-    ctx, _, _ = make_pair(MLP1, X, y, 4, seed=40, precision=S.PREC_BF16)
-    try:
-        with pytest.raises(S.SMCError) as e:
-            S.smc_set_schedule(ctx, S.make_schedule("constant_fresh", 100, 100, 10))
-        assert e.value.status == 1
-    finally:
-        S.smc_destroy(ctx)
-    ctx, _, _ = make_pair(MLP1, X, y, 4, seed=40, precision=S.PREC_BF16)
-    try:
-        S.smc_set_schedule(ctx, S.make_schedule("constant_fresh", 1000, 1000, 10))   # M = N: no window
-    finally:
-        S.smc_destroy(ctx)
+    assert _fresh_window_eval(MLP1, X, y, 4, 40, S.PREC_BF16, "constant_fresh", 300, 10, 4, 128, 2e-2, 0.1)
 
 
 def test_multinomial_unscaled_trajectory_parity():
