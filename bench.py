@@ -469,8 +469,15 @@ def main():
             evals[0] += st["grad_evals"] * st["rows"] * args.J
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-        e2e = {"value": evals[0] / el, "unit": UNIT, "h2d_bytes_per_step": int(hxn.nbytes + hyn.nbytes),
-               "d2h_bytes_per_step": 16 * 8 + 2 * 4}
+        e2e_evals = evals[0]
+        if dist:   # whole job: every rank's evaluations over the slowest rank's time
+            te = torch.tensor([el], dtype=torch.float64, device="cuda")
+            ee = torch.tensor([float(e2e_evals)], dtype=torch.float64, device="cuda")
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+            dist.all_reduce(ee, op=dist.ReduceOp.SUM)
+            el, e2e_evals = te.item(), ee.item()
+        e2e = {"value": e2e_evals / el, "unit": UNIT, "h2d_bytes_per_step": int(hxn.nbytes + hyn.nbytes) * world,
+               "d2h_bytes_per_step": (16 * 8 + 2 * 4) * world}
 
     # ---- per-kernel-family times for the roofline (separate pass, events per launch)
     roof = None
