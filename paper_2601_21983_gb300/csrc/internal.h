@@ -143,6 +143,7 @@ struct smc_ctx {
     std::vector<uint8_t*> pool_idx;  // SIMT: argmax per pool layer
     float* delta[2] = {nullptr, nullptr};
     float* rowll = nullptr;          // [J][chunk]
+    float* conv_part = nullptr;      // SIMT: per-slice partial weight gradients of the largest conv layer
     // BF16 engine workspace
     __nv_bfloat16* H1 = nullptr;     // [chunk_pad][J*H]
     __nv_bfloat16* dZT = nullptr;    // [J*H][chunk_pad]
@@ -227,6 +228,17 @@ cudaError_t launch_sda_moments(smc_ctx* c);
 cudaError_t launch_resample(smc_ctx* c, int kind, int nu);
 cudaError_t launch_gather(smc_ctx* c);
 cudaError_t launch_shadow(smc_ctx* c);
+
+// ----- convolution layers of the FP32 engine as shared-memory implicit GEMMs (k_conv.cu)
+bool conv_fits(const smc_ctx* c, const Layer& L);     // the layer's tiles fit in shared memory
+int conv_wgrad_slices(const smc_ctx* c);               // sample slices of the weight gradient
+size_t conv_wgrad_partial_floats(const smc_ctx* c, int cin, int cout, int k);
+cudaError_t launch_conv_forward(smc_ctx* c, const Layer& L, const float* in, int64_t in_sj, float* out,
+                                int64_t out_sj, int rows);
+cudaError_t launch_conv_data_grad(smc_ctx* c, const Layer& L, const float* dz, int64_t dz_sj, float* din,
+                                  const float* T, int64_t din_sj, int tact, int rows);
+cudaError_t launch_conv_weight_grad(smc_ctx* c, const Layer& L, const float* dz, int64_t dz_sj, const float* in,
+                                    int64_t in_sj, int rows, float* partial);
 cudaError_t launch_eval_logpi(smc_ctx* c, double* out);            // log pi [J] (device) at the current particles
 cudaError_t launch_canon_to_seg(smc_ctx* c, const float* canon, float* seg);
 cudaError_t launch_grad_to_canon(smc_ctx* c, float* canon);        // grad log pi, canonical [J][D] (device)

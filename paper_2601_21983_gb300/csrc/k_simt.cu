@@ -334,6 +334,11 @@ smc_status simt_alloc(smc_ctx* c) {
     }
     for (int b = 0; b < 2; ++b)
         if (cudaMalloc(&c->delta[b], (int64_t)c->J * chunk * maxf * sizeof(float)) != cudaSuccess) return SMC_ENOMEM;
+    size_t part = 0;
+    for (auto& L : c->layers)
+        if (L.kind == SMC_LAYER_CONV && conv_fits(c, L))
+            part = std::max(part, conv_wgrad_partial_floats(c, L.in_c, L.out_c, L.ksize));
+    if (part > 0 && cudaMalloc(&c->conv_part, part * sizeof(float)) != cudaSuccess) return SMC_ENOMEM;
     if (cudaMalloc(&c->rowll, (int64_t)c->J * chunk * sizeof(float)) != cudaSuccess) return SMC_ENOMEM;
     return SMC_OK;
 }
@@ -346,10 +351,12 @@ void simt_free(smc_ctx* c) {
     for (int b = 0; b < 2; ++b) { cudaFree(c->delta[b]); c->delta[b] = nullptr; }
     cudaFree(c->rowll);
     c->rowll = nullptr;
+    cudaFree(c->conv_part);
+    c->conv_part = nullptr;
 }
 
 // forward over `rows` rows of x (shared input, row stride in_feat); returns in c->act
-static void simt_forward(smc_ctx* c, const float* x, int rows) {
+static cudaError_t simt_forward(smc_ctx* c, const float* x, int rows) {
     const int J = c->J;
     const int64_t ch = c->chunk;
     for (size_t l = 0; l < c->layers.size(); ++l) {
@@ -367,6 +374,9 @@ static void simt_forward(smc_ctx* c, const float* x, int rows) {
             g.R = rows; g.Cn = (int)L.out_feat(); g.K = (int)L.in_feat();
             g.epi = 0; g.act = L.act; g.bias = c->theta + sb.off; g.bias_sj = sb.size;
             sgemm(c, g, J);
+        } else if (L.kind == SMC_LAYER_CONV && conv_fits(c, L)) {
+            cudaError_t e = launch_conv_forward(c, L, in, in_sj, out, ch * L.out_feat(), rows);
+            if (e != cudaSuccess) return e;
         } else if (L.kind == SMC_LAYER_CONV) {
             ConvShape s{L.in_c, L.in_h, L.in_w, L.out_c, L.out_h, L.out_w, L.ksize};
             const int64_t tot = (int64_t)J * rows * L.out_feat();
@@ -379,6 +389,7 @@ static void simt_forward(smc_ctx* c, const float* x, int rows) {
                               in, ch * L.in_feat(), out, c->pool_idx[l], ch * L.out_feat(), per, J, L.in_h, L.in_w));
         }
     }
+    return cudaGetLastError();
 }
 
 smc_status simt_eval(smc_ctx* c) {
@@ -396,7 +407,7 @@ smc_status simt_eval(smc_ctx* c) {
     for (int64_t g0 = rr[r].first; g0 < rr[r].first + rr[r].count; g0 += ch) {
         const int rows = (int)std::min<int64_t>(ch, rr[r].first + rr[r].count - g0);
         const float* x = c->X + g0 * c->in_feat;
-        simt_forward(c, x, rows);
+        if (cudaError_t e = simt_forward(c, x, rows); e != cudaSuccess) return cuda_check(c, e, "forward");
         // head on the last layer's outputs
         const int C = c->n_out;
         float* dl = c->delta[0];
@@ -437,6 +448,14 @@ smc_status simt_eval(smc_ctx* c) {
                     h.T = c->act[l - 1];
                     sgemm(c, h, J);
                 }
+            } else if (L.kind == SMC_LAYER_CONV && conv_fits(c, L)) {
+                cudaError_t e = launch_conv_weight_grad(c, L, dcur, ch * L.out_feat(), in, in_sj, rows, c->conv_part);
+                if (e == cudaSuccess && l > 0) {
+                    const int ta = (c->layers[l - 1].kind == SMC_LAYER_MAXPOOL2) ? SMC_ACT_IDENTITY : tact;
+                    e = launch_conv_data_grad(c, L, dcur, ch * L.out_feat(), dnext, c->act[l - 1], ch * L.in_feat(),
+                                              ta, rows);
+                }
+                if (e != cudaSuccess) return cuda_check(c, e, "convolution backward");
             } else if (L.kind == SMC_LAYER_CONV) {
                 ConvShape s{L.in_c, L.in_h, L.in_w, L.out_c, L.out_h, L.out_w, L.ksize};
                 const Segment& sw = c->segs[L.seg_w];
@@ -463,6 +482,7 @@ smc_status simt_eval(smc_ctx* c) {
         }
     }
     fam_end(c, F_SIMT_NET);
+    if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return cuda_check(c, e, "FP32 network");
     return SMC_OK;
 }
 
@@ -471,8 +491,9 @@ smc_status simt_predict(smc_ctx* c, const float* x, int64_t n, float* out) {
     const int nl = (int)c->layers.size();
     for (int64_t g0 = 0; g0 < n; g0 += ch) {
         const int rows = (int)std::min<int64_t>(ch, n - g0);
-        simt_forward(c, x + g0 * c->in_feat, rows);
-        cudaError_t e = launch_predict_reduce(c, c->act[nl - 1], ch * c->n_out, c->n_out, rows, out + g0 * c->n_out,
+        cudaError_t e = simt_forward(c, x + g0 * c->in_feat, rows);
+        if (e != cudaSuccess) return cuda_check(c, e, "forward (predict)");
+        e = launch_predict_reduce(c, c->act[nl - 1], ch * c->n_out, c->n_out, rows, out + g0 * c->n_out,
                                               nullptr);
         if (e != cudaSuccess) return cuda_check(c, e, "predict_reduce");
     }
