@@ -319,6 +319,7 @@ cudaError_t corr_dispatch(smc_ctx* c, CorrArgs& a) {
     a.spb = (int)std::max<int64_t>(1, (a.rows + per_j - 1) / per_j);
     if (need <= 4) return corr_launch<MODE, 4>(c, a, smem);
     if (need <= 8) return corr_launch<MODE, 8>(c, a, smem);
+    if (need <= 13) return corr_launch<MODE, 13>(c, a, smem);   // 28 x 28 outputs over 64 position threads
     return corr_launch<MODE, 16>(c, a, smem);
 }
 

@@ -215,49 +215,48 @@ __global__ void conv_bwd_bias_kernel(const float* __restrict__ dz, int64_t dz_sj
 }
 
 // 2x2 max pool, stride 2; window order (0,0),(0,1),(1,0),(1,1), first maximum wins.
+// 2x2 max pool, stride 2; window order (0,0),(0,1),(1,0),(1,1), first maximum
+// wins.  One thread per pooled output o of particle blockIdx.y; per_out =
+// rows x channels x Ho x Wo (below 2^31 per particle).
 __global__ void pool_fwd_kernel(const float* __restrict__ in, int64_t in_sj, float* __restrict__ out,
-                                uint8_t* __restrict__ idx, int64_t out_sj, int64_t per_j, int J, int H, int W) {
-    const int64_t tt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (tt >= per_j * J) return;
-    const int j = (int)(tt / per_j);
-    const int64_t t = tt - (int64_t)j * per_j;     // (m, c, y, x) within particle j
+                                uint8_t* __restrict__ idx, int64_t out_sj, int per_out, int H, int W) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= per_out) return;
+    const int j = blockIdx.y;
     const int Ho = H / 2, Wo = W / 2;
-    const int x = (int)(t % Wo), y = (int)((t / Wo) % Ho);
-    const int64_t plane = t / ((int64_t)Ho * Wo);   // (m, c) flattened
-    const float* p = in + j * in_sj + plane * H * W + (int64_t)(2 * y) * W + 2 * x;
-    out += j * out_sj;
-    idx += j * out_sj;
+    const int xo = o % Wo, r = o / Wo, yo = r % Ho, plane = r / Ho;   // plane = (sample, channel)
+    const float* p = in + j * in_sj + (int64_t)plane * H * W + (2 * yo) * W + 2 * xo;
     float best = p[0];
     int bi = 0;
     if (p[1] > best) { best = p[1]; bi = 1; }
     if (p[W] > best) { best = p[W]; bi = 2; }
     if (p[W + 1] > best) { best = p[W + 1]; bi = 3; }
-    out[t] = best;
-    idx[t] = (uint8_t)bi;
+    out[j * out_sj + o] = best;
+    idx[j * out_sj + o] = (uint8_t)bi;
 }
 
-// d_in = scatter of d_out to the argmax, times act'(T) of the pool's input
+// d_in = d_out at the argmax of each window, 0 elsewhere, times act'(T) of the
+// pool's input.  One thread per pooled output writes its window (and, on the
+// last pooled row / column of an odd-sized input, the leftover input row /
+// column, which no window covers).
 __global__ void pool_bwd_kernel(const float* __restrict__ dout, const uint8_t* __restrict__ idx, int64_t out_sj,
-                                float* __restrict__ din, const float* __restrict__ T, int64_t in_sj, int64_t per_j,
-                                int J, int H, int W, int tact) {
-    const int64_t tt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (tt >= per_j * J) return;
-    const int j = (int)(tt / per_j);
-    const int64_t t = tt - (int64_t)j * per_j;
-    dout += j * out_sj;
-    idx += j * out_sj;
-    din += j * in_sj;
-    T += j * in_sj;
-    const int x = (int)(t % W), y = (int)((t / W) % H);
-    const int64_t plane = t / ((int64_t)H * W);
+                                float* __restrict__ din, const float* __restrict__ T, int64_t in_sj, int per_out,
+                                int H, int W, int tact) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= per_out) return;
+    const int j = blockIdx.y;
     const int Ho = H / 2, Wo = W / 2;
-    float v = 0.0f;
-    if (y < 2 * Ho && x < 2 * Wo) {
-        const int64_t o = plane * Ho * Wo + (int64_t)(y / 2) * Wo + x / 2;
-        const int wi = (y & 1) * 2 + (x & 1);
-        if (idx[o] == wi) v = dout[o];
-    }
-    din[t] = v * act_grad_from_out(tact, T[t]);
+    const int xo = o % Wo, r = o / Wo, yo = r % Ho, plane = r / Ho;
+    const float d = dout[j * out_sj + o];
+    const int wi = idx[j * out_sj + o];
+    const int ny = (yo == Ho - 1 && (H & 1)) ? 3 : 2, nx = (xo == Wo - 1 && (W & 1)) ? 3 : 2;
+    const int64_t base = j * in_sj + (int64_t)plane * H * W + (2 * yo) * W + 2 * xo;
+    for (int dy = 0; dy < ny; ++dy)
+        for (int dx = 0; dx < nx; ++dx) {
+            const int64_t e = base + dy * W + dx;
+            const float v = (dy < 2 && dx < 2 && dy * 2 + dx == wi) ? d : 0.0f;
+            din[e] = v * act_grad_from_out(tact, T[e]);
+        }
 }
 
 // ------------------------------------------------------------------- head
@@ -384,9 +383,9 @@ static cudaError_t simt_forward(smc_ctx* c, const float* x, int rows) {
                               in, in_sj, c->theta + c->segs[L.seg_w].off, c->theta + c->segs[L.seg_b].off, out,
                               ch * L.out_feat(), rows, J, s, L.act));
         } else {
-            const int64_t per = (int64_t)rows * L.out_feat();
-            SMC_LAUNCH(c, pool_fwd_kernel<<<nblk(per * J), 256, 0, c->stream>>>(
-                              in, ch * L.in_feat(), out, c->pool_idx[l], ch * L.out_feat(), per, J, L.in_h, L.in_w));
+            const int per = (int)((int64_t)rows * L.out_feat());
+            SMC_LAUNCH(c, pool_fwd_kernel<<<dim3(nblk(per), J), 256, 0, c->stream>>>(
+                              in, ch * L.in_feat(), out, c->pool_idx[l], ch * L.out_feat(), per, L.in_h, L.in_w));
         }
     }
     return cudaGetLastError();
@@ -473,10 +472,10 @@ smc_status simt_eval(smc_ctx* c) {
                 }
             } else {   // pool: scatter to the argmax, times act' of the producing layer
                 const int ta = (l > 0) ? c->layers[l - 1].act : SMC_ACT_IDENTITY;
-                const int64_t per = (int64_t)rows * L.in_feat();
-                SMC_LAUNCH(c, pool_bwd_kernel<<<nblk(per * J), 256, 0, c->stream>>>(
+                const int per = (int)((int64_t)rows * L.out_feat());
+                SMC_LAUNCH(c, pool_bwd_kernel<<<dim3(nblk(per), J), 256, 0, c->stream>>>(
                                   dcur, c->pool_idx[l], ch * L.out_feat(), dnext, c->act[l - 1], ch * L.in_feat(), per,
-                                  J, L.in_h, L.in_w, ta));
+                                  L.in_h, L.in_w, ta));
             }
             cur ^= 1;
         }
