@@ -432,6 +432,14 @@ smc_status smc_k_philox_normals(uint64_t seed, uint32_t stream_id, uint32_t iter
 smc_status smc_k_philox_u32(uint32_t k0, uint32_t k1, uint32_t c2, uint32_t c3,
                             int64_t n, uint32_t* out_dev, void* stream);
 
+/* Failure-detection probe (no counterpart in the paper): launches one thread
+ * that waits, through the same bounded device-side wait as the tensor-core
+ * kernels (an mbarrier polled with a %globaltimer limit, here limit_ms), on an
+ * mbarrier it completes itself only if `arrive` != 0.  Returns SMC_OK when the
+ * phase completed and SMC_ETIMEOUT when the wait gave up; the GPU context stays
+ * usable either way.  SMC_EINVAL unless 0 < limit_ms <= 10000. */
+smc_status smc_k_wait_probe(double limit_ms, int32_t arrive, void* stream);
+
 /* C[m][n] = sum_k A[m][k] B[n][k] on tcgen05 tensor cores: A [M][K] and B [N][K]
  * BF16 row-major with row pitches lda, ldb (elements, multiples of 8), C FP32
  * row-major with pitch ldc.  Device pointers.  K-tails and ragged M/N are

@@ -423,6 +423,7 @@ smc_status smc_init(const smc_model* model, const smc_data* train, const smc_con
     if (!ok) {
         free_all(c);
         delete c;
+        cudaGetLastError();   // a failed allocation is not sticky: clear it for later launch checks
         return SMC_ENOMEM;
     }
     cudaMemsetAsync(c->theta, 0, flat * sizeof(float), c->stream);
@@ -1220,6 +1221,20 @@ smc_status smc_k_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ld
     cudaFree(err);
     if (e != cudaSuccess) return SMC_ECUDA;
     return herr ? SMC_ETIMEOUT : SMC_OK;
+}
+
+smc_status smc_k_wait_probe(double limit_ms, int32_t arrive, void* stream) {
+    if (!(limit_ms > 0.0) || limit_ms > 10000.0) return SMC_EINVAL;
+    int* r = nullptr;
+    if (cudaMalloc(&r, sizeof(int)) != cudaSuccess) return SMC_ENOMEM;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = launch_wait_probe(arrive ? 1 : 0, (uint64_t)(limit_ms * 1e6), r, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, r, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(r);
+    if (e != cudaSuccess) return SMC_ECUDA;
+    return h ? SMC_ETIMEOUT : SMC_OK;
 }
 
 }  // extern "C"

@@ -290,6 +290,7 @@ int64_t fused_slots(const smc_ctx* c, int64_t mc);
 cudaError_t launch_fused_images(smc_ctx* c);
 cudaError_t launch_fused_fwd_head(smc_ctx* c, const __nv_bfloat16* x, int64_t g0, int64_t mc, int slot_base,
                                   int* nslots);
+cudaError_t launch_wait_probe(int arrive, uint64_t limit_ns, int* result, cudaStream_t s);
 cudaError_t tc_gemm_public(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
                            int64_t M, int64_t N, int64_t K, int accumulate, cudaStream_t s, int* err_dev,
                            int num_sms);

@@ -672,6 +672,19 @@ static int choose_kslices(int64_t units, int kb_total, int workers, int max_s, d
     return best;
 }
 
+// Failure-detection probe: one thread waits, with the bounded wait of the
+// kernels above and a limit of limit_ns, on an mbarrier that it completes
+// itself only when `arrive` is set.  result: 0 the phase completed, 1 the wait
+// gave up.
+__global__ void wait_probe_kernel(int arrive, uint64_t limit_ns, int* result) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    if (arrive) mbar_arrive(&bar);
+    *result = mbar_wait_slow(&bar, 0, nullptr, limit_ns) ? 0 : 1;
+}
+
 }  // namespace tcg
 
 using namespace tcg;
@@ -963,6 +976,11 @@ smc_status tc_predict(smc_ctx* c, const float* x, int64_t n, float* out) {
     cudaFree(xb);
     cudaFree(logits);
     return st;
+}
+
+cudaError_t launch_wait_probe(int arrive, uint64_t limit_ns, int* result, cudaStream_t s) {
+    wait_probe_kernel<<<1, 32, 0, s>>>(arrive, limit_ns, result);
+    return cudaGetLastError();
 }
 
 cudaError_t tc_gemm_public(const void* A, int64_t lda, const void* B, int64_t ldb, float* Cout, int64_t ldc,

@@ -60,14 +60,16 @@ static __device__ __forceinline__ bool mbar_try_suspend(uint64_t* b, uint32_t pa
 }
 constexpr uint32_t kSuspendNs = 100000;   // 0.1 ms per suspended try
 
-// Bounded wait, slow path: false on timeout or when another role raised the abort flag.
-static __device__ __noinline__ bool mbar_wait_slow(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+// Bounded wait, slow path: false on timeout (limit_ns of %globaltimer) or when
+// another role raised the abort flag.
+static __device__ __noinline__ bool mbar_wait_slow(uint64_t* b, uint32_t parity, volatile int* abort_flag,
+                                                   uint64_t limit_ns = kTimeoutNs) {
     const uint64_t t0 = gtimer();
     for (uint32_t it = 1; it < (1u << 26); ++it) {
         if (mbar_try_suspend(b, parity, kSuspendNs)) return true;
         if ((it & 7) == 0) {
             if (abort_flag != nullptr && *abort_flag) return false;
-            if (gtimer() - t0 > kTimeoutNs) return false;
+            if (gtimer() - t0 > limit_ns) return false;
         }
     }
     return false;

@@ -136,6 +136,7 @@ _SIGS = {
                                        C.c_void_p]),
     "smc_k_philox_u32": (C.c_int, [C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int64, C.c_void_p,
                                    C.c_void_p]),
+    "smc_k_wait_probe": (C.c_int, [C.c_double, C.c_int32, C.c_void_p]),
     "smc_k_gemm_bf16": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                   C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_void_p]),
 }
@@ -486,3 +487,9 @@ def smc_k_gemm_bf16(A, B, Cout, accumulate=False, stream=None):
     _check(load().smc_k_gemm_bf16(A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0), Cout.data_ptr(),
                                   Cout.stride(0), M, N, K, 1 if accumulate else 0, _stream(stream)),
            "smc_k_gemm_bf16")
+
+
+def smc_k_wait_probe(limit_ms, arrive, stream=None):
+    """Bounded device wait on an mbarrier (completed by the kernel only when
+    `arrive`); raises SMCError(SMC_ETIMEOUT) when the wait gives up."""
+    _check(load().smc_k_wait_probe(float(limit_ms), 1 if arrive else 0, _stream(stream)), "smc_k_wait_probe")
