@@ -717,17 +717,38 @@ __global__ void head_reduce_kernel(const float* __restrict__ part_w, const doubl
 __global__ void splitk_reduce_kernel(const float* __restrict__ part, int ks, int64_t slice, int64_t rows,
                                      int ncol, int64_t ldp, int din, float* __restrict__ gW, float* __restrict__ gb,
                                      int accumulate) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= rows * ncol) return;
-    const int64_t r = t / ncol;
-    const int cidx = (int)(t % ncol);
-    float s = 0.0f;
-    for (int q = 0; q < ks; ++q) s += part[q * slice + r * ldp + cidx];
-    if (cidx < din) {
-        float* d = gW + r * din + cidx;
-        *d = accumulate ? *d + s : s;
-    } else if (cidx == din) {
-        gb[r] = accumulate ? gb[r] + s : s;
+    // rows r of the output, 4 columns per thread (the partial rows are 16-byte
+    // aligned: ldp and slice are multiples of 4); slices summed in order
+    const int nq = (ncol + 3) / 4;
+    const bool vec_out = (din & 3) == 0 && (reinterpret_cast<uintptr_t>(gW) & 15) == 0;
+    for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
+        for (int q4 = blockIdx.x * blockDim.x + threadIdx.x; q4 < nq; q4 += gridDim.x * blockDim.x) {
+            const int c0 = 4 * q4;
+            float4 sum = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            for (int q = 0; q < ks; ++q) {
+                const float4 v = *reinterpret_cast<const float4*>(part + q * slice + r * ldp + c0);
+                sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
+            }
+            if (vec_out && c0 + 4 <= din) {
+                float4* d = reinterpret_cast<float4*>(gW + r * din + c0);
+                if (accumulate) {
+                    const float4 o = *d;
+                    sum = make_float4(o.x + sum.x, o.y + sum.y, o.z + sum.z, o.w + sum.w);
+                }
+                *d = sum;
+                continue;
+            }
+            const float sv[4] = {sum.x, sum.y, sum.z, sum.w};
+            for (int e = 0; e < 4; ++e) {
+                const int c = c0 + e;
+                if (c < din) {
+                    float* d = gW + r * din + c;
+                    *d = accumulate ? *d + sv[e] : sv[e];
+                } else if (c == din && c < ncol) {   // the bias column (present when ncol = din + 1)
+                    gb[r] = accumulate ? gb[r] + sv[e] : sv[e];
+                }
+            }
+        }
     }
 }
 
@@ -872,8 +893,9 @@ static cudaError_t launch_wgrad(smc_ctx* c, int64_t g0, int64_t mc, bool with_b1
                         : launch_gemm<400, 200, 3, 2>(c->dZT, c->chunk, c->XTa + g0, c->Npad, g, c->stream, c->num_sms);
     c->launches++;
     if (e == cudaSuccess && g.kslices > 1) {
-        const int64_t n = JH * ncol;
-        SMC_LAUNCH(c, splitk_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+        const int nq = (int)((ncol + 3) / 4);
+        const dim3 grid((unsigned)((nq + 255) / 256), (unsigned)std::min<int64_t>(JH, 65535));
+        SMC_LAUNCH(c, splitk_reduce_kernel<<<grid, 256, 0, c->stream>>>(
                           c->gemm_part, g.kslices, slice, JH, (int)ncol, ldp, (int)Din, gW1, gb1, !first));
         e = cudaGetLastError();
     }
