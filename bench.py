@@ -15,7 +15,8 @@ evaluations) / time.  `value` is device-timed with inputs resident in HBM;
 while step k computes) and reads the step statistics back.
 
 `--impl reference` times the FP64 CPU oracle on a bounded sample of the same
-workload instead (the reference arm of this build).
+workload instead (the reference arm: there is no reference implementation of
+the paper to run).
 """
 from __future__ import annotations
 
@@ -25,6 +26,7 @@ import datetime
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -100,7 +102,8 @@ class Clocks:
     def __init__(self, idx):
         self.proc = None
         self.window = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        out_dir = os.environ.get("SMC_CLOCKS_DIR", tempfile.gettempdir())
+        self.path = os.path.join(out_dir, f"smc_clocks_{os.getpid()}.csv")
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")

@@ -50,7 +50,7 @@ typedef enum {
     SMC_ESTATE = 4,        /* call out of order, or context already failed */
     SMC_ENUMERIC = 5,      /* every particle's log-weight is -inf or NaN */
     SMC_ETIMEOUT = 6,      /* a bounded device-side wait gave up */
-    SMC_EUNSUPPORTED = 7   /* valid request this build does not implement */
+    SMC_EUNSUPPORTED = 7   /* valid request this library does not implement */
 } smc_status;
 
 enum { SMC_LAYER_DENSE = 0, SMC_LAYER_CONV = 1, SMC_LAYER_MAXPOOL2 = 2 };

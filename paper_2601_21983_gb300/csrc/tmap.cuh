@@ -1,6 +1,6 @@
 // Host-side TMA tensor-map encoding for the tcgen05 kernels (BF16 operands,
 // 64-element = 128-byte inner boxes with 128-byte swizzle, and unswizzled store
-// boxes).  The driver entry point is fetched once through the runtime.
+// boxes).  The CUDA driver API's tensor-map encoder is fetched once through the runtime.
 #pragma once
 
 #include <cuda.h>
