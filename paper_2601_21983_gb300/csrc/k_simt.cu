@@ -92,7 +92,94 @@ __global__ void __launch_bounds__(256) sgemm_kernel(SG g) {
     }
 }
 
+// Same contraction on 128 x 128 tiles, 256 threads x (8 x 8) outputs, K in
+// steps of 8 with the next tile's loads in flight while the current one is
+// used.  Tile loads run along whichever of the operand's strides is 1, so they
+// are coalesced for both the forward (k contiguous) and the weight-gradient
+// (row contiguous) layouts.  Each output sums k = 0 .. K-1 in order, exactly
+// as sgemm_kernel does, so the two kernels give bitwise equal results.
+__device__ __forceinline__ void sg_load_tile(float (*S)[128 + 4], const float* P, int64_t s_rc, int64_t s_k,
+                                             int rc0, int nrc, int k0, int K, int tid) {
+    if (s_k == 1) {   // k contiguous: 8 threads per row (or column)
+#pragma unroll
+        for (int pass = 0; pass < 4; ++pass) {
+            const int t = tid + pass * 256, kk = t & 7, rr = t >> 3;
+            const int rc = rc0 + rr, k = k0 + kk;
+            S[kk][rr] = (rc < nrc && k < K) ? P[rc * s_rc + k] : 0.0f;
+        }
+    } else {          // rows (or columns) contiguous: 128 threads per k
+#pragma unroll
+        for (int pass = 0; pass < 4; ++pass) {
+            const int t = tid + pass * 256, rr = t & 127, kk = t >> 7;
+            const int rc = rc0 + rr, k = k0 + kk;
+            S[kk][rr] = (rc < nrc && k < K) ? P[rc * s_rc + k * s_k] : 0.0f;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) sgemm128_kernel(SG g) {
+    __shared__ __align__(16) float As[2][8][128 + 4];
+    __shared__ __align__(16) float Bs[2][8][128 + 4];
+    const int j = blockIdx.z;
+    const int r0 = blockIdx.y * 128, c0 = blockIdx.x * 128;
+    const int tid = threadIdx.x;
+    const int tr = tid >> 4, tc = tid & 15;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[i][q] = 0.0f;
+    const float* A = g.A + j * g.a_sj;
+    const float* B = g.B + j * g.b_sj;
+    const int nk = (g.K + 7) / 8;
+    sg_load_tile(As[0], A, g.a_sr, g.a_sk, r0, g.R, 0, g.K, tid);
+    sg_load_tile(Bs[0], B, g.b_sc, g.b_sk, c0, g.Cn, 0, g.K, tid);
+    __syncthreads();
+    for (int t = 0; t < nk; ++t) {
+        const int cur = t & 1;
+        if (t + 1 < nk) {
+            sg_load_tile(As[cur ^ 1], A, g.a_sr, g.a_sk, r0, g.R, (t + 1) * 8, g.K, tid);
+            sg_load_tile(Bs[cur ^ 1], B, g.b_sc, g.b_sk, c0, g.Cn, (t + 1) * 8, g.K, tid);
+        }
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][tr * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][tr * 8 + 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tc * 8]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tc * 8 + 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[i][q] = fmaf(a[i], b[q], acc[i][q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int r = r0 + tr * 8 + i;
+        if (r >= g.R) continue;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int cc = c0 + tc * 8 + q;
+            if (cc >= g.Cn) continue;
+            float* dst = g.C + j * g.c_sj + r * g.c_sr + cc * g.c_sc;
+            const float v = acc[i][q];
+            if (g.epi == 0) *dst = act_f(g.act, v + g.bias[j * g.bias_sj + cc]);
+            else if (g.epi == 1) *dst = v * act_grad_from_out(g.act, g.T[j * g.c_sj + r * g.c_sr + cc * g.c_sc]);
+            else if (g.epi == 2) *dst += v;
+            else *dst = v;
+        }
+    }
+}
+
 static void sgemm(smc_ctx* c, const SG& g, int J) {
+    if (g.R >= 128 && g.Cn >= 128) {
+        dim3 grid((g.Cn + 127) / 128, (g.R + 127) / 128, J);
+        SMC_LAUNCH(c, sgemm128_kernel<<<grid, 256, 0, c->stream>>>(g));
+        return;
+    }
     dim3 grid((g.Cn + 63) / 64, (g.R + 63) / 64, J);
     SMC_LAUNCH(c, sgemm_kernel<<<grid, 256, 0, c->stream>>>(g));
 }
