@@ -212,6 +212,56 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+EVAL_CONFIGS = {
+    # name: (layers, input shape, activation, J, rows, chunk rows, FLOP per particle-sample evaluation, data)
+    "cnn": ([("conv", 3, 16, 5), ("pool2",), ("conv", 16, 32, 5), ("pool2",), ("dense", 800, 10)], (3, 32, 32),
+            "tanh", 128, 4096, 1024, 11.49e6, "smooth_field_images"),
+    "mlp4": ([("dense", 784, 400), ("dense", 400, 400), ("dense", 400, 10)], (784,), "relu", 1024, 2048, 512,
+             2.238e6, "template_images"),
+}
+
+
+def run_eval_config(args):
+    """Gradient-evaluation throughput of the FP32 engine's other configurations:
+    the 3x32x32 CNN (conv5x5 3-16, pool, conv5x5 16-32, pool, fc 10; J = 128)
+    and the MLP 784-400-400-10 (J = 1024).  Each evaluation is log pi and its
+    full gradient for every particle over the rows (smc_eval_device), timed
+    with CUDA events after one warm-up evaluation."""
+    import torch
+    import synthetic
+    from paper_2601_21983_gb300 import smc as S
+    S.load()
+    layers, shape, act, J, rows, chunk, flop, data = EVAL_CONFIGS[args.eval_config]
+    X, y = getattr(synthetic, data)(rows, seed=0)
+    model = S.make_model(layers, shape, S.ACT_TANH if act == "tanh" else S.ACT_RELU)
+    stream = torch.cuda.current_stream()
+    cfg = S.make_config(J, 5, S.PREC_FP32, stream=stream, chunk_rows=chunk)
+    ctx = S.smc_init(model, torch.from_numpy(np.ascontiguousarray(X, np.float32)).cuda(),
+                     y_class=torch.from_numpy(y.astype(np.int32)).cuda(), cfg=cfg)
+    S.smc_set_schedule(ctx, S.make_schedule("fb", rows, rows, 5))
+    D = S.smc_num_params(ctx)
+    theta = torch.from_numpy(synthetic.particles(J, D, 5, std=0.05)).cuda()
+    lp = torch.empty(J, dtype=torch.float64, device="cuda")
+    g = torch.empty((J, D), dtype=torch.float32, device="cuda")
+    S.smc_set_state_device(ctx, theta)
+    S.smc_eval_device(ctx, lp, g)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        S.smc_eval_device(ctx, lp, g)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    S.smc_destroy(ctx)
+    units = J * rows
+    print(json.dumps({"metric": "particle*sample grad-evals/s (FP32 engine)", "value": units / (ms / 1e3),
+                      "unit": UNIT, "ms_per_eval": ms, "tflops": units * flop / (ms / 1e3) / 1e12,
+                      "config": {"workload": args.eval_config, "layers": [list(l) for l in layers], "J": J,
+                                 "rows": rows, "chunk_rows": chunk, "params_per_particle": D,
+                                 "flop_per_unit": flop, "precision": "fp32"}}), flush=True)
+
+
 def run_tta(args):
     """Time to test accuracy, learned vs plain proposal (configuration c3):
     the network is trained on exploratory trajectories of the same setup with
@@ -369,6 +419,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline", action="store_true")
     ap.add_argument("--tta", action="store_true", help="time-to-test-accuracy, learned vs plain proposal")
+    ap.add_argument("--eval-config", choices=sorted(EVAL_CONFIGS),
+                    help="gradient-evaluation throughput of another configuration (FP32 engine)")
     ap.add_argument("--grid", action="store_true", help="every DA scheme x {LD, HMC}: runtime and test accuracy")
     ap.add_argument("--grid-iters", type=int, default=200)
     ap.add_argument("--grid-mb", type=int, default=500)
@@ -379,6 +431,8 @@ def main():
     args.steps = max(1, args.steps)
     if args.impl == "reference":
         return run_reference(args)
+    if args.eval_config:
+        return run_eval_config(args)
     if args.tta:
         return run_tta(args)
     if args.grid:
