@@ -26,8 +26,14 @@ smc_status cuda_check(smc_ctx* c, cudaError_t e, const char* what) {
     return fail(c, SMC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// NVTX range names of the kernel families (counter indices of smc_get_counters)
+static const char* const kFamNames[kFamilies] = {"smc:fwd_gemm", "smc:head", "smc:wgrad_gemm", "smc:hidden_gemm",
+                                                 "smc:leapfrog", "smc:weights", "smc:resample", "smc:simt_net",
+                                                 "smc:reduce", "smc:fused_fwd_head"};
+
 void fam_begin(smc_ctx* c, int f) {
     c->fam_calls[f]++;
+    nvtxRangePushA(kFamNames[f]);
     if (!c->timing) return;
     if (!c->timers[f].a) {
         cudaEventCreate(&c->timers[f].a);
@@ -37,6 +43,7 @@ void fam_begin(smc_ctx* c, int f) {
 }
 
 void fam_end(smc_ctx* c, int f) {
+    nvtxRangePop();
     if (!c->timing) return;
     cudaEventRecord(c->timers[f].b, c->stream);
     cudaEventSynchronize(c->timers[f].b);
@@ -259,6 +266,7 @@ const char* smc_last_error(const smc_ctx* c) { return c ? c->last_error.c_str() 
 int64_t smc_num_params(const smc_ctx* c) { return c ? c->D : 0; }
 
 smc_status smc_init(const smc_model* model, const smc_data* train, const smc_config* cfg, smc_ctx** out) {
+    NvtxScope nvtx_scope("smc_init");
     if (!out) return SMC_EINVAL;
     *out = nullptr;
     if (!model || !train || !cfg || model->version != SMC_ABI_VERSION || cfg->version != SMC_ABI_VERSION)
@@ -455,6 +463,7 @@ void smc_destroy(smc_ctx* c) {
 static cudaError_t apply_staged_rows(smc_ctx* c);
 
 smc_status smc_set_schedule(smc_ctx* c, const smc_schedule* s, smc_step_stats* stats) {
+    NvtxScope nvtx_scope("smc_set_schedule");
     if (!c || !s) return SMC_EINVAL;
     if (!ok_ctx(c)) return SMC_ESTATE;
     if (s->kind < SMC_SCHED_CONSTANT || s->kind > SMC_SCHED_CTR_FRESH || s->C < 1 || s->kappa < 1 || s->K < 1 ||
@@ -486,6 +495,7 @@ smc_status smc_set_schedule(smc_ctx* c, const smc_schedule* s, smc_step_stats* s
 }
 
 smc_status smc_step(smc_ctx* c, const smc_step_params* p, smc_step_stats* stats) {
+    NvtxScope nvtx_scope("smc_step");
     if (!c || !p) return SMC_EINVAL;
     if (!ok_ctx(c) || !c->scheduled) return SMC_ESTATE;
     if (!(p->h >= 0.0) || p->S < 1 || p->S > 1000) return fail(c, SMC_EINVAL, "step arguments");
@@ -574,6 +584,7 @@ smc_status smc_anneal_next_moments(smc_ctx* c, const double* moments, smc_anneal
 }
 
 static smc_status anneal_impl(smc_ctx* c, const double* given, smc_anneal_info* info) {
+    NvtxScope nvtx_scope("smc_anneal_next");
     if (!c) return SMC_EINVAL;
     if (!ok_ctx(c) || !c->scheduled) return SMC_ESTATE;
     const int64_t before = c->rows_a + c->rows_b;
@@ -644,6 +655,7 @@ static smc_status anneal_impl(smc_ctx* c, const double* given, smc_anneal_info* 
 }
 
 smc_status smc_resample(smc_ctx* c, int32_t force, int32_t* did) {
+    NvtxScope nvtx_scope("smc_resample");
     if (!c) return SMC_EINVAL;
     if (!ok_ctx(c) || !c->scheduled) return SMC_ESTATE;
     if (did) *did = 0;
@@ -676,6 +688,7 @@ smc_status smc_resample(smc_ctx* c, int32_t force, int32_t* did) {
 }
 
 smc_status smc_posterior_predict(smc_ctx* c, const float* x, int64_t n, int32_t on_device, float* probs) {
+    NvtxScope nvtx_scope("smc_posterior_predict");
     if (!c || !x || !probs || n < 1) return SMC_EINVAL;
     if (!ok_ctx(c)) return SMC_ESTATE;
     if (c->likelihood != SMC_LIK_CATEGORICAL) return fail(c, SMC_EUNSUPPORTED, "predictive needs categorical");
@@ -707,6 +720,7 @@ smc_status smc_posterior_predict(smc_ctx* c, const float* x, int64_t n, int32_t 
 }
 
 smc_status smc_upload_rows(smc_ctx* c, int64_t row0, int64_t n, const float* x, const int32_t* y, const float* yv) {
+    NvtxScope nvtx_scope("smc_upload_rows");
     if (!c || !x || n < 0 || row0 < 0 || row0 + n > c->N) return SMC_EINVAL;
     if (!ok_ctx(c)) return SMC_ESTATE;
     if (n == 0) return SMC_OK;
@@ -741,6 +755,7 @@ static cudaError_t apply_staged_rows(smc_ctx* c) {
 
 smc_status smc_upload_rows_async(smc_ctx* c, int64_t row0, int64_t n, const float* x, const int32_t* y,
                                  const float* yv) {
+    NvtxScope nvtx_scope("smc_upload_rows_async");
     if (!c || !x || n < 0 || row0 < 0 || row0 + n > c->N) return SMC_EINVAL;
     if (!ok_ctx(c)) return SMC_ESTATE;
     if (n == 0) return SMC_OK;
@@ -822,6 +837,7 @@ smc_status smc_sda_partials(smc_ctx* c, double* out) {
 // ---------------------------------------------------------------- checkpoints
 
 smc_status smc_checkpoint(smc_ctx* c, const char* path) {
+    NvtxScope nvtx_scope("smc_checkpoint");
     if (!c || !path) return SMC_EINVAL;
     if (!ok_ctx(c)) return SMC_ESTATE;
     cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -869,6 +885,7 @@ smc_status smc_checkpoint(smc_ctx* c, const char* path) {
 }
 
 smc_status smc_restore(smc_ctx* c, const char* path) {
+    NvtxScope nvtx_scope("smc_restore");
     if (!c || !path) return SMC_EINVAL;
     if (!ok_ctx(c)) return SMC_ESTATE;
     FILE* f = fopen(path, "rb");
@@ -982,6 +999,7 @@ smc_status smc_set_uniforms(smc_ctx* c, const double* u, int32_t n) {
 }
 
 smc_status smc_eval(smc_ctx* c, double* logpi, float* grad_ll, double* la, double* lb) {
+    NvtxScope nvtx_scope("smc_eval");
     if (!c) return SMC_EINVAL;
     if (!ok_ctx(c) || !c->scheduled) return SMC_ESTATE;
     smc_status st = engine_eval(c);
@@ -1011,6 +1029,7 @@ smc_status smc_set_state_device(smc_ctx* c, const float* theta) {
 }
 
 smc_status smc_eval_device(smc_ctx* c, double* logpi, float* grad) {
+    NvtxScope nvtx_scope("smc_eval_device");
     if (!c) return SMC_EINVAL;
     if (!ok_ctx(c) || !c->scheduled) return SMC_ESTATE;
     smc_status st = engine_eval(c);

@@ -11,6 +11,8 @@
 
 #include "../../include/smc.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace smc {
 
 constexpr int kMaxSegments = 32;
@@ -207,9 +209,17 @@ const char* stateless_error();
 smc_status fail(smc_ctx* c, smc_status s, const std::string& msg);
 smc_status cuda_check(smc_ctx* c, cudaError_t e, const char* what);
 
-// per-family timing around launches
+// per-family timing (CUDA events when enabled) and NVTX ranges around launches
 void fam_begin(smc_ctx* c, int fam);
 void fam_end(smc_ctx* c, int fam);
+
+// NVTX range over one public call (visible to Nsight tools; no cost without one)
+struct NvtxScope {
+    explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope&) = delete;
+    NvtxScope& operator=(const NvtxScope&) = delete;
+};
 
 // ----- SMC kernels (k_smc.cu)
 struct SegTable {
