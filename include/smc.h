@@ -237,8 +237,9 @@ smc_status smc_upload_rows(smc_ctx* ctx, int64_t row0, int64_t n,
  * smc_anneal_next (in stream order, before that iteration's evaluations), so
  * a caller can upload iteration k+1's rows while iteration k computes.
  * x / y_class / y_value must stay valid and unchanged until that call has
- * returned; pinned memory
- * makes the copy asynchronous.  Uploads not yet applied apply in call order.
+ * returned; pinned memory makes the copy asynchronous.  Uploads apply in
+ * call order, also when mixed with smc_upload_rows (which first applies
+ * staged rows).
  * Like smc_upload_rows this moves data and does not change the target: the
  * rows are expected to carry the training set's values, and a cached
  * gradient or log pi is kept.  Errors: SMC_EINVAL (range), SMC_ENOMEM (the

@@ -724,8 +724,11 @@ smc_status smc_upload_rows(smc_ctx* c, int64_t row0, int64_t n, const float* x, 
     if (!c || !x || n < 0 || row0 < 0 || row0 + n > c->N) return SMC_EINVAL;
     if (!ok_ctx(c)) return SMC_ESTATE;
     if (n == 0) return SMC_OK;
-    cudaError_t e = cudaMemcpyAsync(c->X + row0 * c->in_feat, x, (size_t)n * c->in_feat * 4, cudaMemcpyHostToDevice,
-                                    c->stream);
+    // rows staged by smc_upload_rows_async were uploaded first: they apply first
+    cudaError_t e = apply_staged_rows(c);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->X + row0 * c->in_feat, x, (size_t)n * c->in_feat * 4, cudaMemcpyHostToDevice,
+                            c->stream);
     if (e == cudaSuccess && y) e = cudaMemcpyAsync(c->Y + row0, y, n * 4, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && yv) e = cudaMemcpyAsync(c->Yv + row0, yv, n * 4, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && c->precision == SMC_PREC_BF16) e = launch_bf16_data(c);

@@ -113,3 +113,31 @@ def test_prefetched_upload_is_not_seen_by_the_running_iteration():
             S.smc_destroy(ctx)
     for u, v in zip(res[0], res[1]):
         assert np.array_equal(np.asarray(u), np.asarray(v))
+
+
+def test_async_then_sync_upload_keep_call_order():
+    """Rows staged asynchronously and then overwritten synchronously: the later
+    (synchronous) rows win, as if both had been synchronous."""
+    spec, X, y = _case(S.PREC_FP32)
+    J, D = 4, spec.n_params
+    r = np.random.default_rng(64)
+    a_x = np.ascontiguousarray(r.normal(size=(100, 16)), np.float32)
+    b_x = np.ascontiguousarray(r.normal(size=(100, 16)), np.float32)
+    lab = np.ascontiguousarray(r.integers(0, 4, 100), np.int32)
+    th0 = synthetic.particles(J, D, 64, std=0.3)
+    ref, _, _ = make_pair(spec, X, y, J, seed=64)
+    got, _, _ = make_pair(spec, X, y, J, seed=64)
+    try:
+        for ctx, mode in ((ref, "sync"), (got, "mixed")):
+            S.smc_set_state(ctx, th0)
+            if mode == "sync":
+                S.smc_upload_rows(ctx, 0, a_x, lab)
+            else:
+                S.smc_upload_rows_async(ctx, 0, a_x, lab)
+            S.smc_upload_rows(ctx, 50, b_x, lab)
+            S.smc_set_schedule(ctx, S.make_schedule("fb", 512, 512, 5))
+        for u, v in zip(_eval(ref, J, D), _eval(got, J, D)):
+            assert np.array_equal(u, v)
+    finally:
+        S.smc_destroy(ref)
+        S.smc_destroy(got)
