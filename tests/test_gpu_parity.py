@@ -387,6 +387,12 @@ def test_cnn_config_sda_parity():
             orc.step(0.005, 2, z)
             th, _, lp = S.smc_get_state(ctx, J, CNN2.n_params)
             assert _per_particle_rel(th, orc.theta) < 1e-5 and np.allclose(lp, orc.logpi, rtol=1e-5)
+        # posterior predictive over a separate test draw (weights from the last move)
+        Xt, _ = synthetic.smooth_field_images(50, seed=12, test=True)
+        probs = np.empty((50, 10), np.float32)
+        S.smc_posterior_predict(ctx, np.ascontiguousarray(Xt, np.float32), probs)
+        ref = orc.predict(Xt.astype(np.float64))
+        assert np.max(np.abs(probs - ref)) < 1e-5
     finally:
         S.smc_destroy(ctx)
 
