@@ -529,11 +529,14 @@ smc_status smc_step(smc_ctx* c, const smc_step_params* p, smc_step_stats* stats)
         c->lp_track_jump = used == SMC_PROPOSAL_EXPLORE;
     }
     c->lp_last_groups = G;
-    e = launch_momentum(c, c->pending_noise);
+    // P^0: injected draws go through the momentum buffer; Philox draws are made
+    // inside the first leapfrog pass (the same values, one pass fewer)
+    const bool injected = c->pending_noise;
+    if (injected) e = launch_momentum(c, true);
     c->pending_noise = false;
     const double h = p->h;
     fam_begin(c, F_LEAPFROG);
-    if (e == cudaSuccess) e = launch_leapfrog(c, 0, 0.5 * h, h, 0);
+    if (e == cudaSuccess) e = launch_leapfrog(c, injected ? 0 : 3, 0.5 * h, h, 0);
     fam_end(c, F_LEAPFROG);
     if (e != cudaSuccess) return cuda_check(c, e, "leapfrog");
     for (int s = 0; s < p->S; ++s) {

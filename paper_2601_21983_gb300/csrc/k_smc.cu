@@ -150,10 +150,39 @@ __device__ __forceinline__ void leap_elem(float& th, float& p, float g0, float* 
     }
 }
 
+// Momentum draw fused into the first pass: element e (canonical order) of
+// this context takes normal (base + e) of the (seed, sid, it) sequence, i.e.
+// lane (base + e) mod 4 of Philox block (base + e) / 4 -- the draws
+// canon_normals_kernel writes, bit for bit.
+struct LeapDraw {
+    uint64_t seed;
+    uint32_t sid, it;
+    int64_t D, base;   // parameters per particle; stream position of this context's element 0
+};
+
+// the four normals of stream positions g0 .. g0 + 3 (one or two Philox blocks)
+__device__ __forceinline__ float4 draw4(const LeapDraw& d, uint64_t g0) {
+    float a[4], b[4];
+    normals4(d.seed, d.sid, d.it, g0 >> 2, a);
+    const int r0 = (int)(g0 & 3);
+    if (r0 == 0) return make_float4(a[0], a[1], a[2], a[3]);
+    normals4(d.seed, d.sid, d.it, (g0 >> 2) + 1, b);
+    if (r0 == 1) return make_float4(a[1], a[2], a[3], b[0]);
+    if (r0 == 2) return make_float4(a[2], a[3], b[0], b[1]);
+    return make_float4(a[3], b[0], b[1], b[2]);
+}
+__device__ __forceinline__ float draw1(const LeapDraw& d, uint64_t g) {
+    float a[4];
+    normals4(d.seed, d.sid, d.it, g >> 2, a);
+    const int r = (int)(g & 3);
+    return r == 0 ? a[0] : (r == 1 ? a[1] : (r == 2 ? a[2] : a[3]));
+}
+
 // Block (ch, j): chunk ch of every segment of particle j.  Segments whose
 // per-particle size is a multiple of 4 move 16 bytes per access (their starts
-// are 64-element aligned, so every particle row is 16-byte aligned).
-template <int PHASE>
+// are 64-element aligned, so every particle row is 16-byte aligned).  Phase 3
+// is phase 0 with the momentum drawn in place instead of read from `mom`.
+template <int PHASE_IN>
 __global__ void __launch_bounds__(256) leapfrog_kernel(float* __restrict__ theta, float* __restrict__ mom,
                                                        const float* __restrict__ grad,
                                                        __nv_bfloat16* __restrict__ shadow, SegTable t,
@@ -161,7 +190,9 @@ __global__ void __launch_bounds__(256) leapfrog_kernel(float* __restrict__ theta
                                                        const float* __restrict__ hscale, int G,
                                                        float* __restrict__ theta_old, int J, int nchunks,
                                                        float h_kick, float h_drift, float inv_sig2,
-                                                       double* __restrict__ part) {
+                                                       double* __restrict__ part, LeapDraw draw) {
+    constexpr bool DRAW = PHASE_IN == 3;
+    constexpr int PHASE = DRAW ? 0 : PHASE_IN;
     __shared__ double sh[256];
     const int j = blockIdx.y, ch = blockIdx.x;
     const int grp = (int)(((int64_t)j * G) / J);
@@ -181,8 +212,10 @@ __global__ void __launch_bounds__(256) leapfrog_kernel(float* __restrict__ theta
             float4* p4 = reinterpret_cast<float4*>(mom + base);
             const float4* g4 = reinterpret_cast<const float4*>(grad + base);
             float4* to4 = theta_old ? reinterpret_cast<float4*>(theta_old + base) : nullptr;
+            const uint64_t g_seg = (uint64_t)(draw.base + (int64_t)j * draw.D + t.canon[s]);
             for (int64_t q = lo + threadIdx.x; q < hi; q += blockDim.x) {
-                float4 th = th4[q], p = p4[q];
+                float4 th = th4[q];
+                float4 p = DRAW ? draw4(draw, g_seg + 4 * (uint64_t)q) : p4[q];
                 const float4 g = g4[q];
                 float4 to = (to4 && PHASE == 2) ? to4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
                 float* tp = (to4 && PHASE != 1) ? &to.x : nullptr;
@@ -207,7 +240,8 @@ __global__ void __launch_bounds__(256) leapfrog_kernel(float* __restrict__ theta
             const int64_t lo = size * ch / nchunks, hi = size * (ch + 1) / nchunks;
             for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
                 const int64_t idx = base + e;
-                float th = theta[idx], p = mom[idx];
+                float th = theta[idx];
+                float p = DRAW ? draw1(draw, (uint64_t)(draw.base + (int64_t)j * draw.D + t.canon[s] + e)) : mom[idx];
                 float to = (theta_old && PHASE == 2) ? theta_old[idx] : 0.0f;
                 leap_elem<PHASE>(th, p, grad[idx], (theta_old && PHASE != 1) ? &to : nullptr, im, sqrt_m, hk, hd,
                                  inv_sig2, ke, sq, jump);
@@ -605,18 +639,16 @@ cudaError_t launch_leapfrog(smc_ctx* c, int phase, double h_kick, double h_drift
     const float* hsc = c->lp_groups > 0 ? c->lp_hscale : nullptr;
     const int G = c->lp_groups > 0 ? c->lp_groups : 1;
     float* told = c->lp_track_jump ? c->theta_alt : nullptr;
-    if (phase == 0)
-        SMC_LAUNCH(c, leapfrog_kernel<0><<<grid, 256, 0, c->stream>>>(c->theta, c->mom, c->grad, c->shadow, t, im, hsc,
-                                                                     G, told, c->J, c->part_chunks, (float)h_kick,
-                                                                     (float)h_drift, inv_sig2, c->part));
-    else if (phase == 1)
-        SMC_LAUNCH(c, leapfrog_kernel<1><<<grid, 256, 0, c->stream>>>(c->theta, c->mom, c->grad, c->shadow, t, im, hsc,
-                                                                     G, told, c->J, c->part_chunks, (float)h_kick,
-                                                                     (float)h_drift, inv_sig2, c->part));
-    else
-        SMC_LAUNCH(c, leapfrog_kernel<2><<<grid, 256, 0, c->stream>>>(c->theta, c->mom, c->grad, c->shadow, t, im, hsc,
-                                                                     G, told, c->J, c->part_chunks, (float)h_kick,
-                                                                     (float)h_drift, inv_sig2, c->part));
+    LeapDraw d{c->seed, RNG_MOMENTUM, (uint32_t)c->step_index, c->D, c->particle_offset * c->D};
+#define SMC_LEAP(P)                                                                                              \
+    SMC_LAUNCH(c, leapfrog_kernel<P><<<grid, 256, 0, c->stream>>>(c->theta, c->mom, c->grad, c->shadow, t, im, hsc, \
+                                                                  G, told, c->J, c->part_chunks, (float)h_kick,     \
+                                                                  (float)h_drift, inv_sig2, c->part, d))
+    if (phase == 0) SMC_LEAP(0);
+    else if (phase == 1) SMC_LEAP(1);
+    else if (phase == 2) SMC_LEAP(2);
+    else SMC_LEAP(3);
+#undef SMC_LEAP
     return cudaGetLastError();
 }
 

@@ -676,3 +676,37 @@ def test_multinomial_unscaled_trajectory_parity():
         assert np.allclose(lp, orc.logpi, rtol=1e-4)
     finally:
         S.smc_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", [S.PREC_FP32, S.PREC_BF16])
+def test_fused_momentum_draw_matches_philox_stream(precision):
+    """The first leapfrog pass draws P^0 itself; a twin context given the same
+    (seed, momentum stream, step) Philox normals as injected noise must follow
+    the same trajectory bit for bit."""
+    if precision == S.PREC_FP32:
+        spec, (X, y), h = MLP0, _mixture(512, 56), 0.01
+    else:
+        spec, (X, y), h = MLP1, _images(512, 56), 0.002
+    J, D, seed = 8, spec.n_params, 56
+    a, _, _ = make_pair(spec, X, y, J, seed=seed, precision=precision)
+    b, _, _ = make_pair(spec, X, y, J, seed=seed, precision=precision)
+    try:
+        th0 = synthetic.particles(J, D, 56, std=0.1)
+        for ctx in (a, b):
+            S.smc_set_state(ctx, th0)
+            S.smc_set_schedule(ctx, S.make_schedule("linear", 128, 128, 10))
+        for step in range(3):
+            for ctx in (a, b):
+                S.smc_anneal_next(ctx)
+            z = torch.empty(J * D, dtype=torch.float32, device="cuda")
+            S.smc_k_philox_normals(seed, 2, step, 0, z)
+            torch.cuda.synchronize()
+            S.smc_set_noise(b, z.cpu().numpy().reshape(J, D))
+            sa = S.smc_step(a, h, 2)
+            sb = S.smc_step(b, h, 2)
+            assert sa["ess"] == sb["ess"], step
+            for u, v in zip(S.smc_get_state(a, J, D), S.smc_get_state(b, J, D)):
+                assert np.array_equal(u, v), step
+    finally:
+        S.smc_destroy(a)
+        S.smc_destroy(b)
