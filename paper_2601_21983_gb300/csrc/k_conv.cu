@@ -48,7 +48,7 @@ size_t wgrad_smem(int cin, int h, int w, int cout, int oh, int ow, int k, int* t
     const int tiles = (nop / 4) * ((K + 1 + kTK - 1) / kTK);
     const int G = std::max(1, kThreads / std::max(tiles, 1));
     *tiles_out = tiles;
-    const size_t stage = ((size_t)oh * ow * (nop + 4) + (size_t)cin * h * w) * 4;
+    const size_t stage = ((size_t)oh * ow * (nop + 4) + (size_t)(cin + 2) * h * w) * 4;
     const size_t red = G > 1 ? (size_t)G * tiles * 64 * 4 : 0;
     return std::max(stage, red);
 }
@@ -198,9 +198,13 @@ __global__ void __launch_bounds__(kThreads) conv_wgrad_kernel(const WgArgs a) {
     const bool worker = threadIdx.x < tiles * G;
     const int og = tile % ogroups, kg = tile / ogroups;
     float* dzs = sm;
-    float* src = dzs + (int64_t)P * nops;
+    float* src = dzs + (int64_t)P * nops;   // [cin][h][w] of the sample | ones [h w] | zeros [h w]
+    for (int i = threadIdx.x; i < HW; i += blockDim.x) {
+        src[a.cin * HW + i] = 1.0f;
+        src[(a.cin + 1) * HW + i] = 0.0f;
+    }
 
-    int toff[kTK];   // source offset of each tap at position (0, 0); -1: the bias (constant 1)
+    int toff[kTK];   // source offset of each tap at position (0, 0): the bias reads ones, past it zeros
 #pragma unroll
     for (int i = 0; i < kTK; ++i) {
         const int t = kg * kTK + i;
@@ -208,7 +212,7 @@ __global__ void __launch_bounds__(kThreads) conv_wgrad_kernel(const WgArgs a) {
             const int c = t / k2, r = t - c * k2, dy = r / a.k, dx = r - dy * a.k;
             toff[i] = (c * a.h + dy) * a.w + dx;
         } else {
-            toff[i] = -1;
+            toff[i] = (t == K ? a.cin : a.cin + 1) * HW;
         }
     }
     float acc[4][kTK];
@@ -230,12 +234,15 @@ __global__ void __launch_bounds__(kThreads) conv_wgrad_kernel(const WgArgs a) {
         for (int i = threadIdx.x; i < a.cin * HW; i += blockDim.x) src[i] = sg[i];
         __syncthreads();
         if (!worker) continue;
+        int y = g / a.ow, x = g - (g / a.ow) * a.ow;   // output position p = y ow + x, stepped by G
         for (int p = g; p < P; p += G) {
             const float4 d = *reinterpret_cast<const float4*>(dzs + p * nops + 4 * og);
-            const int pb = (p / a.ow) * a.w + (p % a.ow);
+            const int pb = y * a.w + x;
+            x += G;
+            while (x >= a.ow) { x -= a.ow; ++y; }
 #pragma unroll
             for (int i = 0; i < kTK; ++i) {
-                const float v = toff[i] >= 0 ? src[toff[i] + pb] : (kg * kTK + i == K ? 1.0f : 0.0f);
+                const float v = src[toff[i] + pb];
                 acc[0][i] = fmaf(d.x, v, acc[0][i]);
                 acc[1][i] = fmaf(d.y, v, acc[1][i]);
                 acc[2][i] = fmaf(d.z, v, acc[2][i]);
