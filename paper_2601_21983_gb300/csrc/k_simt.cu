@@ -196,6 +196,10 @@ __global__ void colsum_kernel(const float* __restrict__ dz, int64_t sj, int64_t 
 }
 
 // ---------------------------------------------------------------- conv / pool
+// Direct convolution kernels (one output element per thread): the fallback for
+// layers whose shared-memory tiles do not fit (conv_fits); every other
+// convolution runs on the implicit-GEMM kernels of k_conv.cu, which compute
+// the same sums.
 struct ConvShape { int cin, h, w, cout, oh, ow, k; };
 
 // out(j,m,o,y,x) = act(b(j,o) + sum_{c,dy,dx} W(j,o,c,dy,dx) in(j,m,c,y+dy,x+dx))
