@@ -710,3 +710,25 @@ def test_fused_momentum_draw_matches_philox_stream(precision):
     finally:
         S.smc_destroy(a)
         S.smc_destroy(b)
+
+
+def test_fp32_conv_fallback_parity():
+    """A 64 -> 64 channel 5x5 convolution needs more shared memory than a block
+    has (1600 taps x 64 channels of weights), so that layer runs on the direct
+    kernels while the first (3 -> 64) runs on the tiled ones: evaluation
+    against the oracle, whole gradient per particle."""
+    spec = nn.Spec([("conv", 3, 64, 5), ("conv", 64, 64, 5), ("dense", 64 * 8 * 8, 10)], (3, 16, 16), nn.TANH)
+    N, J = 8, 2
+    X, y = synthetic.smooth_field_images(N, seed=57, side=16)
+    ctx, orc, _ = make_pair(spec, X, y, J, seed=57)
+    try:
+        th0 = synthetic.particles(J, spec.n_params, 57, std=0.05)
+        S.smc_set_state(ctx, th0)
+        S.smc_set_schedule(ctx, S.make_schedule("fb", N, N, 5))
+        orc.set_schedule("fb", N, N, 5, th0)
+        lp, g, la, lb = S.smc_eval(ctx, J, spec.n_params)
+        rlp, rg, rla, rlb = oracle_eval(orc)
+        assert np.allclose(la, rla, rtol=1e-5) and np.allclose(lp, rlp, rtol=1e-5)
+        assert _per_particle_rel(g, rg) < 1e-5
+    finally:
+        S.smc_destroy(ctx)
