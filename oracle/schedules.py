@@ -85,7 +85,8 @@ def sda_next_beta(beta: float, wn, omega, omega_hat, delta_s: float = 1.0) -> fl
     Update beta' = beta - dS / (Var(Oh) + Cov(O, Oh)); if that does not exceed
     beta, the sign of dS is flipped; beta' is clipped to 1.
     Reading r10: a zero or non-finite denominator gives beta' = 1.
-    The garbled "E[Omega, Omega_hat]" of the last moment is read as E[Omega Omega_hat].
+    The last moment, printed with a comma between Omega and Omega_hat, is read
+    as the mixed moment E[Omega Omega_hat].
     """
     e_oh = sum(w * oh for w, oh in zip(wn, omega_hat))
     e_oh2 = sum(w * oh * oh for w, oh in zip(wn, omega_hat))
@@ -124,8 +125,7 @@ class SDAState:
     def advance(self, wn, omega, omega_hat) -> bool:
         """Move to the next target.  If beta already reached 1 the block joins
         the fully included data and the next kappa rows become the new block
-        with beta = beta_reinit ("append an additional MB and reinitialise");
-        with no rows left the sampler stays at the full data set.  Otherwise
+        with beta restarting at beta_reinit (Sec. 3.1); with no rows left the sampler stays at the full data set.  Otherwise
         beta follows sda_next_beta.  Returns True when data were appended."""
         if self.beta >= 1.0:
             if self.m_total >= self.N:

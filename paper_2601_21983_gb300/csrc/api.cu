@@ -601,7 +601,8 @@ static smc_status anneal_impl(smc_ctx* c, const double* given, smc_anneal_info* 
         if (c->rows_a != old_a || c->coef_a != old_c || c->row_start != old_s) c->target_id++;
         appended = c->rows_a > old_a;
     } else if (c->beta >= 1.0) {
-        // "append an additional MB and reinitialise beta" (Sec. 3.1)
+        // Sec. 3.1: once beta reaches 1 the block joins the fully included rows,
+        // the next mini-batch becomes the block and beta restarts
         if (c->rows_a + c->rows_b >= c->N) {
             c->rows_a = c->N;
             c->rows_b = 0;
