@@ -45,7 +45,7 @@ def workload_config(args):
         "workload": (f"MLP {DIN}-{H}-{NCLS} ReLU, J={args.J} particles, synthetic {args.n}x{DIN} 10-class images, "
                      f"Linear DA (C=kappa={MB}, K={K_SCHED}) at its full-subset phase |D_k|={args.n}, "
                      f"HMC S={S_LF}, h={STEP_H}"),
-        "particles": args.J, "rows": args.n, "model": f"mlp-{DIN}-{H}-{NCLS}-relu",
+        "particles": args.J, "rows": args.n,
         "schedule": "linear", "leapfrog_steps": S_LF,
         "l2": "no flush: per-step working set (activations 2x3 GB) far above the 129 MB L2",
     }
