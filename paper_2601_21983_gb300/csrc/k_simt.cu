@@ -93,11 +93,27 @@ __global__ void __launch_bounds__(256) sgemm_kernel(SG g) {
 }
 
 // Same contraction on 128 x 128 tiles, 256 threads x (8 x 8) outputs, K in
-// steps of 8 with the next tile's loads in flight while the current one is
-// used.  Tile loads run along whichever of the operand's strides is 1, so they
-// are coalesced for both the forward (k contiguous) and the weight-gradient
-// (row contiguous) layouts.  Each output sums k = 0 .. K-1 in order, exactly
-// as sgemm_kernel does, so the two kernels give bitwise equal results.
+// steps of 8 through a three-stage cp.async pipeline: the tiles of the next
+// two K steps are in flight while the current one is used.  Tile loads run
+// along whichever of the operand's strides is 1, so they are coalesced for
+// both the forward (k contiguous) and the weight-gradient (row contiguous)
+// layouts.  Each output sums k = 0 .. K-1 in order, exactly as sgemm_kernel
+// does, so the two kernels give bitwise equal results.
+constexpr int SG_STAGES = 3;
+
+// 4-byte asynchronous global -> shared copy; src_bytes = 0 writes a zero
+// without reading (the source is then the operand's base, a valid address).
+__device__ __forceinline__ void sg_cp4(float* dst, const float* src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void sg_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void sg_wait_prev() { asm volatile("cp.async.wait_group %0;" ::"n"(SG_STAGES - 2) : "memory"); }
+
+// Stage the [8][128] slice k0 .. k0+7 of an operand (rows or columns rc0 ..
+// rc0+127); out-of-range elements become zeros.  Each thread copies 4
+// elements.
 __device__ __forceinline__ void sg_load_tile(float (*S)[128 + 4], const float* P, int64_t s_rc, int64_t s_k,
                                              int rc0, int nrc, int k0, int K, int tid) {
     if (s_k == 1) {   // k contiguous: 8 threads per row (or column)
@@ -105,21 +121,23 @@ __device__ __forceinline__ void sg_load_tile(float (*S)[128 + 4], const float* P
         for (int pass = 0; pass < 4; ++pass) {
             const int t = tid + pass * 256, kk = t & 7, rr = t >> 3;
             const int rc = rc0 + rr, k = k0 + kk;
-            S[kk][rr] = (rc < nrc && k < K) ? P[rc * s_rc + k] : 0.0f;
+            const bool ok = rc < nrc && k < K;
+            sg_cp4(&S[kk][rr], ok ? P + (rc * s_rc + k) : P, ok ? 4 : 0);
         }
     } else {          // rows (or columns) contiguous: 128 threads per k
 #pragma unroll
         for (int pass = 0; pass < 4; ++pass) {
             const int t = tid + pass * 256, rr = t & 127, kk = t >> 7;
             const int rc = rc0 + rr, k = k0 + kk;
-            S[kk][rr] = (rc < nrc && k < K) ? P[rc * s_rc + k * s_k] : 0.0f;
+            const bool ok = rc < nrc && k < K;
+            sg_cp4(&S[kk][rr], ok ? P + (rc * s_rc + k * s_k) : P, ok ? 4 : 0);
         }
     }
 }
 
-__global__ void __launch_bounds__(256) sgemm128_kernel(SG g) {
-    __shared__ __align__(16) float As[2][8][128 + 4];
-    __shared__ __align__(16) float Bs[2][8][128 + 4];
+__global__ void __launch_bounds__(256, 2) sgemm128_kernel(SG g) {
+    __shared__ __align__(16) float As[SG_STAGES][8][128 + 4];
+    __shared__ __align__(16) float Bs[SG_STAGES][8][128 + 4];
     const int j = blockIdx.z;
     const int r0 = blockIdx.y * 128, c0 = blockIdx.x * 128;
     const int tid = threadIdx.x;
@@ -132,15 +150,29 @@ __global__ void __launch_bounds__(256) sgemm128_kernel(SG g) {
     const float* A = g.A + j * g.a_sj;
     const float* B = g.B + j * g.b_sj;
     const int nk = (g.K + 7) / 8;
-    sg_load_tile(As[0], A, g.a_sr, g.a_sk, r0, g.R, 0, g.K, tid);
-    sg_load_tile(Bs[0], B, g.b_sc, g.b_sk, c0, g.Cn, 0, g.K, tid);
-    __syncthreads();
-    for (int t = 0; t < nk; ++t) {
-        const int cur = t & 1;
-        if (t + 1 < nk) {
-            sg_load_tile(As[cur ^ 1], A, g.a_sr, g.a_sk, r0, g.R, (t + 1) * 8, g.K, tid);
-            sg_load_tile(Bs[cur ^ 1], B, g.b_sc, g.b_sk, c0, g.Cn, (t + 1) * 8, g.K, tid);
+    // prologue: K steps 0 .. SG_STAGES-2, one commit group each (empty past nk)
+#pragma unroll
+    for (int p = 0; p < SG_STAGES - 1; ++p) {
+        if (p < nk) {
+            sg_load_tile(As[p], A, g.a_sr, g.a_sk, r0, g.R, p * 8, g.K, tid);
+            sg_load_tile(Bs[p], B, g.b_sc, g.b_sk, c0, g.Cn, p * 8, g.K, tid);
         }
+        sg_commit();
+    }
+    for (int t = 0; t < nk; ++t) {
+        // Groups committed so far cover K steps 0 .. t + SG_STAGES - 2; all but
+        // the newest SG_STAGES - 2 are complete, so step t has landed.  The
+        // barrier publishes it and ends every thread's use of the buffer that
+        // step t + SG_STAGES - 1 refills (the one step t - 1 read).
+        sg_wait_prev();
+        __syncthreads();
+        const int nx = t + SG_STAGES - 1;
+        if (nx < nk) {
+            sg_load_tile(As[nx % SG_STAGES], A, g.a_sr, g.a_sk, r0, g.R, nx * 8, g.K, tid);
+            sg_load_tile(Bs[nx % SG_STAGES], B, g.b_sc, g.b_sk, c0, g.Cn, nx * 8, g.K, tid);
+        }
+        sg_commit();
+        const int cur = t % SG_STAGES;
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
             const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][tr * 8]);
@@ -154,12 +186,42 @@ __global__ void __launch_bounds__(256) sgemm128_kernel(SG g) {
 #pragma unroll
                 for (int q = 0; q < 8; ++q) acc[i][q] = fmaf(a[i], b[q], acc[i][q]);
         }
-        __syncthreads();
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");   // only empty groups remain; nothing left in flight
+    // Epilogue.  A thread's 8 outputs of a row are adjacent when the output is
+    // column-contiguous: then they move as two 16-byte accesses (and so does
+    // T for epilogue 1); the values are those of the scalar path.
+    const int cc0 = c0 + tc * 8;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int r = r0 + tr * 8 + i;
         if (r >= g.R) continue;
+        const int64_t rowoff = j * g.c_sj + r * g.c_sr;
+        if (g.c_sc == 1 && cc0 + 8 <= g.Cn && ((reinterpret_cast<uintptr_t>(g.C + rowoff + cc0) & 15) == 0) &&
+            (g.epi != 1 || (reinterpret_cast<uintptr_t>(g.T + rowoff + cc0) & 15) == 0)) {
+            float4* d4 = reinterpret_cast<float4*>(g.C + rowoff + cc0);
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = acc[i][q];
+            if (g.epi == 0) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = act_f(g.act, v[q] + g.bias[j * g.bias_sj + cc0 + q]);
+            } else if (g.epi == 1) {
+                const float4* t4 = reinterpret_cast<const float4*>(g.T + rowoff + cc0);
+                const float4 t0 = t4[0], t1 = t4[1];
+                const float t[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = v[q] * act_grad_from_out(g.act, t[q]);
+            } else if (g.epi == 2) {
+                const float4 o0 = d4[0], o1 = d4[1];
+                const float o[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = o[q] + v[q];
+            }
+            d4[0] = make_float4(v[0], v[1], v[2], v[3]);
+            d4[1] = make_float4(v[4], v[5], v[6], v[7]);
+            continue;
+        }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int cc = c0 + tc * 8 + q;

@@ -79,6 +79,40 @@ def test_fp32_mlp_eval_parity(chunk):
         S.smc_destroy(ctx)
 
 
+MLP_RAGGED = nn.Spec([("dense", 37, 150), ("dense", 150, 131), ("dense", 131, 3)], (37,), nn.TANH)
+
+
+def test_fp32_ragged_dense_tiles_parity():
+    """FP32 dense engine on shapes that leave every tile ragged: 203 rows in
+    chunks of 141 (second chunk 62 rows), K = 37, 150 and 131 (not multiples of
+    the 8-deep K step), 131 output columns (a 3-column last tile), and
+    weight-gradient rows of 150 / 131 floats (row starts alternate between
+    16-byte aligned and not, so both epilogue store paths run)."""
+    N, J = 203, 3
+    X, y = synthetic.gaussian_mixture(N, d=37, n_classes=3, seed=21)
+    ctx, orc, _ = make_pair(MLP_RAGGED, X, y, J, seed=21, chunk=141)
+    try:
+        th0 = synthetic.particles(J, MLP_RAGGED.n_params, 21, std=0.2)
+        S.smc_set_state(ctx, th0)
+        S.smc_set_schedule(ctx, S.make_schedule("fb", N, N, 5))
+        orc.set_schedule("fb", N, N, 5, th0)
+        lp, g, la, lb = S.smc_eval(ctx, J, MLP_RAGGED.n_params)
+        rlp, rg, rla, rlb = oracle_eval(orc)
+        assert np.allclose(la, rla, rtol=1e-5)
+        assert np.allclose(lp, rlp, rtol=1e-5)
+        assert _per_particle_rel(g, rg) < 1e-5
+        # every parameter segment separately (a wrong tile edge shows up in one)
+        off = 0
+        for L in MLP_RAGGED.layers:
+            nw, nb = L[1] * L[2], L[2]
+            for seg in (slice(off, off + nw), slice(off + nw, off + nw + nb)):
+                assert _per_particle_rel(g[:, seg], rg[:, seg]) < 1e-5
+            off += nw + nb
+        assert off == MLP_RAGGED.n_params
+    finally:
+        S.smc_destroy(ctx)
+
+
 def test_fp32_cnn_eval_parity():
     N, J = 70, 3
     X = synthetic.smooth_field_images(N, seed=2, side=10, channels=3)[0]
