@@ -92,13 +92,17 @@ __global__ void __launch_bounds__(256) sgemm_kernel(SG g) {
     }
 }
 
-// Same contraction on 128 x 128 tiles, 256 threads x (8 x 8) outputs, K in
-// steps of 8 through a three-stage cp.async pipeline: the tiles of the next
-// two K steps are in flight while the current one is used.  Tile loads run
-// along whichever of the operand's strides is 1, so they are coalesced for
-// both the forward (k contiguous) and the weight-gradient (row contiguous)
-// layouts.  Each output sums k = 0 .. K-1 in order, exactly as sgemm_kernel
-// does, so the two kernels give bitwise equal results.
+// Same contraction on larger tiles: TRT x TCT threads, each owning 8 x 8
+// outputs (rows tr*4 .. +3 and BR/2 + tr*4 .. +3 of the tile, columns
+// likewise, so a warp's 16-byte shared-memory reads hit distinct banks), the
+// tile BR x BC = 8 TRT x 8 TCT.  K runs in steps of 8 through a three-stage
+// cp.async pipeline: the next two steps' tiles are in flight while the current
+// one is used.  Tile loads run along whichever of the operand's strides is 1,
+// so they are coalesced for both the forward (k contiguous) and the
+// weight-gradient (row contiguous) layouts.  Each output sums k = 0 .. K-1 in
+// order, exactly as sgemm_kernel does, so every tile shape gives bitwise equal
+// results; the host picks the shape whose tiles waste the least of R x Cn
+// (400 = 2 x 200 and 784 = 7 x 112 instead of 512 and 896 on 128 x 128 tiles).
 constexpr int SG_STAGES = 3;
 
 // 4-byte asynchronous global -> shared copy; src_bytes = 0 writes a zero
@@ -111,37 +115,76 @@ __device__ __forceinline__ void sg_cp4(float* dst, const float* src, int src_byt
 __device__ __forceinline__ void sg_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void sg_wait_prev() { asm volatile("cp.async.wait_group %0;" ::"n"(SG_STAGES - 2) : "memory"); }
 
-// Stage the [8][128] slice k0 .. k0+7 of an operand (rows or columns rc0 ..
-// rc0+127); out-of-range elements become zeros.  Each thread copies 4
-// elements.
-__device__ __forceinline__ void sg_load_tile(float (*S)[128 + 4], const float* P, int64_t s_rc, int64_t s_k,
-                                             int rc0, int nrc, int k0, int K, int tid) {
-    if (s_k == 1) {   // k contiguous: 8 threads per row (or column)
+// Stage the [8][NRC] slice k0 .. k0+7 of an operand (rows or columns rc0 ..
+// rc0+NRC-1) into S (row stride NRC + 4 floats); out-of-range elements become
+// zeros.  Element e = tid + pass * T of the 8 x NRC slice: with k contiguous,
+// 8 consecutive threads cover one row's 8 k values; otherwise NRC consecutive
+// threads cover one k.
+template <int NRC, int T>
+__device__ __forceinline__ void sg_stage(float* S, const float* P, int64_t s_rc, int64_t s_k, int rc0, int nrc,
+                                         int k0, int K, int tid) {
+    constexpr int LD = NRC + 4, NE = 8 * NRC, PASSES = (NE + T - 1) / T;
 #pragma unroll
-        for (int pass = 0; pass < 4; ++pass) {
-            const int t = tid + pass * 256, kk = t & 7, rr = t >> 3;
-            const int rc = rc0 + rr, k = k0 + kk;
-            const bool ok = rc < nrc && k < K;
-            sg_cp4(&S[kk][rr], ok ? P + (rc * s_rc + k) : P, ok ? 4 : 0);
-        }
-    } else {          // rows (or columns) contiguous: 128 threads per k
-#pragma unroll
-        for (int pass = 0; pass < 4; ++pass) {
-            const int t = tid + pass * 256, rr = t & 127, kk = t >> 7;
-            const int rc = rc0 + rr, k = k0 + kk;
-            const bool ok = rc < nrc && k < K;
-            sg_cp4(&S[kk][rr], ok ? P + (rc * s_rc + k * s_k) : P, ok ? 4 : 0);
-        }
+    for (int pass = 0; pass < PASSES; ++pass) {
+        const int e = tid + pass * T;
+        if (NE % T != 0 && e >= NE) break;
+        const int kk = (s_k == 1) ? (e & 7) : (e / NRC);
+        const int rr = (s_k == 1) ? (e >> 3) : (e % NRC);
+        const int rc = rc0 + rr, k = k0 + kk;
+        const bool ok = rc < nrc && k < K;
+        sg_cp4(S + kk * LD + rr, ok ? P + (rc * s_rc + k * s_k) : P, ok ? 4 : 0);
     }
 }
 
-__global__ void __launch_bounds__(256, 2) sgemm128_kernel(SG g) {
-    __shared__ __align__(16) float As[SG_STAGES][8][128 + 4];
-    __shared__ __align__(16) float Bs[SG_STAGES][8][128 + 4];
+// Epilogue of 4 adjacent outputs v[0..3] at row r, columns cc .. cc+3: two
+// 16-byte accesses when the output is column-contiguous and aligned (and T for
+// epilogue 1), else element by element; the values are the same either way.
+__device__ __forceinline__ void sg_store4(const SG& g, int j, int r, int cc, const float (&v)[4]) {
+    const int64_t rowoff = j * g.c_sj + r * g.c_sr;
+    if (g.c_sc == 1 && cc + 4 <= g.Cn && ((reinterpret_cast<uintptr_t>(g.C + rowoff + cc) & 15) == 0) &&
+        (g.epi != 1 || (reinterpret_cast<uintptr_t>(g.T + rowoff + cc) & 15) == 0)) {
+        float4* d4 = reinterpret_cast<float4*>(g.C + rowoff + cc);
+        float o[4] = {v[0], v[1], v[2], v[3]};
+        if (g.epi == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o[q] = act_f(g.act, o[q] + g.bias[j * g.bias_sj + cc + q]);
+        } else if (g.epi == 1) {
+            const float4 t = *reinterpret_cast<const float4*>(g.T + rowoff + cc);
+            o[0] = o[0] * act_grad_from_out(g.act, t.x);
+            o[1] = o[1] * act_grad_from_out(g.act, t.y);
+            o[2] = o[2] * act_grad_from_out(g.act, t.z);
+            o[3] = o[3] * act_grad_from_out(g.act, t.w);
+        } else if (g.epi == 2) {
+            const float4 t = *d4;
+            o[0] = t.x + o[0];
+            o[1] = t.y + o[1];
+            o[2] = t.z + o[2];
+            o[3] = t.w + o[3];
+        }
+        *d4 = make_float4(o[0], o[1], o[2], o[3]);
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c = cc + q;
+        if (c >= g.Cn) continue;
+        float* dst = g.C + rowoff + c * g.c_sc;
+        if (g.epi == 0) *dst = act_f(g.act, v[q] + g.bias[j * g.bias_sj + c]);
+        else if (g.epi == 1) *dst = v[q] * act_grad_from_out(g.act, g.T[rowoff + c * g.c_sc]);
+        else if (g.epi == 2) *dst += v[q];
+        else *dst = v[q];
+    }
+}
+
+template <int TRT, int TCT, int MINB>
+__global__ void __launch_bounds__(TRT * TCT, MINB) sgemm_tile_kernel(SG g) {
+    constexpr int T = TRT * TCT, BR = 8 * TRT, BC = 8 * TCT, LDA = BR + 4, LDB = BC + 4;
+    __shared__ __align__(16) float As[SG_STAGES][8][LDA];
+    __shared__ __align__(16) float Bs[SG_STAGES][8][LDB];
     const int j = blockIdx.z;
-    const int r0 = blockIdx.y * 128, c0 = blockIdx.x * 128;
+    const int r0 = blockIdx.y * BR, c0 = blockIdx.x * BC;
     const int tid = threadIdx.x;
-    const int tr = tid >> 4, tc = tid & 15;
+    const int tr = tid / TCT, tc = tid % TCT;
     float acc[8][8];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
@@ -154,8 +197,8 @@ __global__ void __launch_bounds__(256, 2) sgemm128_kernel(SG g) {
 #pragma unroll
     for (int p = 0; p < SG_STAGES - 1; ++p) {
         if (p < nk) {
-            sg_load_tile(As[p], A, g.a_sr, g.a_sk, r0, g.R, p * 8, g.K, tid);
-            sg_load_tile(Bs[p], B, g.b_sc, g.b_sk, c0, g.Cn, p * 8, g.K, tid);
+            sg_stage<BR, T>(&As[p][0][0], A, g.a_sr, g.a_sk, r0, g.R, p * 8, g.K, tid);
+            sg_stage<BC, T>(&Bs[p][0][0], B, g.b_sc, g.b_sk, c0, g.Cn, p * 8, g.K, tid);
         }
         sg_commit();
     }
@@ -168,17 +211,17 @@ __global__ void __launch_bounds__(256, 2) sgemm128_kernel(SG g) {
         __syncthreads();
         const int nx = t + SG_STAGES - 1;
         if (nx < nk) {
-            sg_load_tile(As[nx % SG_STAGES], A, g.a_sr, g.a_sk, r0, g.R, nx * 8, g.K, tid);
-            sg_load_tile(Bs[nx % SG_STAGES], B, g.b_sc, g.b_sk, c0, g.Cn, nx * 8, g.K, tid);
+            sg_stage<BR, T>(&As[nx % SG_STAGES][0][0], A, g.a_sr, g.a_sk, r0, g.R, nx * 8, g.K, tid);
+            sg_stage<BC, T>(&Bs[nx % SG_STAGES][0][0], B, g.b_sc, g.b_sk, c0, g.Cn, nx * 8, g.K, tid);
         }
         sg_commit();
         const int cur = t % SG_STAGES;
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
-            const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][tr * 8]);
-            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][tr * 8 + 4]);
-            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tc * 8]);
-            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tc * 8 + 4]);
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][tr * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][BR / 2 + tr * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tc * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][BC / 2 + tc * 4]);
             const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -188,58 +231,55 @@ __global__ void __launch_bounds__(256, 2) sgemm128_kernel(SG g) {
         }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");   // only empty groups remain; nothing left in flight
-    // Epilogue.  A thread's 8 outputs of a row are adjacent when the output is
-    // column-contiguous: then they move as two 16-byte accesses (and so does
-    // T for epilogue 1); the values are those of the scalar path.
-    const int cc0 = c0 + tc * 8;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        const int r = r0 + tr * 8 + i;
+        const int r = r0 + (i < 4 ? tr * 4 + i : BR / 2 + tr * 4 + i - 4);
         if (r >= g.R) continue;
-        const int64_t rowoff = j * g.c_sj + r * g.c_sr;
-        if (g.c_sc == 1 && cc0 + 8 <= g.Cn && ((reinterpret_cast<uintptr_t>(g.C + rowoff + cc0) & 15) == 0) &&
-            (g.epi != 1 || (reinterpret_cast<uintptr_t>(g.T + rowoff + cc0) & 15) == 0)) {
-            float4* d4 = reinterpret_cast<float4*>(g.C + rowoff + cc0);
-            float v[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = acc[i][q];
-            if (g.epi == 0) {
-#pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] = act_f(g.act, v[q] + g.bias[j * g.bias_sj + cc0 + q]);
-            } else if (g.epi == 1) {
-                const float4* t4 = reinterpret_cast<const float4*>(g.T + rowoff + cc0);
-                const float4 t0 = t4[0], t1 = t4[1];
-                const float t[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
-#pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] = v[q] * act_grad_from_out(g.act, t[q]);
-            } else if (g.epi == 2) {
-                const float4 o0 = d4[0], o1 = d4[1];
-                const float o[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
-#pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] = o[q] + v[q];
-            }
-            d4[0] = make_float4(v[0], v[1], v[2], v[3]);
-            d4[1] = make_float4(v[4], v[5], v[6], v[7]);
-            continue;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int cc = c0 + tc * 8 + q;
-            if (cc >= g.Cn) continue;
-            float* dst = g.C + j * g.c_sj + r * g.c_sr + cc * g.c_sc;
-            const float v = acc[i][q];
-            if (g.epi == 0) *dst = act_f(g.act, v + g.bias[j * g.bias_sj + cc]);
-            else if (g.epi == 1) *dst = v * act_grad_from_out(g.act, g.T[j * g.c_sj + r * g.c_sr + cc * g.c_sc]);
-            else if (g.epi == 2) *dst += v;
-            else *dst = v;
-        }
+        const float lo[4] = {acc[i][0], acc[i][1], acc[i][2], acc[i][3]};
+        const float hi[4] = {acc[i][4], acc[i][5], acc[i][6], acc[i][7]};
+        sg_store4(g, j, r, c0 + tc * 4, lo);
+        sg_store4(g, j, r, c0 + BC / 2 + tc * 4, hi);
     }
+}
+
+// Tile shapes (threads along rows, along columns, resident blocks per SM the
+// register budget is set for); the first is the default.
+struct SgShape { int trt, tct; };
+constexpr SgShape kSgShapes[] = {{16, 16}, {16, 25}, {25, 16}, {10, 25}, {25, 14}, {16, 14}};
+
+static void sgemm_tiles(const SG& g, int J, int shape, cudaStream_t s) {
+    const SgShape sh = kSgShapes[shape];
+    const dim3 grid((g.Cn + 8 * sh.tct - 1) / (8 * sh.tct), (g.R + 8 * sh.trt - 1) / (8 * sh.trt), J);
+    const int T = sh.trt * sh.tct;
+    switch (shape) {
+        case 0: sgemm_tile_kernel<16, 16, 2><<<grid, T, 0, s>>>(g); break;
+        case 1: sgemm_tile_kernel<16, 25, 1><<<grid, T, 0, s>>>(g); break;
+        case 2: sgemm_tile_kernel<25, 16, 1><<<grid, T, 0, s>>>(g); break;
+        case 3: sgemm_tile_kernel<10, 25, 2><<<grid, T, 0, s>>>(g); break;
+        case 4: sgemm_tile_kernel<25, 14, 1><<<grid, T, 0, s>>>(g); break;
+        default: sgemm_tile_kernel<16, 14, 2><<<grid, T, 0, s>>>(g); break;
+    }
+}
+
+// The shape whose tiles cover R x Cn with the least padding; another shape
+// replaces the 128 x 128 default only when it pads at least 5% less.
+static int sgemm_shape(int R, int Cn) {
+    auto padded = [&](const SgShape& sh) {
+        const double br = 8.0 * sh.trt, bc = 8.0 * sh.tct;
+        return std::ceil(R / br) * br * std::ceil(Cn / bc) * bc;
+    };
+    int best = 0;
+    double best_w = padded(kSgShapes[0]);
+    for (int i = 1; i < (int)(sizeof(kSgShapes) / sizeof(kSgShapes[0])); ++i) {
+        const double w = padded(kSgShapes[i]);
+        if (w < 0.95 * best_w) { best = i; best_w = w; }
+    }
+    return best;
 }
 
 static void sgemm(smc_ctx* c, const SG& g, int J) {
     if (g.R >= 128 && g.Cn >= 128) {
-        dim3 grid((g.Cn + 127) / 128, (g.R + 127) / 128, J);
-        SMC_LAUNCH(c, sgemm128_kernel<<<grid, 256, 0, c->stream>>>(g));
+        SMC_LAUNCH(c, sgemm_tiles(g, J, sgemm_shape(g.R, g.Cn), c->stream));
         return;
     }
     dim3 grid((g.Cn + 63) / 64, (g.R + 63) / 64, J);

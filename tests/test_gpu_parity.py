@@ -79,36 +79,47 @@ def test_fp32_mlp_eval_parity(chunk):
         S.smc_destroy(ctx)
 
 
-MLP_RAGGED = nn.Spec([("dense", 37, 150), ("dense", 150, 131), ("dense", 131, 3)], (37,), nn.TANH)
+# (hidden layers, rows, chunk rows): together they run every tile shape of the
+# FP32 dense GEMM.  37-150-131-3 on 203 rows in chunks of 141 leaves every tile
+# ragged (K = 37, 150, 131 off the 8-deep K step, a 3-column last tile,
+# weight-gradient rows of 150 / 131 floats whose starts alternate between
+# 16-byte aligned and not, so both epilogue store paths run) on 80 x 200
+# tiles; 224-128 in chunks of 256 and of 200 runs 128 x 112, 128 x 128,
+# 200 x 112 and 200 x 128 tiles; 400 in chunks of 256 runs 128 x 200 tiles.
+DENSE_TILE_CASES = {
+    "ragged_80x200": ((150, 131), 203, 141),
+    "128x112_128x128": ((224, 128), 600, 256),
+    "200x112_200x128": ((224, 128), 456, 200),
+    "128x200": ((400,), 300, 256),
+}
 
 
-def test_fp32_ragged_dense_tiles_parity():
-    """FP32 dense engine on shapes that leave every tile ragged: 203 rows in
-    chunks of 141 (second chunk 62 rows), K = 37, 150 and 131 (not multiples of
-    the 8-deep K step), 131 output columns (a 3-column last tile), and
-    weight-gradient rows of 150 / 131 floats (row starts alternate between
-    16-byte aligned and not, so both epilogue store paths run)."""
-    N, J = 203, 3
+@pytest.mark.parametrize("case", sorted(DENSE_TILE_CASES))
+def test_fp32_dense_tile_shapes_parity(case):
+    hidden, N, chunk = DENSE_TILE_CASES[case]
+    dims = (37,) + hidden + (3,)
+    spec = nn.Spec([("dense", a, b) for a, b in zip(dims[:-1], dims[1:])], (37,), nn.TANH)
+    J = 3
     X, y = synthetic.gaussian_mixture(N, d=37, n_classes=3, seed=21)
-    ctx, orc, _ = make_pair(MLP_RAGGED, X, y, J, seed=21, chunk=141)
+    ctx, orc, _ = make_pair(spec, X, y, J, seed=21, chunk=chunk)
     try:
-        th0 = synthetic.particles(J, MLP_RAGGED.n_params, 21, std=0.2)
+        th0 = synthetic.particles(J, spec.n_params, 21, std=0.2)
         S.smc_set_state(ctx, th0)
         S.smc_set_schedule(ctx, S.make_schedule("fb", N, N, 5))
         orc.set_schedule("fb", N, N, 5, th0)
-        lp, g, la, lb = S.smc_eval(ctx, J, MLP_RAGGED.n_params)
+        lp, g, la, lb = S.smc_eval(ctx, J, spec.n_params)
         rlp, rg, rla, rlb = oracle_eval(orc)
         assert np.allclose(la, rla, rtol=1e-5)
         assert np.allclose(lp, rlp, rtol=1e-5)
         assert _per_particle_rel(g, rg) < 1e-5
         # every parameter segment separately (a wrong tile edge shows up in one)
         off = 0
-        for L in MLP_RAGGED.layers:
+        for L in spec.layers:
             nw, nb = L[1] * L[2], L[2]
             for seg in (slice(off, off + nw), slice(off + nw, off + nw + nb)):
                 assert _per_particle_rel(g[:, seg], rg[:, seg]) < 1e-5
             off += nw + nb
-        assert off == MLP_RAGGED.n_params
+        assert off == spec.n_params
     finally:
         S.smc_destroy(ctx)
 
