@@ -115,24 +115,85 @@ __device__ __forceinline__ void sg_cp4(float* dst, const float* src, int src_byt
 __device__ __forceinline__ void sg_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void sg_wait_prev() { asm volatile("cp.async.wait_group %0;" ::"n"(SG_STAGES - 2) : "memory"); }
 
-// Stage the [8][NRC] slice k0 .. k0+7 of an operand (rows or columns rc0 ..
-// rc0+NRC-1) into S (row stride NRC + 4 floats); out-of-range elements become
-// zeros.  Element e = tid + pass * T of the 8 x NRC slice: with k contiguous,
-// 8 consecutive threads cover one row's 8 k values; otherwise NRC consecutive
-// threads cover one k.
+// Per-thread copy plan of one operand's [8][NRC] K-step slices (rows or
+// columns rc0 .. rc0+NRC-1, shared-memory row stride NRC + 4 floats), fixed
+// for the whole kernel so that a K step costs one offset, one bound test and
+// one cp.async per element.  With k contiguous (s_k == 1) the first T & ~7
+// threads copy k = tid & 7 of rows tid / 8 + p RP (RP = (T & ~7) / 8 rows per
+// pass): 8 threads read 32 contiguous bytes.  Otherwise the first KP NRC
+// threads (KP = T / NRC) copy row tid % NRC at k = tid / NRC + p KP: NRC
+// threads read one contiguous run.  Elements outside the operand are zeros.
 template <int NRC, int T>
-__device__ __forceinline__ void sg_stage(float* S, const float* P, int64_t s_rc, int64_t s_k, int rc0, int nrc,
-                                         int k0, int K, int tid) {
-    constexpr int LD = NRC + 4, NE = 8 * NRC, PASSES = (NE + T - 1) / T;
+struct SgPlan {
+    static_assert(T >= NRC && T >= 8, "one pass covers a whole row of the slice");
+    static constexpr int LD = NRC + 4;
+    static constexpr int RP = (T & ~7) / 8;
+    static constexpr int KP = T / NRC;
+    static constexpr int PK = (NRC + RP - 1) / RP, PR = (8 + KP - 1) / KP;
+    static constexpr int PASSES = PK > PR ? PK : PR;
+    static_assert(PASSES <= 32, "pass masks");
+    int64_t off0;            // element offset of pass 0 at K step 0
+    int64_t pass_stride;     // elements between passes
+    int64_t step_stride;     // elements between K steps
+    int kk0, kk_step;        // k within the step of pass p: kk0 + p kk_step
+    int soff0, soff_step;    // shared-memory offset (floats) of pass p: soff0 + p soff_step
+    uint32_t use;            // bit p: the thread copies in pass p
+    uint32_t row_ok;         // bit p: pass p's row (or column) lies inside the operand
+};
+
+template <int NRC, int T>
+__device__ __forceinline__ SgPlan<NRC, T> sg_plan(int64_t s_rc, int64_t s_k, int rc0, int nrc, int tid) {
+    using PL = SgPlan<NRC, T>;
+    PL pl;
+    pl.use = 0;
+    pl.row_ok = 0;
+    if (s_k == 1) {
+        const int kk = tid & 7, rr0 = tid >> 3;
+        pl.kk0 = kk;
+        pl.kk_step = 0;
+        pl.soff0 = kk * PL::LD + rr0;
+        pl.soff_step = PL::RP;
+        pl.off0 = (int64_t)(rc0 + rr0) * s_rc + kk;
+        pl.pass_stride = (int64_t)PL::RP * s_rc;
+        pl.step_stride = 8;
 #pragma unroll
-    for (int pass = 0; pass < PASSES; ++pass) {
-        const int e = tid + pass * T;
-        if (NE % T != 0 && e >= NE) break;
-        const int kk = (s_k == 1) ? (e & 7) : (e / NRC);
-        const int rr = (s_k == 1) ? (e >> 3) : (e % NRC);
-        const int rc = rc0 + rr, k = k0 + kk;
-        const bool ok = rc < nrc && k < K;
-        sg_cp4(S + kk * LD + rr, ok ? P + (rc * s_rc + k * s_k) : P, ok ? 4 : 0);
+        for (int p = 0; p < PL::PASSES; ++p) {
+            const int rr = rr0 + p * PL::RP;
+            if (tid < (T & ~7) && rr < NRC) {
+                pl.use |= 1u << p;
+                if (rc0 + rr < nrc) pl.row_ok |= 1u << p;
+            }
+        }
+    } else {
+        const int rr = tid % NRC, kk0 = tid / NRC;
+        pl.kk0 = kk0;
+        pl.kk_step = PL::KP;
+        pl.soff0 = kk0 * PL::LD + rr;
+        pl.soff_step = PL::KP * PL::LD;
+        pl.off0 = (int64_t)(rc0 + rr) + (int64_t)kk0 * s_k;
+        pl.pass_stride = (int64_t)PL::KP * s_k;
+        pl.step_stride = 8 * s_k;
+#pragma unroll
+        for (int p = 0; p < PL::PASSES; ++p) {
+            if (tid < PL::KP * NRC && kk0 + p * PL::KP < 8) {
+                pl.use |= 1u << p;
+                if (rc0 + rr < nrc) pl.row_ok |= 1u << p;
+            }
+        }
+    }
+    return pl;
+}
+
+// Stage K step t (k = 8 t .. 8 t + 7) of operand P into S.
+template <int NRC, int T>
+__device__ __forceinline__ void sg_stage(float* S, const SgPlan<NRC, T>& pl, const float* P, int t, int K) {
+    const int64_t st = pl.off0 + t * pl.step_stride;
+    const int k0 = 8 * t + pl.kk0;
+#pragma unroll
+    for (int p = 0; p < SgPlan<NRC, T>::PASSES; ++p) {
+        if (!((pl.use >> p) & 1u)) continue;
+        const bool ok = ((pl.row_ok >> p) & 1u) && k0 + p * pl.kk_step < K;
+        sg_cp4(S + pl.soff0 + p * pl.soff_step, ok ? P + (st + p * pl.pass_stride) : P, ok ? 4 : 0);
     }
 }
 
@@ -193,12 +254,14 @@ __global__ void __launch_bounds__(TRT * TCT, MINB) sgemm_tile_kernel(SG g) {
     const float* A = g.A + j * g.a_sj;
     const float* B = g.B + j * g.b_sj;
     const int nk = (g.K + 7) / 8;
+    const SgPlan<BR, T> pa = sg_plan<BR, T>(g.a_sr, g.a_sk, r0, g.R, tid);
+    const SgPlan<BC, T> pb = sg_plan<BC, T>(g.b_sc, g.b_sk, c0, g.Cn, tid);
     // prologue: K steps 0 .. SG_STAGES-2, one commit group each (empty past nk)
 #pragma unroll
     for (int p = 0; p < SG_STAGES - 1; ++p) {
         if (p < nk) {
-            sg_stage<BR, T>(&As[p][0][0], A, g.a_sr, g.a_sk, r0, g.R, p * 8, g.K, tid);
-            sg_stage<BC, T>(&Bs[p][0][0], B, g.b_sc, g.b_sk, c0, g.Cn, p * 8, g.K, tid);
+            sg_stage<BR, T>(&As[p][0][0], pa, A, p, g.K);
+            sg_stage<BC, T>(&Bs[p][0][0], pb, B, p, g.K);
         }
         sg_commit();
     }
@@ -211,8 +274,8 @@ __global__ void __launch_bounds__(TRT * TCT, MINB) sgemm_tile_kernel(SG g) {
         __syncthreads();
         const int nx = t + SG_STAGES - 1;
         if (nx < nk) {
-            sg_stage<BR, T>(&As[nx % SG_STAGES][0][0], A, g.a_sr, g.a_sk, r0, g.R, nx * 8, g.K, tid);
-            sg_stage<BC, T>(&Bs[nx % SG_STAGES][0][0], B, g.b_sc, g.b_sk, c0, g.Cn, nx * 8, g.K, tid);
+            sg_stage<BR, T>(&As[nx % SG_STAGES][0][0], pa, A, nx, g.K);
+            sg_stage<BC, T>(&Bs[nx % SG_STAGES][0][0], pb, B, nx, g.K);
         }
         sg_commit();
         const int cur = t % SG_STAGES;
