@@ -2,7 +2,13 @@
 marshalling only.  Host arrays are numpy arrays; device arrays are torch CUDA
 tensors (passed by data pointer).  Every call raises SMCError on a non-zero
 status.  There is no fallback: if libsmc.so is missing the import of the
-library fails loudly."""
+library fails loudly.
+
+The C calls take bare pointers and trust the caller for sizes, so the binding
+checks every array before the call (dtype, host or device placement,
+contiguity, element count against the context's J, D, rows, input width and
+outputs, recorded by smc_init) and raises TypeError / ValueError instead of
+letting the library read or write past a buffer."""
 from __future__ import annotations
 
 import ctypes as C
@@ -158,19 +164,82 @@ def load():
     return _lib
 
 
-def _ptr(a):
-    """Pointer of a numpy array (host) or torch tensor (device); None -> NULL."""
+def _numel(a):
+    return int(a.size) if isinstance(a, np.ndarray) else int(a.numel())
+
+
+def _arg(a, where, name, dtype, n=None, place=None, contiguous=True):
+    """Pointer of argument `a` (None -> NULL) after checking it: a numpy array
+    (host) or a torch tensor (host or CUDA) of dtype `dtype` (a numpy dtype,
+    or "bfloat16"), C-contiguous unless told otherwise, with n elements (None:
+    any), on place "host", "device" or either (None)."""
     if a is None:
         return None
     if isinstance(a, np.ndarray):
-        assert a.flags["C_CONTIGUOUS"], "host arrays must be C-contiguous"
-        return a.ctypes.data
-    if hasattr(a, "data_ptr"):
-        assert a.is_contiguous(), "device tensors must be contiguous"
-        return a.data_ptr()
-    if isinstance(a, int):
-        return a
-    raise TypeError(type(a))
+        if place == "device":
+            raise TypeError(f"{where}: {name} must be a CUDA tensor, got a numpy array")
+        if dtype == "bfloat16" or a.dtype != np.dtype(dtype):
+            raise TypeError(f"{where}: {name} has dtype {a.dtype}, expected {np.dtype(dtype) if dtype != 'bfloat16' else dtype}")
+        if contiguous and not a.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{where}: {name} must be C-contiguous")
+        ptr = a.ctypes.data
+    elif hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        import torch
+        want = getattr(torch, dtype if isinstance(dtype, str) else np.dtype(dtype).name)
+        if place == "device" and not a.is_cuda:
+            raise TypeError(f"{where}: {name} must be a CUDA tensor")
+        if place == "host" and a.is_cuda:
+            raise TypeError(f"{where}: {name} must be in host memory")
+        if a.dtype != want:
+            raise TypeError(f"{where}: {name} has dtype {a.dtype}, expected {want}")
+        if contiguous and not a.is_contiguous():
+            raise ValueError(f"{where}: {name} must be contiguous")
+        ptr = a.data_ptr()
+    else:
+        raise TypeError(f"{where}: {name} must be a numpy array or a torch tensor, got {type(a).__name__}")
+    if n is not None and _numel(a) != n:
+        raise ValueError(f"{where}: {name} has {_numel(a)} elements, expected {n}")
+    return ptr
+
+
+def _on_device(a):
+    return not isinstance(a, np.ndarray) and bool(getattr(a, "is_cuda", False))
+
+
+# Dimensions of every live context made by smc_init, keyed by its address:
+# particles J, parameters D, training rows N, input width F, outputs C.
+_CTX = {}
+
+
+def _key(ctx):
+    return ctx.value if isinstance(ctx, C.c_void_p) else ctx
+
+
+def _dims(ctx, where):
+    d = _CTX.get(_key(ctx))
+    if d is None:
+        raise ValueError(f"{where}: not a live context made by smc_init")
+    return d
+
+
+def _same(where, name, given, actual):
+    if given is not None and int(given) != actual:
+        raise ValueError(f"{where}: {name} = {given}, the context has {actual}")
+    return actual
+
+
+def _model_dims(model):
+    """(input width, output width) of a model by the shape rules of its layers."""
+    shp = (model.in_c, model.in_h, model.in_w)
+    for i in range(model.n_layers):
+        l = model.layers[i]
+        if l.kind == LAYER_DENSE:
+            shp = (l.n_out, 1, 1)
+        elif l.kind == LAYER_CONV:
+            shp = (l.n_out, shp[1] - l.ksize + 1, shp[2] - l.ksize + 1)
+        else:
+            shp = (shp[0], shp[1] // 2, shp[2] // 2)
+    return model.in_c * model.in_h * model.in_w, shp[0] * shp[1] * shp[2]
 
 
 def _stream(s):
@@ -218,15 +287,31 @@ def make_schedule(kind, C_, kappa, K, k_start=0, beta0=0.1, beta_reinit=0.1, del
 
 # ------------------------------------------------------------ functions
 def smc_init(model, x, y_class=None, y_value=None, cfg=None):
-    """x / y on the host (numpy) or the device (torch CUDA tensors)."""
-    on_dev = not isinstance(x, np.ndarray)
-    data = smc_data(_ptr(x), _ptr(y_class), _ptr(y_value), x.shape[0], 1 if on_dev else 0)
+    """x [N][input] float32 and y (y_class int32 or y_value float32 [N]) both
+    on the host (numpy) or both on the device (torch CUDA tensors)."""
+    W = "smc_init"
+    if cfg is None:
+        raise ValueError(f"{W}: cfg is required (make_config)")
+    F, Cout = _model_dims(model)
+    on_dev = _on_device(x)
+    place = "device" if on_dev else "host"
+    if isinstance(x, np.ndarray) or hasattr(x, "data_ptr"):
+        N = int(x.shape[0]) if len(x.shape) > 0 else 0
+    else:
+        raise TypeError(f"{W}: x must be a numpy array or a torch tensor")
+    px = _arg(x, W, "x", np.float32, N * F, place)
+    pyc = _arg(y_class, W, "y_class", np.int32, N, place)
+    pyv = _arg(y_value, W, "y_value", np.float32, N, place)
+    data = smc_data(px, pyc, pyv, N, 1 if on_dev else 0)
     ctx = C.c_void_p()
-    _check(load().smc_init(C.byref(model), C.byref(data), C.byref(cfg), C.byref(ctx)), "smc_init")
+    _check(load().smc_init(C.byref(model), C.byref(data), C.byref(cfg), C.byref(ctx)), W)
+    lib = load()
+    _CTX[_key(ctx)] = {"J": int(cfg.n_particles), "D": int(lib.smc_num_params(ctx)), "N": N, "F": F, "C": Cout}
     return ctx
 
 
 def smc_destroy(ctx):
+    _CTX.pop(_key(ctx), None)
     load().smc_destroy(ctx)
 
 
@@ -255,9 +340,9 @@ def smc_anneal_next(ctx):
 
 def smc_anneal_next_moments(ctx, moments):
     m = np.ascontiguousarray(moments, np.float64)
-    assert m.shape == (4,)
+    pm = _arg(m, "smc_anneal_next_moments", "moments", np.float64, 4, "host")
     info = smc_anneal_info()
-    _check(load().smc_anneal_next_moments(ctx, _ptr(m), C.byref(info)), "smc_anneal_next_moments", ctx)
+    _check(load().smc_anneal_next_moments(ctx, pm, C.byref(info)), "smc_anneal_next_moments", ctx)
     return info.as_dict()
 
 
@@ -266,19 +351,24 @@ def smc_set_shard(ctx, first_particle):
 
 
 def smc_draw_uniforms(ctx, n):
+    if int(n) < 0:
+        raise ValueError(f"smc_draw_uniforms: n = {n}")
     u = np.empty(int(n), np.float64)
-    _check(load().smc_draw_uniforms(ctx, int(n), _ptr(u)), "smc_draw_uniforms", ctx)
+    _check(load().smc_draw_uniforms(ctx, int(n), _arg(u, "smc_draw_uniforms", "u", np.float64)),
+           "smc_draw_uniforms", ctx)
     return u
 
 
 def smc_set_weights(ctx, wn, ess):
+    W = "smc_set_weights"
     w = np.ascontiguousarray(wn, np.float64)
-    _check(load().smc_set_weights(ctx, _ptr(w), float(ess)), "smc_set_weights", ctx)
+    pw = _arg(w, W, "wn", np.float64, _dims(ctx, W)["J"], "host")
+    _check(load().smc_set_weights(ctx, pw, float(ess)), W, ctx)
 
 
 def smc_sda_partials(ctx):
     out = np.empty(4, np.float64)
-    _check(load().smc_sda_partials(ctx, _ptr(out)), "smc_sda_partials", ctx)
+    _check(load().smc_sda_partials(ctx, _arg(out, "smc_sda_partials", "out", np.float64)), "smc_sda_partials", ctx)
     return out
 
 
@@ -289,79 +379,132 @@ def smc_resample(ctx, force=False):
 
 
 def smc_posterior_predict(ctx, x, out):
-    on_dev = 0 if isinstance(x, np.ndarray) else 1
-    _check(load().smc_posterior_predict(ctx, _ptr(x), x.shape[0], on_dev, _ptr(out)), "smc_posterior_predict", ctx)
+    """probs out [n][outputs] float32 of test rows x [n][input] float32; x and
+    out both on the host or both on the device."""
+    W = "smc_posterior_predict"
+    d = _dims(ctx, W)
+    on_dev = _on_device(x)
+    place = "device" if on_dev else "host"
+    n = int(x.shape[0])
+    px = _arg(x, W, "x", np.float32, n * d["F"], place)
+    po = _arg(out, W, "out", np.float32, n * d["C"], place)
+    _check(load().smc_posterior_predict(ctx, px, n, 1 if on_dev else 0, po), W, ctx)
     return out
 
 
+def _upload_args(ctx, W, row0, x, y_class, y_value):
+    d = _dims(ctx, W)
+    n = int(x.shape[0])
+    if row0 < 0 or row0 + n > d["N"]:
+        raise ValueError(f"{W}: rows [{row0}, {row0 + n}) outside the {d['N']} training rows")
+    return (n, _arg(x, W, "x", np.float32, n * d["F"], "host"), _arg(y_class, W, "y_class", np.int32, n, "host"),
+            _arg(y_value, W, "y_value", np.float32, n, "host"))
+
+
 def smc_upload_rows(ctx, row0, x, y_class=None, y_value=None):
-    _check(load().smc_upload_rows(ctx, row0, x.shape[0], _ptr(x), _ptr(y_class), _ptr(y_value)),
-           "smc_upload_rows", ctx)
+    """Replace training rows [row0, row0 + n) (annealed order) with host x
+    [n][input] float32 and y [n]."""
+    n, px, pyc, pyv = _upload_args(ctx, "smc_upload_rows", row0, x, y_class, y_value)
+    _check(load().smc_upload_rows(ctx, row0, n, px, pyc, pyv), "smc_upload_rows", ctx)
 
 
 def smc_upload_rows_async(ctx, row0, x, y_class=None, y_value=None):
     """Enqueue the rows' host-to-device copy and return at once; they take
     effect at the next smc_set_schedule / smc_anneal_next.  The caller keeps
     x / y alive (and unchanged) until then; pinned arrays copy asynchronously."""
-    _check(load().smc_upload_rows_async(ctx, row0, x.shape[0], _ptr(x), _ptr(y_class), _ptr(y_value)),
-           "smc_upload_rows_async", ctx)
+    n, px, pyc, pyv = _upload_args(ctx, "smc_upload_rows_async", row0, x, y_class, y_value)
+    _check(load().smc_upload_rows_async(ctx, row0, n, px, pyc, pyv), "smc_upload_rows_async", ctx)
 
 
-def smc_get_state(ctx, J, D, theta=True):
+def smc_get_state(ctx, J=None, D=None, theta=True):
+    """Particles [J][D] float32 (None with theta=False), raw log-weights [J]
+    and log pi [J]; J and D, if given, must be the context's."""
+    W = "smc_get_state"
+    d = _dims(ctx, W)
+    J, D = _same(W, "J", J, d["J"]), _same(W, "D", D, d["D"])
     th = np.empty((J, D), np.float32) if theta else None
     lw = np.empty(J, np.float64)
     lp = np.empty(J, np.float64)
-    _check(load().smc_get_state(ctx, _ptr(th), _ptr(lw), _ptr(lp)), "smc_get_state", ctx)
+    _check(load().smc_get_state(ctx, _arg(th, W, "theta", np.float32), _arg(lw, W, "logw", np.float64),
+                                _arg(lp, W, "logpi", np.float64)), W, ctx)
     return th, lw, lp
 
 
 def smc_set_state(ctx, theta=None, logw=None, logpi=None):
+    """Overwrite particles [J][D], log-weights [J] and / or log pi [J] (host;
+    None leaves that part)."""
+    W = "smc_set_state"
+    d = _dims(ctx, W)
     th = None if theta is None else np.ascontiguousarray(theta, np.float32)
     lw = None if logw is None else np.ascontiguousarray(logw, np.float64)
     lp = None if logpi is None else np.ascontiguousarray(logpi, np.float64)
-    _check(load().smc_set_state(ctx, _ptr(th), _ptr(lw), _ptr(lp)), "smc_set_state", ctx)
+    args = (_arg(th, W, "theta", np.float32, d["J"] * d["D"], "host"),
+            _arg(lw, W, "logw", np.float64, d["J"], "host"), _arg(lp, W, "logpi", np.float64, d["J"], "host"))
+    _check(load().smc_set_state(ctx, *args), W, ctx)
 
 
 def smc_set_noise(ctx, z):
+    """Standard-normal momentum draws z [J][D] (host) for the next move."""
+    W = "smc_set_noise"
+    d = _dims(ctx, W)
     z = np.ascontiguousarray(z, np.float32)
-    _check(load().smc_set_noise(ctx, _ptr(z)), "smc_set_noise", ctx)
+    pz = _arg(z, W, "z", np.float32, d["J"] * d["D"], "host")
+    _check(load().smc_set_noise(ctx, pz), W, ctx)
 
 
 def smc_set_uniforms(ctx, u):
     u = np.ascontiguousarray(np.atleast_1d(u), np.float64)
-    _check(load().smc_set_uniforms(ctx, _ptr(u), len(u)), "smc_set_uniforms", ctx)
+    _check(load().smc_set_uniforms(ctx, _arg(u, "smc_set_uniforms", "u", np.float64, None, "host"), len(u)),
+           "smc_set_uniforms", ctx)
 
 
-def smc_eval(ctx, J, D):
+def smc_eval(ctx, J=None, D=None):
+    """log pi [J], log-likelihood gradient [J][D] and the two region sums [J]
+    at the current particles; J and D, if given, must be the context's."""
+    W = "smc_eval"
+    d = _dims(ctx, W)
+    J, D = _same(W, "J", J, d["J"]), _same(W, "D", D, d["D"])
     lp = np.empty(J, np.float64)
     g = np.empty((J, D), np.float32)
     la = np.empty(J, np.float64)
     lb = np.empty(J, np.float64)
-    _check(load().smc_eval(ctx, _ptr(lp), _ptr(g), _ptr(la), _ptr(lb)), "smc_eval", ctx)
+    _check(load().smc_eval(ctx, _arg(lp, W, "logpi", np.float64), _arg(g, W, "grad", np.float32),
+                           _arg(la, W, "la", np.float64), _arg(lb, W, "lb", np.float64)), W, ctx)
     return lp, g, la, lb
 
 
 def smc_set_state_device(ctx, theta):
     """Overwrite the particles from a contiguous float32 CUDA tensor [J, D]."""
-    _check(load().smc_set_state_device(ctx, _ptr(theta)), "smc_set_state_device", ctx)
+    W = "smc_set_state_device"
+    d = _dims(ctx, W)
+    pt = _arg(theta, W, "theta", np.float32, d["J"] * d["D"], "device")
+    _check(load().smc_set_state_device(ctx, pt), W, ctx)
 
 
 def smc_eval_device(ctx, logpi=None, grad=None):
     """Enqueue log pi [J] (float64) and grad log pi [J, D] (float32) of the
     current target into CUDA tensors (either may be None)."""
-    _check(load().smc_eval_device(ctx, _ptr(logpi), _ptr(grad)), "smc_eval_device", ctx)
+    W = "smc_eval_device"
+    d = _dims(ctx, W)
+    pl = _arg(logpi, W, "logpi", np.float64, d["J"], "device")
+    pg = _arg(grad, W, "grad", np.float32, d["J"] * d["D"], "device")
+    _check(load().smc_eval_device(ctx, pl, pg), W, ctx)
 
 
-def smc_get_weights(ctx, J):
+def smc_get_weights(ctx, J=None):
+    W = "smc_get_weights"
+    J = _same(W, "J", J, _dims(ctx, W)["J"])
     w = np.empty(J, np.float64)
-    _check(load().smc_get_weights(ctx, _ptr(w)), "smc_get_weights", ctx)
+    _check(load().smc_get_weights(ctx, _arg(w, W, "wn", np.float64)), W, ctx)
     return w
 
 
 def smc_learned_params(ctx, set_params=None):
+    W = "smc_learned_params"
     got = np.empty(LEARNED_NUM_PARAMS, np.float32)
     sp = None if set_params is None else np.ascontiguousarray(set_params, np.float32)
-    _check(load().smc_learned_params(ctx, _ptr(got), _ptr(sp)), "smc_learned_params", ctx)
+    _check(load().smc_learned_params(ctx, _arg(got, W, "get", np.float32),
+                                     _arg(sp, W, "set", np.float32, LEARNED_NUM_PARAMS, "host")), W, ctx)
     return got
 
 
@@ -372,10 +515,12 @@ def smc_learned_train(ctx, epochs, lr):
 
 
 def smc_learned_data(ctx, cap=16384):
+    W = "smc_learned_data"
     n = C.c_int64(cap)
     F = np.empty((cap, 8), np.float32)
     T = np.empty((cap, 2), np.float32)
-    _check(load().smc_learned_data(ctx, C.byref(n), _ptr(F), _ptr(T)), "smc_learned_data", ctx)
+    _check(load().smc_learned_data(ctx, C.byref(n), _arg(F, W, "features", np.float32),
+                                   _arg(T, W, "targets", np.float32)), W, ctx)
     k = min(cap, n.value)
     return F[:k].copy(), T[:k].copy()
 
@@ -385,9 +530,13 @@ def smc_learned_reset_data(ctx):
 
 
 def smc_learned_load_data(ctx, F, T):
+    W = "smc_learned_load_data"
     F = np.ascontiguousarray(F, np.float32)
     T = np.ascontiguousarray(T, np.float32)
-    _check(load().smc_learned_load_data(ctx, _ptr(F), _ptr(T), F.shape[0]), "smc_learned_load_data", ctx)
+    n = int(F.shape[0])
+    pf = _arg(F, W, "features", np.float32, 8 * n, "host")
+    pt = _arg(T, W, "targets", np.float32, 2 * n, "host")
+    _check(load().smc_learned_load_data(ctx, pf, pt, n), W, ctx)
 
 
 def smc_num_segments(ctx):
@@ -395,34 +544,43 @@ def smc_num_segments(ctx):
 
 
 def smc_learned_last(ctx, groups=1):
+    W = "smc_learned_last"
     ns = smc_num_segments(ctx)
     F = np.empty((ns, 8), np.float32)
     cand = np.empty((max(groups, 1), ns + 1), np.float32)
     sc = np.empty(max(groups, 1) + 1, np.float64)
-    _check(load().smc_learned_last(ctx, _ptr(F), _ptr(cand), _ptr(sc)), "smc_learned_last", ctx)
+    _check(load().smc_learned_last(ctx, _arg(F, W, "features", np.float32), _arg(cand, W, "candidates", np.float32),
+                                   _arg(sc, W, "scores", np.float64)), W, ctx)
     return F, cand, sc
 
 
 def smc_k_learned_loss_grad(F, T, params, stream=None):
+    W = "smc_k_learned_loss_grad"
     F = np.ascontiguousarray(F, np.float32)
     T = np.ascontiguousarray(T, np.float32)
     P = np.ascontiguousarray(params, np.float32)
+    n = int(F.shape[0])
     g = np.empty(LEARNED_NUM_PARAMS, np.float32)
     loss = C.c_double(0.0)
-    _check(load().smc_k_learned_loss_grad(_ptr(F), _ptr(T), F.shape[0], _ptr(P), _ptr(g), C.byref(loss),
-                                          _stream(stream)), "smc_k_learned_loss_grad")
+    args = (_arg(F, W, "features", np.float32, 8 * n, "host"), _arg(T, W, "targets", np.float32, 2 * n, "host"), n,
+            _arg(P, W, "params", np.float32, LEARNED_NUM_PARAMS, "host"), _arg(g, W, "grad", np.float32))
+    _check(load().smc_k_learned_loss_grad(*args, C.byref(loss), _stream(stream)), W)
     return loss.value, g
 
 
-def smc_get_permutation(ctx, N):
+def smc_get_permutation(ctx, N=None):
+    W = "smc_get_permutation"
+    N = _same(W, "N", N, _dims(ctx, W)["N"])
     p = np.empty(N, np.int32)
-    _check(load().smc_get_permutation(ctx, _ptr(p)), "smc_get_permutation", ctx)
+    _check(load().smc_get_permutation(ctx, _arg(p, W, "perm", np.int32)), W, ctx)
     return p
 
 
-def smc_get_ancestors(ctx, J):
+def smc_get_ancestors(ctx, J=None):
+    W = "smc_get_ancestors"
+    J = _same(W, "J", J, _dims(ctx, W)["J"])
     a = np.empty(J, np.int32)
-    _check(load().smc_get_ancestors(ctx, _ptr(a)), "smc_get_ancestors", ctx)
+    _check(load().smc_get_ancestors(ctx, _arg(a, W, "ancestors", np.int32)), W, ctx)
     return a
 
 
@@ -438,10 +596,12 @@ def smc_restore(ctx, path):
 
 
 def smc_get_counters(ctx):
+    W = "smc_get_counters"
     n = C.c_int64(0)
     t = np.zeros(N_FAMILIES, np.float64)
     calls = np.zeros(N_FAMILIES, np.int64)
-    _check(load().smc_get_counters(ctx, C.byref(n), _ptr(t), N_FAMILIES, _ptr(calls)), "smc_get_counters", ctx)
+    _check(load().smc_get_counters(ctx, C.byref(n), _arg(t, W, "ms", np.float64), N_FAMILIES,
+                                   _arg(calls, W, "calls", np.int64)), W, ctx)
     return int(n.value), dict(zip(FAMILIES, t.tolist())), dict(zip(FAMILIES, calls.tolist()))
 
 
@@ -450,43 +610,76 @@ def smc_reset_counters(ctx):
 
 
 def smc_k_normalise(logw_dev, wn_dev, ess_dev, stream=None):
-    _check(load().smc_k_normalise(_ptr(logw_dev), logw_dev.numel(), _ptr(wn_dev), _ptr(ess_dev), _stream(stream)),
-           "smc_k_normalise")
+    """wn [J] and ESS [1] (float64 CUDA tensors) of log-weights [J] (float64 CUDA)."""
+    W = "smc_k_normalise"
+    pl = _arg(logw_dev, W, "logw", np.float64, None, "device")
+    J = _numel(logw_dev)
+    pw = _arg(wn_dev, W, "wn", np.float64, J, "device")
+    pe = _arg(ess_dev, W, "ess", np.float64, 1, "device")
+    _check(load().smc_k_normalise(pl, J, pw, pe, _stream(stream)), W)
+
+
+def _resample_args(W, wn_dev, kind, u, anc_dev, J):
+    pw = _arg(wn_dev, W, "wn", np.float64, None, "device")
+    J = _numel(wn_dev) if J is None else int(J)
+    if J < 0 or J > _numel(wn_dev):
+        raise ValueError(f"{W}: J = {J} for {_numel(wn_dev)} weights")
+    u = np.ascontiguousarray(np.atleast_1d(u), np.float64)
+    need = 1 if kind == RESAMPLE_SYSTEMATIC else J
+    if len(u) < need:
+        raise ValueError(f"{W}: {len(u)} uniforms, the resampler reads {need}")
+    pu = _arg(u, W, "u", np.float64, None, "host")
+    pa = _arg(anc_dev, W, "ancestors", np.int32, None, "device")
+    if _numel(anc_dev) < J:
+        raise ValueError(f"{W}: ancestors has {_numel(anc_dev)} elements, expected {J}")
+    return pw, J, pu, pa, u
 
 
 def smc_k_resample(wn_dev, kind, u, anc_dev, stream=None):
-    u = np.ascontiguousarray(np.atleast_1d(u), np.float64)
-    _check(load().smc_k_resample(_ptr(wn_dev), wn_dev.numel(), kind, _ptr(u), _ptr(anc_dev), _stream(stream)),
-           "smc_k_resample")
+    """Ancestors [J] (int32 CUDA) from normalised weights [J] (float64 CUDA)
+    and host uniforms (1 for systematic, J for multinomial)."""
+    W = "smc_k_resample"
+    pw, J, pu, pa, _keep = _resample_args(W, wn_dev, kind, u, anc_dev, None)
+    _check(load().smc_k_resample(pw, J, kind, pu, pa, _stream(stream)), W)
 
 
 def smc_k_resample_noalloc(wn_dev, kind, u, anc_dev, stream=None, J=None):
-    u = np.ascontiguousarray(np.atleast_1d(u), np.float64)
-    n = wn_dev.numel() if J is None else J
-    st = load().smc_k_resample_noalloc(_ptr(wn_dev), n, kind, _ptr(u), _ptr(anc_dev), _stream(stream))
+    W = "smc_k_resample_noalloc"
+    pw, n, pu, pa, _keep = _resample_args(W, wn_dev, kind, u, anc_dev, J)
+    st = load().smc_k_resample_noalloc(pw, n, kind, pu, pa, _stream(stream))
     if st != 0:
-        raise SMCError(st, "smc_k_resample_noalloc", (load().smc_last_error(None) or b"").decode())
+        raise SMCError(st, W, (load().smc_last_error(None) or b"").decode())
 
 
 def smc_k_philox_normals(seed, stream_id, iteration, offset, out_dev, stream=None):
-    _check(load().smc_k_philox_normals(seed, stream_id, iteration, offset, out_dev.numel(), _ptr(out_dev),
-                                       _stream(stream)), "smc_k_philox_normals")
+    W = "smc_k_philox_normals"
+    po = _arg(out_dev, W, "out", np.float32, None, "device")
+    _check(load().smc_k_philox_normals(seed, stream_id, iteration, offset, _numel(out_dev), po, _stream(stream)), W)
 
 
 def smc_k_philox_u32(k0, k1, c2, c3, out_dev, stream=None):
-    _check(load().smc_k_philox_u32(k0, k1, c2, c3, out_dev.shape[0], _ptr(out_dev), _stream(stream)),
-           "smc_k_philox_u32")
+    """Raw Philox4x32-10 blocks into out_dev [n][4] (int32 CUDA tensor, read as u32)."""
+    W = "smc_k_philox_u32"
+    if len(out_dev.shape) != 2 or out_dev.shape[1] != 4:
+        raise ValueError(f"{W}: out must be [n][4], got {tuple(out_dev.shape)}")
+    po = _arg(out_dev, W, "out", np.int32, None, "device")
+    _check(load().smc_k_philox_u32(k0, k1, c2, c3, out_dev.shape[0], po, _stream(stream)), W)
 
 
 def smc_k_gemm_bf16(A, B, Cout, accumulate=False, stream=None):
     """A [M][K], B [N][K] BF16 and Cout [M][N] FP32 device tensors with unit
     inner stride (row pitches may exceed the logical width)."""
+    W = "smc_k_gemm_bf16"
+    for t, name, dt in ((A, "A", "bfloat16"), (B, "B", "bfloat16"), (Cout, "Cout", np.float32)):
+        _arg(t, W, name, dt, None, "device", contiguous=False)
+        if len(t.shape) != 2 or t.stride(1) != 1:
+            raise ValueError(f"{W}: {name} must be a 2-D tensor with unit inner stride")
     M, K = A.shape
     N = B.shape[0]
-    assert A.stride(1) == 1 and B.stride(1) == 1 and Cout.stride(1) == 1
+    if B.shape[1] != K or tuple(Cout.shape) != (M, N):
+        raise ValueError(f"{W}: shapes A {tuple(A.shape)}, B {tuple(B.shape)}, Cout {tuple(Cout.shape)} do not match")
     _check(load().smc_k_gemm_bf16(A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0), Cout.data_ptr(),
-                                  Cout.stride(0), M, N, K, 1 if accumulate else 0, _stream(stream)),
-           "smc_k_gemm_bf16")
+                                  Cout.stride(0), M, N, K, 1 if accumulate else 0, _stream(stream)), W)
 
 
 def smc_k_wait_probe(limit_ms, arrive, stream=None):
