@@ -113,11 +113,6 @@ smc_status sync_and_check(smc_ctx* c, const char* what) {
     return SMC_OK;
 }
 
-// Set the target's row regions for the current iteration (fixed schedules) or
-// from the SDA state.
-struct SdaHost { int64_t m_full = 0, block = 0; };
-SdaHost g_unused;
-
 // First row of iteration k's subset: the cumulative schedules take a prefix;
 // the fresh kinds move an M-row window by M rows per iteration, wrapping.
 int64_t subset_start(int kind, int64_t k, int64_t N, int64_t M) {
@@ -125,6 +120,8 @@ int64_t subset_start(int kind, int64_t k, int64_t N, int64_t M) {
     return (fresh && M < N) ? (int64_t)(((unsigned __int128)k * (uint64_t)M) % (uint64_t)N) : 0;
 }
 
+// The target's row regions of the current iteration under a fixed schedule:
+// M_k rows from subset_start, all with coefficient N / M_k (1 when unscaled).
 void set_regions_fixed(smc_ctx* c) {
     const smc_schedule& s = c->sched;
     const int64_t M = subset_size(s.kind, c->k, c->N, s.C, s.kappa, s.K);
@@ -356,11 +353,6 @@ smc_status smc_init(const smc_model* model, const smc_data* train, const smc_con
         return bad("precision");
     }
 
-    smc_status st = SMC_OK;
-    auto cfail = [&](cudaError_t e, const char* w) {
-        st = cuda_check(c, e, w);
-        return st;
-    };
     cudaGetDevice(&c->device);
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
 
@@ -384,6 +376,7 @@ smc_status smc_init(const smc_model* model, const smc_data* train, const smc_con
         cudaFree(xsrc); cudaFree(ysrc); cudaFree(yvsrc); cudaFree(perm_dev);
         free_all(c);
         delete c;
+        cudaGetLastError();   // a failed allocation is not sticky: clear it for later launch checks
         return SMC_ENOMEM;
     }
     const float* xs = train->x;
@@ -403,11 +396,8 @@ smc_status smc_init(const smc_model* model, const smc_data* train, const smc_con
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(xsrc); cudaFree(ysrc); cudaFree(yvsrc); cudaFree(perm_dev);
     if (e != cudaSuccess) {
-        cfail(e, "data upload");
-        std::string m = c->last_error;
         free_all(c);
         delete c;
-        (void)m;
         return SMC_ECUDA;
     }
 
