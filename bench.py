@@ -158,6 +158,22 @@ def make_data(n, seed=0):
     return synthetic.template_images(n, seed=seed)
 
 
+def host_threads():
+    """Threads the oracle's numpy BLAS may use: an explicit thread-count
+    variable when set, else the cores this process may run on."""
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        try:
+            n = int(os.environ.get(var, ""))
+        except ValueError:
+            continue
+        if n > 0:
+            return n
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
 def cpu_baseline(seconds=12.0, J_s=2, M_s=2000):
     """The FP64 oracle's gradient evaluation on a bounded sample of the
     workload: J_s particles x M_s rows of the same model and data."""
@@ -177,7 +193,7 @@ def cpu_baseline(seconds=12.0, J_s=2, M_s=2000):
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    return {"value": n_eval * M_s / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+    return {"value": n_eval * M_s / el, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
             "sample": f"{n_eval} FP64 oracle gradient evaluations of single particles over {M_s} rows "
                       f"({el:.1f} s, numpy BLAS default threads)"}
 
@@ -205,7 +221,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
                              "sample": f"each step: one FP64 oracle SMC move (S={S_LF}) of {J_s} particles over "
                                        f"{M_s} rows (bounded sample of the workload)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
