@@ -305,8 +305,9 @@ __global__ void __launch_bounds__(TRT * TCT, MINB) sgemm_tile_kernel(SG g) {
     }
 }
 
-// Tile shapes (threads along rows, along columns, resident blocks per SM the
-// register budget is set for); the first is the default.
+// Tile shapes (threads along rows, threads along columns); the first is the
+// default.  sgemm_tiles launches each with a register budget for two resident
+// blocks per SM when two fit (blocks of up to 256 threads), else one.
 struct SgShape { int trt, tct; };
 constexpr SgShape kSgShapes[] = {{16, 16}, {16, 25}, {25, 16}, {10, 25}, {25, 14}, {16, 14}};
 
