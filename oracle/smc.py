@@ -1,8 +1,9 @@
 """The data-annealed SMC sampler in float64 (oracle side; test infrastructure only).
 
-Order of one iteration (reading r9, the paper is silent):
-    step (move + reweight + normalise + ESS) -> anneal_next -> resample.
-`set_schedule` is iteration 0 (eq. init_weight).  The target of iteration k is
+Order of the calls (reading r9, the paper is silent): after `set_schedule`
+(iteration 0, eq. init_weight) each iteration k runs
+    anneal_next (target k; SDA moments from the previous step's weights)
+    -> resample (if J_eff < J/2) -> step (move + reweight + normalise + ESS).  The target of iteration k is
     log pi_k(theta) = -|theta|^2 / (2 sigma^2) + sum_{i in D_k} c_i log p(y_i | theta)
 with prior N(0, sigma^2 I) (reading r4) and per-row coefficients
     fixed schedules: c_i = N / M_k on D_k = rows [0, M_k)  (eq. approx-grad; reading r1
