@@ -406,8 +406,9 @@ smc_status smc_k_resample(const double* wn_dev, int32_t J, int32_t kind,
                           const double* u_host, int32_t* ancestors_dev, void* stream);
 
 /* Same result as smc_k_resample, for callers that cannot allocate device
- * memory: code that runs while a stream is being captured, code under an
- * allocator that owns all device memory, or a loop that cannot afford the
+ * memory: code under an allocator that owns all device memory (a framework's
+ * caching allocator that has reserved the GPU, where a cudaMalloc of its own
+ * would fail or fragment the pool), or a loop that cannot afford the
  * device-wide synchronisation a cudaFree implies.  It calls no cudaMalloc,
  * cudaFree or allocating library routine; the uniforms are staged in a static
  * 32 KiB device array (4096 doubles) that every GPU loading the library keeps

@@ -41,7 +41,7 @@ enum { ERR_PRODUCER = 0x101, ERR_MMA = 0x102, ERR_EPILOGUE = 0x103 };
 struct GemmArgs {
     int M, N, K;
     int tiles_m, tiles_n, kslices, kb_total, kb_per_slice, num_units;
-    int cs;                 // CTAs per cluster sharing each B tile (units are per cluster)
+    int cs;                 // CTAs per cluster: consecutive m-tiles of one B tile (units are per cluster)
     int epi;
     void* out;              // BF16 [M][ldo] or FP32 [M][ldo] (+ ks * slice_stride)
     int64_t ldo;
@@ -149,7 +149,6 @@ struct Cfg {
     static constexpr int SMEM = STAGES * STAGE_BYTES + STAGING + 1024 /*align*/ + 256 /*barriers*/;
     static_assert(BN % 16 == 0 && N0 % 16 == 0 && N1 % 16 == 0, "N must be a multiple of 16");
     static_assert(BN % BNBOX == 0 && BNBOX <= 256, "TMA box rows <= 256");
-    static_assert(CS == 1 || BN == CS * BNBOX, "each CTA of a cluster loads one B slice");
     static_assert((BNBOX * 128) % 1024 == 0, "B slices start on a swizzle atom");
     static_assert(ACC * BN <= 512, "TMEM has 512 columns");
     static_assert(SMEM <= 232448, "shared memory");
@@ -162,7 +161,6 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     using C = Cfg<BN, BNBOX, STAGES, CS>;
     const int rank = CS > 1 ? (int)cluster_rank() : 0;
     const int cid = blockIdx.x / CS, ncl = gridDim.x / CS;
-    constexpr uint16_t kMask = (uint16_t)((1u << CS) - 1);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* staging = smem + STAGES * C::STAGE_BYTES;
@@ -176,8 +174,8 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        // empty[s] completes when the MMAs of every CTA of the cluster released stage s
-        for (int s = 0; s < STAGES; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, CS); }
+        // every CTA fills and drains its own stages (no copy reaches another CTA)
+        for (int s = 0; s < STAGES; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
         for (int a = 0; a < C::ACC; ++a) { mbar_init(tfull + a, 1); mbar_init(tempty + a, 4); }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -186,7 +184,6 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     if (warp == 1) tmem_alloc(tslot, C::TCOLS);
     tc_fence_before();
     __syncthreads();
-    if (CS > 1) cluster_sync();   // the peers' barriers exist before any multicast reaches them
     tc_fence_after();
     const uint32_t tbase = *tslot;
 
@@ -207,15 +204,11 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     uint8_t* sa = smem + stage * C::STAGE_BYTES;
                     uint8_t* sb = sa + C::A_BYTES;
                     tma_load_2d(sa, &tmA, kb * BK, tm * BM, full + stage);
-                    if (CS == 1) {
+                    // the whole B tile into this CTA's own shared memory; the other
+                    // CTAs of the cluster read the same rows, mostly from L2
 #pragma unroll
-                        for (int b = 0; b < BN / BNBOX; ++b)
-                            tma_load_2d(sb + b * BNBOX * 128, &tmB, kb * BK, tn * BN + b * BNBOX, full + stage);
-                    } else {
-                        // this CTA's slice of the shared B tile, delivered to all CTAs of the cluster
-                        tma_load_2d_mc(sb + rank * BNBOX * 128, &tmB, kb * BK, tn * BN + rank * BNBOX, full + stage,
-                                       kMask);
-                    }
+                    for (int b = 0; b < BN / BNBOX; ++b)
+                        tma_load_2d(sb + b * BNBOX * 128, &tmB, kb * BK, tn * BN + b * BNBOX, full + stage);
                     ++issued;
                     if (++stage == STAGES) { stage = 0; ph ^= 1; }
                 }
@@ -258,8 +251,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         umma_bf16(dt, ad, sdesc(sb + k * 32), ID0, accum);
                         if (C::N1 > 0) umma_bf16(dt + C::N0, ad, sdesc(sb + C::N0 * 128 + k * 32), ID1, accum);
                     }
-                    if (CS == 1) umma_commit(empty + stage);
-                    else umma_commit_mc(empty + stage, kMask);   // frees the stage in every CTA of the cluster
+                    umma_commit(empty + stage);
                     if (++stage == STAGES) { stage = 0; ph ^= 1; }
                 }
                 if (!ok) break;
@@ -359,7 +351,6 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
     tc_fence_before();
     __syncthreads();
-    if (CS > 1) cluster_sync();   // no CTA leaves while a peer may still multicast into it
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tbase, C::TCOLS);

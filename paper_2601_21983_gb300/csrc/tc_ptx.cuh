@@ -1,5 +1,5 @@
 // Inline PTX wrappers for the Blackwell tensor-core kernels: mbarriers, TMA
-// (tiled loads, multicast loads, bulk stores), TMEM allocation and loads,
+// (tiled loads, bulk stores), TMEM allocation and loads,
 // tcgen05.mma / commit, shared-memory matrix and instruction descriptors, and
 // thread-block-cluster helpers.  Every wait built on these is bounded by the
 // caller.
@@ -96,16 +96,6 @@ static __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap*
         : "memory");
 }
 
-// TMA load delivered to the same shared-memory offset of every CTA in ctaMask,
-// each completing tx bytes on the mbarrier at the same offset.
-static __device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar,
-                                               uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3}], [%4], %5;"
-        ::"r"(su32(dst)), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(su32(bar)), "h"(mask)
-        : "memory");
-}
 static __device__ __forceinline__ uint32_t cluster_rank() {
     uint32_t r;
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -172,13 +162,6 @@ static __device__ __forceinline__ void umma_commit(uint64_t* b) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
                  : "memory");
 }
-// Same, arriving on the mbarrier at this offset in every CTA of ctaMask.
-static __device__ __forceinline__ void umma_commit_mc(uint64_t* b, uint16_t mask) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-                 ::"r"(su32(b)), "h"(mask)
-                 : "memory");
-}
-
 // ---- CTA-pair (cta_group::2) forms: the two CTAs of a cluster pair run one
 // M = 256 MMA; each stages its own 128 rows of A and half of the B rows.
 // TMEM allocation is collective: one warp of each CTA of the pair executes it.

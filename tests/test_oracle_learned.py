@@ -65,3 +65,28 @@ def test_group_scores():
     wn = np.array([0.25, 0.25, 0.5, 0.0])
     s = L.group_scores(th0, th1, wn, [[0, 1], [2, 3]])
     assert np.allclose(s, [1.5 * (0.25 / 0.125) / 2, 2.0 * (0.25 / 0.25) / 2])
+
+
+def test_adam_first_two_steps_by_hand():
+    """Adam (Kingma & Ba 2015) on a network whose first layer and output
+    weights are zero: the hidden units are tanh(0) = 0, the output is b2 and the
+    loss gradient is g = b2 - mean(T) for b2 and exactly 0 elsewhere.  With
+    mean(T) = (1, -2), b2 = 0, lr = 0.5, beta1 = 0.9, beta2 = 0.999:
+      step 1: m = 0.1 g, v = 0.001 g^2, bias-corrected m^ = g, v^ = g^2, so
+              b2 = -lr g / (|g| + eps) = (0.5, -0.5) up to eps;
+      step 2: g = (-0.5, 1.5), m = 0.09 (-1, 2) + 0.1 g = (-0.14, 0.33),
+              v = 0.000999 (1, 4) + 0.001 g^2 = (0.001249, 0.006246),
+              m^ = m / 0.19, v^ = v / 0.001999, b2 -= lr m^ / (sqrt(v^) + eps):
+              b2 = (0.5 + 0.4660898..., -0.5 - 0.4912875...).
+    Every other parameter keeps its (zero) gradient and does not move."""
+    F = np.random.default_rng(4).normal(size=(6, 8))
+    T = np.tile(np.array([1.0, -2.0]), (6, 1)) + np.array([[0.3, -0.1]]) * np.array([[1], [-1], [1], [-1], [1],
+                                                                                      [-1]])
+    p0 = np.zeros(L.N_PARAMS)
+    p1, _ = L.adam(p0, F, T, 1, 0.5)
+    b2 = p1[-2:]
+    assert np.allclose(b2, [0.5, -0.5], rtol=1e-7) and np.all(p1[:-2] == 0.0)
+    p2, _ = L.adam(p0, F, T, 2, 0.5)
+    step2 = np.array([0.46608981940570154, 0.4912875407292165])
+    assert np.allclose(p2[-2:], [0.5 + step2[0], -0.5 - step2[1]], rtol=1e-7, atol=1e-12)
+    assert np.all(p2[:-2] == 0.0)

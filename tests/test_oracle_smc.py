@@ -250,3 +250,70 @@ def test_fresh_batch_target_is_the_prefix_target_of_rotated_data():
     a, b = fresh.target(th[0]), plain.target(th[0])
     assert np.isclose(a[0], b[0], rtol=1e-13) and np.allclose(a[1], b[1], rtol=1e-12, atol=1e-14)
     assert list(fresh.rows()) == list(range(3, 13))
+
+
+# ------------------------------------------- SDA wiring of the sampler (p1, p7)
+def _gauss_nll(Xb, yp, theta, lo, hi, sn):
+    """-sum_{i in [lo, hi)} log N(y_i; x_i . theta, sn^2), written out here
+    (not through the oracle's network code)."""
+    r = yp[lo:hi] - Xb[lo:hi] @ theta
+    return float(0.5 * np.sum(r * r) / sn ** 2 + (hi - lo) * math.log(math.sqrt(2.0 * math.pi) * sn))
+
+
+def _tempered_check(s, Xb, yp, coef, sn):
+    """Weighted mean of the particles against the closed-form posterior whose
+    likelihood exponents are `coef` (per row), within Monte Carlo error."""
+    mu, Sig = nn.linear_gaussian_posterior(Xb, yp, coef, 1.0, sn)
+    m = s.wn @ s.theta
+    se = np.sqrt(np.diag(Sig) / s.ess) * 3.0
+    return bool(np.all(np.abs(m - mu) < 4.0 * se + 1e-3))
+
+
+@pytest.mark.parametrize("seed", [2, 3])
+def test_sda_sampler_tracks_tempered_posteriors_and_beta_rule(seed):
+    """SDA inside the sampler (Sec. 3.1, eq. sda_initial_target and the
+    annealed target after it) on a linear-Gaussian model, where every target is
+    Gaussian.  (i) Before each temperature update the next beta is recomputed
+    from the pre-resampling weights with Omega (fully included rows) and
+    Omega_hat (tempered block) evaluated here from scratch: beta moves by
+    dS / |Var(Omega_hat) + Cov(Omega, Omega_hat)|, clipped to 1.  A swap of
+    Omega and Omega_hat, a sign slip or stale moments in the sampler's wiring
+    changes that value.  (ii) After each move the weighted particle mean
+    matches the closed-form posterior with exponent 1 on the fully included
+    rows, beta on the block and 0 elsewhere.  A planted mistake in (ii) (the
+    block at exponent 1 while beta < 1) must be rejected somewhere along the run."""
+    d, N, J, sn, K = 2, 40, 400, 0.5, 40
+    X, yv, _ = synthetic.linear_gaussian(N, d, seed=seed, noise_std=sn)
+    spec = nn.Spec([("dense", d, 1)], (d,), nn.IDENTITY, nn.GAUSSIAN, noise_sigma=sn)
+    perm = rng.fisher_yates_permutation(N, seed)
+    s = smc.Sampler(spec, X, yv, J, perm, prior_sigma=1.0)
+    s.set_schedule("sda", 5, 5, K, synthetic.particles(J, spec.n_params, 60 + seed))
+    Xb = np.concatenate([X[perm].astype(np.float64), np.ones((N, 1))], axis=1)
+    yp = yv[perm].astype(np.float64)
+    g = rng.SplitMix64(seed)
+    n_beta, n_append, n_planted_rejected = 0, 0, 0
+    for k in range(1, K):
+        full, block, beta = s.sda.m_full, s.sda.block, s.sda.beta
+        w = s.wn.copy()
+        om = np.array([_gauss_nll(Xb, yp, th, 0, full, sn) for th in s.theta])
+        oh = np.array([_gauss_nll(Xb, yp, th, full, full + block, sn) for th in s.theta])
+        appended = s.anneal_next()
+        if beta < 1.0:
+            e = lambda a: float(np.dot(w, a))
+            den = (e(oh * oh) - e(oh) ** 2) + (e(om * oh) - e(om) * e(oh))
+            expect = min(beta + 1.0 / abs(den), 1.0)
+            assert not appended and s.sda.beta == pytest.approx(expect, rel=1e-9), (k, s.sda.beta, expect)
+            n_beta += 1
+        elif full + block < N:
+            assert appended and s.sda.m_full == full + block and s.sda.beta == 0.1
+            n_append += 1
+        s.resample(u=g.next_double())
+        s.step(0.05, 3, synthetic.normals((J, spec.n_params), 500 * seed + k))
+        full, block, beta = s.sda.m_full, s.sda.block, s.sda.beta
+        coef = np.concatenate([np.ones(full), np.full(block, beta), np.zeros(N - full - block)])
+        assert _tempered_check(s, Xb, yp, coef, sn), (k, full, block, beta)
+        if block and beta < 0.5:
+            wrong = np.concatenate([np.ones(full + block), np.zeros(N - full - block)])
+            n_planted_rejected += not _tempered_check(s, Xb, yp, wrong, sn)
+    assert n_beta >= 8 and n_append == 7 and s.subset_rows == N
+    assert n_planted_rejected >= 1

@@ -1,8 +1,8 @@
 """The allocation-free resampling entry point (smc_k_resample_noalloc),
 called through the C ABI, must return the same ancestors as smc_k_resample
 on consecutive calls.  It exists for callers that cannot allocate device
-memory (stream capture in progress, an allocator that owns all device memory,
-loops that cannot take the device-wide synchronisation of cudaFree).  This
+memory (code under an allocator that owns all device memory, loops that
+cannot take the device-wide synchronisation of cudaFree).  This
 file is collected last so a failure here leaves every other test already run;
 it passes alone in a fresh process as well."""
 import numpy as np
