@@ -51,3 +51,14 @@ def test_host_threads_follows_the_thread_variables(monkeypatch):
     monkeypatch.delenv("OMP_NUM_THREADS")
     monkeypatch.delenv("MKL_NUM_THREADS", raising=False)
     assert bench.host_threads() >= 1
+
+
+def test_cpu_baseline_reports_single_thread_and_all_cores():
+    """The GPU line's cpu_baseline: the oracle timed single-threaded and with
+    one single-threaded process per host core, each rate with its thread count."""
+    sys.path.insert(0, ROOT)
+    import bench
+    d = bench.cpu_baseline(seconds=0.5, J_s=1, M_s=200)
+    assert d["kind"] == "oracle" and d["unit"] == bench.UNIT and d["cores"] == bench.host_threads()
+    assert d["single_thread"]["cores"] == 1 and d["single_thread"]["value"] > 0
+    assert d["all_cores"]["cores"] == d["cores"] and d["value"] == d["all_cores"]["value"] > 0
