@@ -450,6 +450,26 @@ smc_status smc_k_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ld
                            float* C, int64_t ldc, int64_t M, int64_t N, int64_t K,
                            int32_t accumulate, void* stream);
 
+/* Batched form of smc_k_gemm_bf16 on tcgen05 CTA pairs (the contraction of
+ * the BF16 engine's hidden layers and weight gradients, Sec. 3 eq. approx-grad
+ * summed over rows): for b = 0..batch-1
+ *     C_b[m][n] = sum_k A_b[m][k] B_b[n][k]
+ * with A_b's element (m, k) at A + b a_bstride + (a_mn_major ? k lda + m : m lda + k)
+ * and B_b's element (n, k) at B + b b_bstride + (b_mn_major ? k ldb + n : n ldb + k)
+ * (BF16 elements; a_bstride = 0 / b_bstride = 0: every batch reads the same
+ * matrix), C_b[m][n] at C + b c_bstride + m ldc + n (FP32).  An MN-major
+ * operand is read in place as the transpose of a row-major matrix, so
+ * dW = dZ^T A over the rows of two [rows][width] arrays needs no transposed
+ * copy.  Device pointers, 16-byte aligned; lda, ldb, a_bstride, b_bstride
+ * multiples of 8 elements.  K tails and ragged M / N read zeros.
+ * accumulate != 0 adds into C.  Synchronises `stream`.  Errors: SMC_EINVAL
+ * (sizes, pitches, alignment), SMC_ENOMEM, SMC_ECUDA, SMC_ETIMEOUT. */
+smc_status smc_k_gemm_bf16_batched(const void* A, int32_t a_mn_major, int64_t lda, int64_t a_bstride,
+                                   const void* B, int32_t b_mn_major, int64_t ldb, int64_t b_bstride,
+                                   float* C, int64_t ldc, int64_t c_bstride,
+                                   int64_t M, int64_t N, int64_t K, int32_t batch,
+                                   int32_t accumulate, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

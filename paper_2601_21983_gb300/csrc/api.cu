@@ -3,6 +3,7 @@
 // stateless kernel entry points.  Host code only orchestrates: every step of
 // the sampler's arithmetic runs in the kernels of k_smc.cu / k_simt.cu / k_tc.cu.
 #include "internal.h"
+#include "k_grouped.h"
 
 #include <algorithm>
 #include <cmath>
@@ -414,7 +415,8 @@ smc_status smc_init(const smc_model* model, const smc_data* train, const smc_con
     if (ok) ok = cudaMallocHost((void**)&c->stats_host, 64 * sizeof(double)) == cudaSuccess;
     if (ok && c->precision == SMC_PREC_BF16) {
         c->xta_rows = rup(c->in_feat + 1, 8);
-        ok = dalloc(c->shadow, (size_t)J * c->segs[c->layers[0].seg_w].size) &&
+        plan_shadow(c);
+        ok = dalloc(c->shadow, (size_t)c->shadow_elems) &&
              dalloc(c->Xb, (size_t)c->Npad * c->in_feat) && dalloc(c->XTa, (size_t)c->xta_rows * c->Npad);
     }
     if (ok) ok = ((c->precision == SMC_PREC_BF16) ? tc_alloc(c) : simt_alloc(c)) == SMC_OK;
@@ -1231,6 +1233,57 @@ smc_status smc_k_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ld
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
     if (e == cudaSuccess) e = tc_gemm_public(A, lda, B, ldb, C, ldc, M, N, K, accumulate, s, err, sms);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (e != cudaSuccess) return SMC_ECUDA;
+    return herr ? SMC_ETIMEOUT : SMC_OK;
+}
+
+smc_status smc_k_gemm_bf16_batched(const void* A, int32_t a_mn_major, int64_t lda, int64_t a_bstride, const void* B,
+                                   int32_t b_mn_major, int64_t ldb, int64_t b_bstride, float* C, int64_t ldc,
+                                   int64_t c_bstride, int64_t M, int64_t N, int64_t K, int32_t batch,
+                                   int32_t accumulate, void* stream) {
+    if (!A || !B || !C || M < 1 || N < 1 || K < 1 || batch < 1 || ldc < N) return SMC_EINVAL;
+    if (M > (1 << 30) || N > (1 << 30) || K > (1 << 30) || lda < 1 || ldb < 1) return SMC_EINVAL;
+    if ((lda % 8) || (ldb % 8) || (a_bstride % 8) || (b_bstride % 8) || a_bstride < 0 || b_bstride < 0)
+        return SMC_EINVAL;
+    if ((a_mn_major ? lda < M : lda < K) || (b_mn_major ? ldb < N : ldb < K)) return SMC_EINVAL;
+    // one operand as a 3-D array: inner = the contiguous index, outer = the other one
+    auto operand = [&](const void* base, int mn, int64_t ld, int64_t bstride, int64_t mn_ext) {
+        gk::GOperand o{};
+        o.base = base;
+        o.mn_major = mn ? 1 : 0;
+        o.inner = (uint64_t)(mn ? mn_ext : K);
+        o.outer = (uint64_t)(mn ? K : mn_ext);
+        o.outer_pitch = (uint64_t)ld * 2;
+        o.batched = bstride != 0;
+        o.batch = o.batched ? (uint64_t)batch : 1;
+        o.batch_pitch = o.batched ? (uint64_t)bstride * 2 : o.outer_pitch * o.outer;
+        o.perm = (o.batched && o.batch_pitch < o.outer_pitch) ? 1 : 0;
+        return o;
+    };
+    const gk::GOperand ga = operand(A, a_mn_major, lda, a_bstride, M);
+    const gk::GOperand gb = operand(B, b_mn_major, ldb, b_bstride, N);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int* err = nullptr;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return SMC_ENOMEM;
+    cudaStream_t s = (cudaStream_t)stream;
+    gk::GArgs g{};
+    g.M = (int)M; g.N = (int)N; g.K = (int)K; g.batch = batch;
+    g.epi = gk::EPI_F32;
+    g.out = C; g.ldo = ldc; g.out_bstride = c_bstride; g.accumulate = accumulate;
+    g.aug_col = -1;
+    g.err = err;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = grouped_gemm(ga, gb, g, SMC_ACT_IDENTITY, N > 256 ? 208 : 128, s, sms);
+    if (e == cudaErrorInvalidValue) {
+        cudaFree(err);
+        return SMC_EINVAL;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);

@@ -102,7 +102,10 @@ struct smc_ctx {
     float* mom = nullptr;            // momentum [J*D]
     float* grad = nullptr;           // cached sum_i c_i grad log p at theta under the current target
     float* grad_alt = nullptr;
-    __nv_bfloat16* shadow = nullptr; // BF16 copy of the first layer's W segment (BF16 engine)
+    __nv_bfloat16* shadow = nullptr; // BF16 copies of the hidden layers' W segments (BF16 engine);
+                                     // the first layer's [J][H][Din] block starts at element 0
+    int64_t shadow_off[smc::kMaxSegments];   // start of a segment's [J][size] BF16 block, -1: none
+    int64_t shadow_elems = 0;
     double* logw = nullptr;          // [J]
     double* wn = nullptr;            // [J]
     double* logpi = nullptr;         // [J] log pi of the target the particles were last weighted under
@@ -147,6 +150,7 @@ struct smc_ctx {
     float* rowll = nullptr;          // [J][chunk]
     float* conv_part = nullptr;      // SIMT: per-slice partial weight gradients of the largest conv layer
     // BF16 engine workspace
+    std::vector<__nv_bfloat16*> dact;  // deeper networks: activations of hidden layer l [chunk][J][H_l + 8]
     __nv_bfloat16* H1 = nullptr;     // [chunk_pad][J*H]
     __nv_bfloat16* dZT = nullptr;    // [J*H][chunk_pad]
     float* head_part = nullptr;      // [slices][J][C*H + C]
@@ -225,9 +229,12 @@ struct NvtxScope {
 struct SegTable {
     int n;
     int64_t size[kMaxSegments], off[kMaxSegments], canon[kMaxSegments];
-    int tc[kMaxSegments];   // 1: segment has a BF16 shadow
+    int64_t sh[kMaxSegments];   // offset of the segment's BF16 shadow, -1: none
 };
 SegTable seg_table(const smc_ctx* c);
+// BF16 engine: which weight segments keep a BF16 copy (every dense layer's W
+// except the last layer's) and where; sets shadow_off / shadow_elems.
+void plan_shadow(smc_ctx* c);
 cudaError_t launch_prior_draw(smc_ctx* c);
 cudaError_t launch_momentum(smc_ctx* c, bool injected);
 cudaError_t launch_leapfrog(smc_ctx* c, int phase, double h_kick, double h_drift, int pidx);
@@ -301,6 +308,16 @@ cudaError_t launch_fused_images(smc_ctx* c);
 cudaError_t launch_fused_fwd_head(smc_ctx* c, const __nv_bfloat16* x, int64_t g0, int64_t mc, int slot_base,
                                   int* nslots);
 cudaError_t launch_wait_probe(int arrive, uint64_t limit_ns, int* result, cudaStream_t s);
+// Sum the head's per-slot partials in slot order into the last layer's W / b
+// gradients and the log-likelihood sums la / lb (k_tc.cu).
+cudaError_t launch_head_reduce(smc_ctx* c, int nslots, int H, int C, float* gW, float* gb);
+// ----- BF16 engine for dense networks with two or more hidden layers (k_deep.cu)
+bool deep_model(const smc_ctx* c);
+smc_status deep_check_model(const smc_ctx* c, std::string* why);
+smc_status deep_alloc(smc_ctx* c);
+void deep_free(smc_ctx* c);
+smc_status deep_eval(smc_ctx* c);
+smc_status deep_predict(smc_ctx* c, const float* x, int64_t n, float* out);
 cudaError_t tc_gemm_public(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
                            int64_t M, int64_t N, int64_t K, int accumulate, cudaStream_t s, int* err_dev,
                            int num_sms);

@@ -1,0 +1,58 @@
+// Arguments of the batched tcgen05 GEMM (k_grouped.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace smc {
+namespace gk {
+
+enum { EPI_F32 = 0, EPI_BF16_ACT = 1, EPI_BF16_DACT = 2 };
+
+// One BF16 operand as a 3-D array: `inner` contiguous elements (k for a K-major
+// operand, m or n for an MN-major one), `outer` rows `outer_pitch` bytes apart
+// (the other matrix index) and `batch` matrices `batch_pitch` bytes apart.
+// perm 0 orders the tensor map's dimensions {inner, outer, batch}, perm 1
+// {inner, batch, outer} (for batches interleaved inside a row, as in a
+// [rows][J][H] activation array).  batched = 0: every batch reads matrix 0.
+struct GOperand {
+    const void* base;
+    int mn_major;
+    int perm;
+    int batched;
+    uint64_t inner, outer, batch;
+    uint64_t outer_pitch, batch_pitch;
+};
+
+struct GArgs {
+    int M, N, K;                 // per batch
+    int batch;
+    int epi;                     // EPI_*
+    void* out;                   // element (b, m, n) at out + b out_bstride + m ldo + n
+    int64_t ldo, out_bstride;
+    int accumulate;              // EPI_F32: add into out (and aug_out)
+    const float* bias;           // EPI_BF16_ACT: bias[b bias_bstride + n]
+    int64_t bias_bstride;
+    const __nv_bfloat16* aux;    // EPI_BF16_DACT: activation of (b, m, n) at aux + b aux_bstride + m aux_ld + n
+    int64_t aux_ld, aux_bstride;
+    float* aug_out;              // EPI_F32: column aug_col goes to aug_out[b aug_bstride + m];
+    int aug_col;                 //          columns past it are dropped (-1: none)
+    int64_t aug_bstride;
+    int* err;                    // device error flag (timeouts)
+    // filled by the launcher
+    int a_perm, b_perm, a_batched, b_batched;
+    int tiles_q, tiles_n, kb_total;
+    int64_t units;
+};
+
+}  // namespace gk
+
+// Launch C_b = A_b B_b^T for every batch (see k_grouped.cu).  N tiles of
+// 2 nhalf columns: nhalf 128 (two TMEM accumulators) or 208 (one) for
+// EPI_F32, 200 for the BF16 epilogues (one hidden layer of up to 400 units per
+// tile).  act selects the activation of the BF16 epilogues.
+cudaError_t grouped_gemm(const gk::GOperand& A, const gk::GOperand& B, const gk::GArgs& g, int act, int nhalf,
+                         cudaStream_t s, int num_sms);
+
+}  // namespace smc

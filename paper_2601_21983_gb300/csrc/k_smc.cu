@@ -23,10 +23,22 @@ SegTable seg_table(const smc_ctx* c) {
         t.size[s] = c->segs[s].size;
         t.off[s] = c->segs[s].off;
         t.canon[s] = c->segs[s].canon;
-        t.tc[s] = 0;
+        t.sh[s] = (c->precision == SMC_PREC_BF16 && c->shadow != nullptr) ? c->shadow_off[s] : -1;
     }
-    if (c->precision == SMC_PREC_BF16 && !c->layers.empty()) t.tc[c->layers[0].seg_w] = 1;
     return t;
+}
+
+void plan_shadow(smc_ctx* c) {
+    for (int s = 0; s < kMaxSegments; ++s) c->shadow_off[s] = -1;
+    c->shadow_elems = 0;
+    if (c->precision != SMC_PREC_BF16) return;
+    for (size_t l = 0; l + 1 < c->layers.size(); ++l) {
+        const Layer& L = c->layers[l];
+        if (L.kind != SMC_LAYER_DENSE || L.seg_w < 0) continue;
+        c->shadow_off[L.seg_w] = c->shadow_elems;
+        const int64_t n = (int64_t)c->J * c->segs[L.seg_w].size;
+        c->shadow_elems += (n + 63) / 64 * 64;
+    }
 }
 
 __global__ void philox_normals_kernel(uint64_t seed, uint32_t sid, uint32_t it, uint64_t off, int64_t n,
@@ -204,7 +216,8 @@ __global__ void __launch_bounds__(256) leapfrog_kernel(float* __restrict__ theta
         const int64_t base = t.off[s] + (int64_t)j * size;
         const float im = inv_mass ? inv_mass[grp * t.n + s] : 1.0f;
         const float sqrt_m = rsqrtf(im);
-        const bool has_shadow = t.tc[s] != 0;
+        const bool has_shadow = t.sh[s] >= 0;
+        __nv_bfloat16* shj = has_shadow ? shadow + t.sh[s] + (int64_t)j * size : nullptr;
         if ((size & 3) == 0) {
             const int64_t nq = size >> 2;
             const int64_t lo = nq * ch / nchunks, hi = nq * (ch + 1) / nchunks;
@@ -231,7 +244,7 @@ __global__ void __launch_bounds__(256) leapfrog_kernel(float* __restrict__ theta
                         uint2 v;
                         v.x = *reinterpret_cast<uint32_t*>(&lo2);
                         v.y = *reinterpret_cast<uint32_t*>(&hi2);
-                        *reinterpret_cast<uint2*>(shadow + (int64_t)j * size + 4 * q) = v;
+                        *reinterpret_cast<uint2*>(shj + 4 * q) = v;
                     }
                 }
                 p4[q] = p;
@@ -248,7 +261,7 @@ __global__ void __launch_bounds__(256) leapfrog_kernel(float* __restrict__ theta
                 if (PHASE == 0 && theta_old) theta_old[idx] = to;
                 if (PHASE != 2) {
                     theta[idx] = th;
-                    if (has_shadow) shadow[(int64_t)j * size + e] = __float2bfloat16_rn(th);
+                    if (has_shadow) shj[e] = __float2bfloat16_rn(th);
                 }
                 mom[idx] = p;
             }
@@ -479,19 +492,18 @@ __global__ void __launch_bounds__(1024) resample_kernel(const double* __restrict
 // Particle gather by ancestor: theta, cached gradient and per-particle scalars.
 // New particle j takes the arrays of its ancestor anc[j] (theta and the cached
 // gradient), 16 bytes per access where the segment size allows it (segment
-// offsets are 64-element aligned).  With sh != nullptr, segment sh_seg's BF16
-// shadow [J][size] is written from the gathered values on the way (the same
+// offsets are 64-element aligned).  Segments with a BF16 shadow (t.sh >= 0)
+// have it written from the gathered values on the way (the same
 // round-to-nearest-even conversion as shadow_kernel).
 __global__ void gather_kernel(const float* __restrict__ th_src, float* __restrict__ th_dst,
                               const float* __restrict__ g_src, float* __restrict__ g_dst, SegTable t,
-                              const int32_t* __restrict__ anc, int nchunks, __nv_bfloat16* __restrict__ sh,
-                              int sh_seg) {
+                              const int32_t* __restrict__ anc, int nchunks, __nv_bfloat16* __restrict__ sh) {
     const int j = blockIdx.y, ch = blockIdx.x;
     const int a = anc[j];
     for (int s = 0; s < t.n; ++s) {
         const int64_t size = t.size[s];
         const int64_t dst = t.off[s] + (int64_t)j * size, src = t.off[s] + (int64_t)a * size;
-        __nv_bfloat16* shd = (sh != nullptr && s == sh_seg) ? sh + (int64_t)j * size : nullptr;
+        __nv_bfloat16* shd = (sh != nullptr && t.sh[s] >= 0) ? sh + t.sh[s] + (int64_t)j * size : nullptr;
         if ((size & 3) == 0) {
             const int64_t n4 = size >> 2;
             const int64_t lo = n4 * ch / nchunks, hi = n4 * (ch + 1) / nchunks;
@@ -722,12 +734,11 @@ cudaError_t launch_resample(smc_ctx* c, int kind, int) {
 cudaError_t launch_gather(smc_ctx* c) {
     const int nch = part_chunks_for(c);
     dim3 grid(nch, c->J);
-    // the BF16 engine's first-layer shadow follows the gathered weights
+    // the BF16 engine's weight shadows follow the gathered weights
     const bool shadow = c->precision == SMC_PREC_BF16 && c->shadow != nullptr;
     SMC_LAUNCH(c, gather_kernel<<<grid, 256, 0, c->stream>>>(c->theta, c->theta_alt, c->grad, c->grad_alt,
                                                              seg_table(c), c->anc, nch,
-                                                             shadow ? c->shadow : nullptr,
-                                                             shadow ? c->layers[0].seg_w : -1));
+                                                             shadow ? c->shadow : nullptr));
     SMC_LAUNCH(c, gather_scalars_kernel<<<(c->J + 255) / 256, 256, 0, c->stream>>>(
                       c->J, c->anc, c->logpi, c->logpi_alt, c->la, c->la_alt, c->lb, c->lb_alt, c->logw, c->wn));
     return cudaGetLastError();
@@ -735,9 +746,13 @@ cudaError_t launch_gather(smc_ctx* c) {
 
 cudaError_t launch_shadow(smc_ctx* c) {
     if (c->precision != SMC_PREC_BF16 || c->shadow == nullptr) return cudaSuccess;
-    const Segment& s = c->segs[c->layers[0].seg_w];
-    const int64_t n = (int64_t)c->J * s.size;
-    SMC_LAUNCH(c, shadow_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->theta + s.off, c->shadow, n));
+    for (size_t i = 0; i < c->segs.size(); ++i) {
+        if (c->shadow_off[i] < 0) continue;
+        const Segment& s = c->segs[i];
+        const int64_t n = (int64_t)c->J * s.size;
+        SMC_LAUNCH(c, shadow_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+                          c->theta + s.off, c->shadow + c->shadow_off[i], n));
+    }
     return cudaGetLastError();
 }
 

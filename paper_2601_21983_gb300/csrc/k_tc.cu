@@ -767,6 +767,7 @@ __global__ void to_bf16_rows_kernel(const float* __restrict__ x, int64_t n, int6
 
 // ---------------------------------------------------------------- engine
 smc_status tc_check_model(const smc_ctx* c, std::string* why) {
+    if (deep_model(c)) return deep_check_model(c, why);
     if (c->layers.size() != 2 || c->layers[0].kind != SMC_LAYER_DENSE || c->layers[1].kind != SMC_LAYER_DENSE) {
         *why = "BF16 tensor-core path needs a dense network with one hidden layer";
         return SMC_EUNSUPPORTED;
@@ -786,6 +787,7 @@ static inline int64_t rup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 static int64_t ldh_of(const smc_ctx* c) { return rup((int64_t)c->J * c->layers[0].out_feat(), 8); }
 
 smc_status tc_alloc(smc_ctx* c) {
+    if (deep_model(c)) return deep_alloc(c);
     const int64_t H = c->layers[0].out_feat();
     const int64_t JH = (int64_t)c->J * H;
     int64_t chunk = c->chunk > 0 ? c->chunk : c->N;
@@ -817,6 +819,10 @@ smc_status tc_alloc(smc_ctx* c) {
 }
 
 void tc_free(smc_ctx* c) {
+    if (deep_model(c)) {
+        deep_free(c);
+        return;
+    }
     cudaFree(c->H1); cudaFree(c->dZT); cudaFree(c->head_part); cudaFree(c->head_ll); cudaFree(c->gemm_part);
     cudaFree(c->fimg);
     c->H1 = nullptr; c->dZT = nullptr; c->head_part = nullptr; c->head_ll = nullptr; c->gemm_part = nullptr;
@@ -895,6 +901,7 @@ static cudaError_t launch_wgrad(smc_ctx* c, int64_t g0, int64_t mc, bool with_b1
 }
 
 smc_status tc_eval(smc_ctx* c) {
+    if (deep_model(c)) return deep_eval(c);
     const Layer& L0 = c->layers[0];
     const Layer& L1 = c->layers[1];
     const int H = (int)L0.out_feat(), C = c->n_out;
@@ -961,6 +968,7 @@ smc_status tc_eval(smc_ctx* c) {
 }
 
 smc_status tc_predict(smc_ctx* c, const float* x, int64_t n, float* out) {
+    if (deep_model(c)) return deep_predict(c, x, n, out);
     const Layer& L0 = c->layers[0];
     const Layer& L1 = c->layers[1];
     const int H = (int)L0.out_feat(), C = c->n_out;
@@ -989,6 +997,13 @@ smc_status tc_predict(smc_ctx* c, const float* x, int64_t n, float* out) {
     cudaFree(xb);
     cudaFree(logits);
     return st;
+}
+
+cudaError_t launch_head_reduce(smc_ctx* c, int nslots, int H, int C, float* gW, float* gb) {
+    const int per = C * H + C;
+    SMC_LAUNCH(c, head_reduce_kernel<<<(unsigned)(((int64_t)c->J * per + 255) / 256), 256, 0, c->stream>>>(
+                      c->head_part, c->head_ll, nslots, c->J, H, C, 0, gW, gb, nullptr, c->la, c->lb));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_wait_probe(int arrive, uint64_t limit_ns, int* result, cudaStream_t s) {

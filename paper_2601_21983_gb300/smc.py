@@ -145,6 +145,9 @@ _SIGS = {
     "smc_k_wait_probe": (C.c_int, [C.c_double, C.c_int32, C.c_void_p]),
     "smc_k_gemm_bf16": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                   C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_void_p]),
+    "smc_k_gemm_bf16_batched": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_void_p, C.c_int32,
+                                          C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_int64,
+                                          C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_void_p]),
 }
 EXPORTED = sorted(_SIGS)
 
@@ -680,6 +683,33 @@ def smc_k_gemm_bf16(A, B, Cout, accumulate=False, stream=None):
         raise ValueError(f"{W}: shapes A {tuple(A.shape)}, B {tuple(B.shape)}, Cout {tuple(Cout.shape)} do not match")
     _check(load().smc_k_gemm_bf16(A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0), Cout.data_ptr(),
                                   Cout.stride(0), M, N, K, 1 if accumulate else 0, _stream(stream)), W)
+
+
+def smc_k_gemm_bf16_batched(A, a_layout, B, b_layout, Cout, c_layout, M, N, K, batch, accumulate=False,
+                            stream=None):
+    """C_b[m][n] = sum_k A_b[m][k] B_b[n][k] for b < batch.  A, B: BF16 device
+    tensors; Cout: FP32 device tensor.  a_layout = (mn_major, ld, bstride) in
+    elements (element (m, k) of A_b at b bstride + (k ld + m if mn_major else
+    m ld + k)); b_layout likewise for (n, k); c_layout = (ldc, c_bstride).  Every
+    element the call may touch must lie inside its tensor."""
+    W = "smc_k_gemm_bf16_batched"
+    for t, name, dt in ((A, "A", "bfloat16"), (B, "B", "bfloat16"), (Cout, "Cout", np.float32)):
+        _arg(t, W, name, dt, None, "device", contiguous=False)
+        if not t.is_contiguous():
+            raise ValueError(f"{W}: {name} must be contiguous")
+
+    def last(layout, rows):
+        mn, ld, bs = layout
+        return (batch - 1) * bs + ((K - 1) * ld + rows - 1 if mn else (rows - 1) * ld + K - 1)
+    if last(a_layout, M) >= A.numel() or last(b_layout, N) >= B.numel():
+        raise ValueError(f"{W}: the layout reaches past an operand")
+    ldc, cbs = c_layout
+    if (batch - 1) * cbs + (M - 1) * ldc + N - 1 >= Cout.numel():
+        raise ValueError(f"{W}: the layout reaches past Cout")
+    _check(load().smc_k_gemm_bf16_batched(A.data_ptr(), int(a_layout[0]), a_layout[1], a_layout[2],
+                                          B.data_ptr(), int(b_layout[0]), b_layout[1], b_layout[2],
+                                          Cout.data_ptr(), ldc, cbs, M, N, K, batch, 1 if accumulate else 0,
+                                          _stream(stream)), W)
 
 
 def smc_k_wait_probe(limit_ms, arrive, stream=None):

@@ -57,6 +57,58 @@ def test_tcgen05_gemm_matches_fp32_reference(M, N, K):
     assert (C - 2 * ref).abs().max().item() <= 2e-4 * ref.abs().max().item() + 2e-4
 
 
+def _store(L, mn_major, kind):
+    """Lay the logical operands L [batch][rows][K] (BF16) out in device memory:
+    kind "dense" (one matrix after another), "interleaved" (batches side by side
+    inside each row, as in a [rows][J][H] activation array) or "shared" (one
+    matrix, batch stride 0).  Row padding is NaN, so a read past the logical
+    extent would poison the product.  Returns (buffer, (mn_major, ld, bstride))."""
+    nb, rows, K = L.shape
+    inner, outer = (rows, K) if mn_major else (K, rows)
+    X = L.transpose(1, 2) if mn_major else L                     # [batch][outer][inner]
+    ld = (inner + 7) // 8 * 8 + 8
+    if kind == "interleaved":
+        buf = torch.full((outer, nb, ld), float("nan"), device="cuda", dtype=torch.bfloat16)
+        buf[:, :, :inner] = X.permute(1, 0, 2)
+        return buf.reshape(-1), (mn_major, nb * ld, ld)
+    buf = torch.full((nb, outer, ld), float("nan"), device="cuda", dtype=torch.bfloat16)
+    buf[:, :, :inner] = X
+    return buf.reshape(-1), (mn_major, ld, 0 if kind == "shared" else outer * ld)
+
+
+@pytest.mark.parametrize("M,N,K,batch,a,b", [
+    (300, 200, 100, 3, (0, "dense"), (0, "dense")),
+    (257, 401, 200, 2, (1, "dense"), (1, "dense")),
+    (400, 401, 1000, 4, (1, "interleaved"), (1, "interleaved")),   # weight gradient of a hidden layer
+    (1000, 400, 400, 3, (0, "interleaved"), (0, "dense")),         # forward of a hidden layer
+    (1000, 400, 400, 3, (0, "interleaved"), (1, "dense")),         # adjoint through a hidden layer
+    (600, 785, 300, 1, (1, "dense"), (0, "dense")),                # first-layer weight gradient
+    (130, 64, 17, 2, (0, "shared"), (1, "dense")),
+    (64, 16, 8, 5, (1, "dense"), (0, "shared")),
+    (256, 128, 64, 64, (0, "dense"), (1, "interleaved")),
+])
+def test_batched_tcgen05_gemm_matches_fp32_reference(M, N, K, batch, a, b):
+    """smc_k_gemm_bf16_batched (CTA-pair tcgen05, K-major and MN-major operands)
+    against a plain PyTorch fp32 matmul of the same BF16 operands, per batch."""
+    g = torch.Generator(device="cuda").manual_seed(M + 3 * N + 7 * K + batch)
+    LA = torch.randn(1 if a[1] == "shared" else batch, M, K, device="cuda", generator=g).to(torch.bfloat16)
+    LB = torch.randn(1 if b[1] == "shared" else batch, N, K, device="cuda", generator=g).to(torch.bfloat16)
+    bufA, la = _store(LA, a[0], a[1])
+    bufB, lb = _store(LB, b[0], b[1])
+    ldc = N + 3
+    C = torch.full((batch, M, ldc), float("nan"), device="cuda", dtype=torch.float32)
+    S.smc_k_gemm_bf16_batched(bufA, la, bufB, lb, C.reshape(-1), (ldc, M * ldc), M, N, K, batch)
+    torch.cuda.synchronize()
+    ref = LA.float().expand(batch, M, K) @ LB.float().expand(batch, N, K).transpose(1, 2)
+    got = C[:, :, :N]
+    err = (got - ref).abs().max().item()
+    assert err <= 1e-4 * ref.abs().max().item() + 1e-4, err
+    assert torch.isnan(C[:, :, N:]).all()          # columns past N untouched
+    S.smc_k_gemm_bf16_batched(bufA, la, bufB, lb, C.reshape(-1), (ldc, M * ldc), M, N, K, batch, accumulate=True)
+    torch.cuda.synchronize()
+    assert (C[:, :, :N] - 2 * ref).abs().max().item() <= 2e-4 * ref.abs().max().item() + 2e-4
+
+
 def test_normalise_matches_oracle():
     r = np.random.default_rng(0)
     for J in [1, 5, 256, 1024, 4096]:
