@@ -174,12 +174,15 @@ def host_threads():
         return os.cpu_count()
 
 
-def _oracle_eval_rate(seconds, J_s, M_s, seed):
+def _oracle_eval_rate(seconds, J_s, M_s, seed, scale=False):
     """Particle-sample gradient evaluations per second of the FP64 oracle on
-    J_s particles x M_s rows of the workload's model and data (this process)."""
+    J_s particles x M_s rows of the workload's model and data (this process);
+    scale: the 784-400-400-10 network instead of 784-100-10."""
     import synthetic
     from oracle import nn
-    spec = nn.Spec([("dense", DIN, H), ("dense", H, NCLS)], (DIN,), nn.RELU)
+    layers = [("dense", DIN, 400), ("dense", 400, 400), ("dense", 400, NCLS)] if scale else \
+        [("dense", DIN, H), ("dense", H, NCLS)]
+    spec = nn.Spec(layers, (DIN,), nn.RELU)
     X, y = synthetic.template_images(M_s, seed=3)
     X = X.astype(np.float64)
     th = synthetic.particles(J_s, spec.n_params, seed, std=0.05).astype(np.float64)
@@ -229,6 +232,172 @@ def cpu_baseline(seconds=8.0, J_s=2, M_s=2000):
                       f"one single-threaded process ({ev1} evaluations)",
             "single_thread": {"value": single, "unit": UNIT, "cores": 1},
             "all_cores": {"value": allc, "unit": UNIT, "cores": cores}}
+
+
+# ---------------------------------------------------------------- scale configuration
+SCALE_H, SCALE_J, SCALE_LAYERS = 400, 1024, [("dense", DIN, 400), ("dense", 400, 400), ("dense", 400, NCLS)]
+SCALE_FLOP = 2.238e6       # per particle-sample gradient evaluation (955,200 forward + 1,283,200 backward)
+
+
+def scale_workload(J, n):
+    return {"workload": (f"MLP {DIN}-400-400-{NCLS} ReLU (D = 478,410), J={J} particles, synthetic {n}x{DIN} "
+                         f"10-class images, full batch |D_k|={n} (FB), HMC S={S_LF}, h={STEP_H}, BF16 tcgen05 "
+                         f"contractions with FP32 accumulation"),
+            "particles": J, "rows": n, "schedule": "fb", "leapfrog_steps": S_LF,
+            "l2": "no flush: per-step working set (activations 3 x 6.7 GB per chunk) far above the 129 MB L2"}
+
+
+def scale_cpu_baseline(seconds=6.0, M_s=500):
+    """The FP64 oracle on a bounded sample of the scale configuration: single
+    particles of the 784-400-400-10 network over M_s rows, one
+    single-threaded process and one per host core."""
+    cores = host_threads()
+    cmd_extra = ["--scale"]
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+
+    def workers(n):
+        cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", str(seconds), "1", str(M_s)]
+        procs = [subprocess.Popen(cmd + [str(20 + w)] + cmd_extra, env=env, stdout=subprocess.PIPE,
+                                  stderr=subprocess.DEVNULL, text=True) for w in range(n)]
+        total, longest = 0, 0.0
+        for p in procs:
+            out, _ = p.communicate(timeout=300)
+            ev, el = json.loads(out.strip().splitlines()[-1])
+            total, longest = total + ev, max(longest, el)
+        return total, longest
+
+    ev1, el1 = workers(1)
+    evn, eln = workers(cores)
+    return {"value": evn * M_s / eln, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle gradient evaluations of single particles of the 784-400-400-10 network over "
+                      f"{M_s} rows, {seconds:.0f} s per run: {cores} single-threaded processes ({evn} evaluations) "
+                      f"and one ({ev1} evaluations)",
+            "single_thread": {"value": ev1 * M_s / el1, "unit": UNIT, "cores": 1},
+            "all_cores": {"value": evn * M_s / eln, "unit": UNIT, "cores": cores}}
+
+
+def run_scale_config(steps, warmup, J=SCALE_J, n=N_TRAIN, e2e=True, roofline=True, cpu=True):
+    """One SMC iteration (anneal, resample, HMC move with S = 3 gradient
+    evaluations over all n rows, reweight) of the scale configuration
+    (784-400-400-10, J = 1024) through the C ABI, device-timed with CUDA events
+    on the library's stream; then the same end to end with the rows streamed
+    from pinned host memory each step; then per-kernel times for the roofline."""
+    import torch
+    from paper_2601_21983_gb300 import smc as S
+    S.load()
+    stream = torch.cuda.current_stream()
+    X, y = make_data(n, seed=0)
+    Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    model = S.make_model(SCALE_LAYERS, (DIN,), S.ACT_RELU)
+    sched = S.make_schedule("fb", n, n, K_SCHED)
+
+    def new_ctx(timing=0):
+        ctx = S.smc_init(model, Xd, y_class=yd, cfg=S.make_config(J, 4321, S.PREC_BF16, stream=stream, timing=timing))
+        D = S.smc_num_params(ctx)
+        S.smc_set_state_device(ctx, 0.05 * torch.randn(J, D, device="cuda",
+                                                         generator=torch.Generator(device="cuda").manual_seed(5)))
+        S.smc_set_schedule(ctx, sched)
+        return ctx
+
+    evals = [0]
+
+    def one_step(ctx):
+        S.smc_anneal_next(ctx)
+        S.smc_resample(ctx)
+        st = S.smc_step(ctx, STEP_H, S_LF)
+        evals[0] += st["grad_evals"] * st["rows"] * J
+        return st
+
+    ctx = new_ctx()
+    for _ in range(warmup):
+        one_step(ctx)
+    torch.cuda.synchronize()
+    n0, _, _ = S.smc_get_counters(ctx)
+    evals[0] = 0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        st = one_step(ctx)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    n1, _, _ = S.smc_get_counters(ctx)
+    out = {"metric": METRIC, "value": evals[0] / (ms / 1e3), "unit": UNIT, "steps": steps, "warmup": warmup,
+           "ms_per_step": ms / steps, "dtype": "bf16", "data": "synthetic", "config": scale_workload(J, n),
+           "gpu_launches": n1 - n0, "last_ess": st["ess"]}
+    if e2e:
+        perm = S.smc_get_permutation(ctx, n)
+        hx = torch.from_numpy(np.ascontiguousarray(X[perm])).pin_memory()
+        hy = torch.from_numpy(np.ascontiguousarray(y[perm])).pin_memory()
+        hxn, hyn = hx.numpy(), hy.numpy()
+        torch.cuda.synchronize()
+        evals[0] = 0
+        t0 = time.perf_counter()
+        S.smc_upload_rows_async(ctx, 0, hxn, hyn)
+        for i in range(steps):
+            S.smc_anneal_next(ctx)
+            S.smc_resample(ctx)
+            if i + 1 < steps:
+                S.smc_upload_rows_async(ctx, 0, hxn, hyn)
+            st = S.smc_step(ctx, STEP_H, S_LF)
+            evals[0] += st["grad_evals"] * st["rows"] * J
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        out["e2e"] = {"value": evals[0] / el, "unit": UNIT, "h2d_bytes_per_step": int(hxn.nbytes + hyn.nbytes),
+                      "d2h_bytes_per_step": 16 * 8 + 2 * 4}
+    S.smc_destroy(ctx)
+    if roofline:
+        ctx = new_ctx(timing=1)
+        one_step(ctx)
+        S.smc_reset_counters(ctx)
+        n_evals = one_step(ctx)["grad_evals"]
+        _, times, calls = S.smc_get_counters(ctx)
+        S.smc_destroy(ctx)
+        hbm, tf_burst, tf_sus, src = peaks()
+        units = float(n) * J                           # particle-sample pairs per evaluation
+        H = SCALE_H
+        work = {"fwd_gemm": ("tensor", 2.0 * units * H * DIN),
+                "hidden_gemm": ("tensor", 2.0 * units * H * H),
+                "adjoint_gemm": ("tensor", 2.0 * units * H * H),
+                "hidden_wgrad_gemm": ("tensor", 2.0 * units * H * (H + 1)),
+                "wgrad_gemm": ("tensor", 2.0 * units * H * (DIN + 1)),
+                # the head reads the last hidden activations and writes dZ over them (BF16)
+                "head": ("hbm", 2.0 * units * H * 2.0)}
+        kern = {}
+        gemm_flop, gemm_ms = 0.0, 0.0
+        for k, (bound, amount) in work.items():
+            if not calls.get(k):
+                continue
+            per_eval = times[k] / n_evals                  # ms per gradient evaluation over all rows
+            if bound == "tensor":
+                ach = amount / (per_eval / 1e3) / 1e12
+                kern[k] = {"bound": "tensor", "achieved": ach, "peak": tf_burst, "unit": "TFLOP/s",
+                           "frac": ach / tf_burst, "ms_per_eval": per_eval, "work_per_eval": amount,
+                           "launches_per_eval": calls[k] / n_evals}
+                gemm_flop += amount
+                gemm_ms += per_eval
+            else:
+                ach = amount / (per_eval / 1e3) / 1e9
+                kern[k] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                           "ms_per_eval": per_eval, "work_per_eval": amount,
+                           "launches_per_eval": calls[k] / n_evals}
+        dom = max(kern, key=lambda k: kern[k]["ms_per_eval"])
+        roof = dict(kern[dom])
+        roof["kernel"] = dom
+        roof["traffic"] = None
+        roof["peak_kind"] = f"{src} " + ("bf16_tflops (burst)" if roof["bound"] == "tensor" else "hbm_gbs")
+        roof["all_gemms"] = {"achieved": gemm_flop / (gemm_ms / 1e3) / 1e12, "unit": "TFLOP/s",
+                             "frac": gemm_flop / (gemm_ms / 1e3) / 1e12 / tf_burst, "ms_per_eval": gemm_ms}
+        roof["whole_step"] = {"achieved": units * SCALE_FLOP * S_LF / (out["ms_per_step"] / 1e3) / 1e12,
+                              "unit": "TFLOP/s",
+                              "frac": units * SCALE_FLOP * S_LF / (out["ms_per_step"] / 1e3) / 1e12 / tf_burst}
+        roof["others"] = {k: {"frac": round(v["frac"], 4), "achieved": round(v["achieved"], 1), "unit": v["unit"],
+                              "ms_per_eval": round(v["ms_per_eval"], 3)} for k, v in kern.items() if k != dom}
+        out["roofline"] = roof
+        out["families_ms"] = {k: {"ms": times[k], "calls": calls[k]} for k in times if calls[k]}
+    if cpu:
+        out["cpu_baseline"] = scale_cpu_baseline()
+    return out
 
 
 def run_reference(args):
@@ -493,11 +662,16 @@ def main():
     ap.add_argument("--tta-iters", type=int, default=200)
     ap.add_argument("--tta-seeds", type=int, default=5)
     ap.add_argument("--no-tta", action="store_true", help="leave the time-to-accuracy comparison out of the line")
+    ap.add_argument("--no-scale", action="store_true", help="leave the 784-400-400-10 J = 1024 section out")
+    ap.add_argument("--scale-only", action="store_true", help="only the 784-400-400-10 J = 1024 section")
+    ap.add_argument("--scale-steps", type=int, default=5)
+    ap.add_argument("--scale-J", type=int, default=SCALE_J, help="particles of the scale section (profiling runs)")
+    ap.add_argument("--scale-n", type=int, default=N_TRAIN, help="rows of the scale section (profiling runs)")
     ap.add_argument("--tta-explore", type=int, default=30)
     ap.add_argument("--tta-every", type=int, default=4)
     if len(sys.argv) >= 6 and sys.argv[1] == "--oracle-worker":
         sec, j_s, m_s, seed = float(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]), int(sys.argv[5])
-        print(json.dumps(list(_oracle_eval_rate(sec, j_s, m_s, seed))), flush=True)
+        print(json.dumps(list(_oracle_eval_rate(sec, j_s, m_s, seed, scale="--scale" in sys.argv[6:]))), flush=True)
         return
     args = ap.parse_args()
     args.steps = max(1, args.steps)
@@ -509,6 +683,12 @@ def main():
         return run_tta(args)
     if args.grid:
         return run_grid(args)
+    if args.scale_only:
+        line = run_scale_config(args.scale_steps, max(3, args.warmup), J=args.scale_J, n=args.scale_n,
+                                cpu=not args.no_cpu_baseline, e2e=not args.no_e2e, roofline=not args.no_roofline)
+        line["n_gpus"] = 1
+        print(json.dumps(line), flush=True)
+        return
 
     import torch
     from paper_2601_21983_gb300 import smc as S
@@ -666,6 +846,9 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
                 "config": workload_config(args), "e2e": e2e, "gpu_launches": n1 - n0,
                 "clocks": clk, "roofline": roof, "families_ms": fam}
+        if world == 1 and not args.no_scale:
+            line["scale_config"] = run_scale_config(args.scale_steps, max(3, args.warmup),
+                                                    cpu=not args.no_cpu_baseline)
         if world == 1 and not args.no_tta:
             line["tta"] = tta_compare(args.J, args.n, args.tta_iters, list(range(args.tta_seeds)), args.tta_every,
                                       args.tta_explore)

@@ -387,7 +387,9 @@ smc_status smc_get_ancestors(smc_ctx* ctx, int32_t* ancestors);
  * 0 first-layer forward GEMM, 1 head/adjoint, 2 first-layer weight-gradient GEMM,
  * 3 hidden-layer GEMMs, 4 leapfrog, 5 weights/normalise/ESS, 6 resample+gather,
  * 7 other network kernels (SIMT path), 8 partial reductions, 9 first-layer
- * forward GEMM with the head/adjoint fused into it.  times may be NULL;
+ * forward GEMM with the head/adjoint fused into it, 10 adjoint GEMMs of
+ * hidden layers (dZ_{l-1} = dZ_l W_l * act'), 11 weight-gradient GEMMs of
+ * hidden layers (BF16 engine of deeper networks).  times may be NULL;
  * n_fam is the capacity of times. */
 smc_status smc_get_counters(smc_ctx* ctx, int64_t* launches, double* times, int32_t n_fam,
                             int64_t* calls_per_family);

@@ -30,7 +30,8 @@ smc_status cuda_check(smc_ctx* c, cudaError_t e, const char* what) {
 // NVTX range names of the kernel families (counter indices of smc_get_counters)
 static const char* const kFamNames[kFamilies] = {"smc:fwd_gemm", "smc:head", "smc:wgrad_gemm", "smc:hidden_gemm",
                                                  "smc:leapfrog", "smc:weights", "smc:resample", "smc:simt_net",
-                                                 "smc:reduce", "smc:fused_fwd_head"};
+                                                 "smc:reduce", "smc:fused_fwd_head", "smc:adjoint_gemm",
+                                                 "smc:hidden_wgrad_gemm"};
 
 void fam_begin(smc_ctx* c, int f) {
     c->fam_calls[f]++;
@@ -1279,7 +1280,7 @@ smc_status smc_k_gemm_bf16_batched(const void* A, int32_t a_mn_major, int64_t ld
     g.aug_col = -1;
     g.err = err;
     cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = grouped_gemm(ga, gb, g, SMC_ACT_IDENTITY, N > 256 ? 208 : 128, s, sms);
+    if (e == cudaSuccess) e = grouped_gemm(ga, gb, nullptr, g, SMC_ACT_IDENTITY, N > 256 ? 208 : 128, s, sms);
     if (e == cudaErrorInvalidValue) {
         cudaFree(err);
         return SMC_EINVAL;

@@ -18,10 +18,11 @@ namespace smc {
 constexpr int kMaxSegments = 32;
 constexpr int kMaxLayers = 16;
 constexpr int kMaxParticles = 4096;
-constexpr int kFamilies = 10;
+constexpr int kFamilies = 12;
 constexpr int kMaxGroups = 16;        // candidate groups of the learned proposal
 enum Family { F_FWD_GEMM = 0, F_HEAD = 1, F_WGRAD_GEMM = 2, F_HIDDEN_GEMM = 3, F_LEAPFROG = 4,
-              F_WEIGHTS = 5, F_RESAMPLE = 6, F_SIMT_NET = 7, F_REDUCE = 8, F_FUSED = 9 };
+              F_WEIGHTS = 5, F_RESAMPLE = 6, F_SIMT_NET = 7, F_REDUCE = 8, F_FUSED = 9, F_ADJ_GEMM = 10,
+              F_HWGRAD_GEMM = 11 };
 
 // Philox stream identifiers (counter word 3).
 enum : uint32_t { RNG_PRIOR = 1, RNG_MOMENTUM = 2 };
@@ -150,7 +151,7 @@ struct smc_ctx {
     float* rowll = nullptr;          // [J][chunk]
     float* conv_part = nullptr;      // SIMT: per-slice partial weight gradients of the largest conv layer
     // BF16 engine workspace
-    std::vector<__nv_bfloat16*> dact;  // deeper networks: activations of hidden layer l [chunk][J][H_l + 8]
+    std::vector<__nv_bfloat16*> dact;  // deeper networks: activations of hidden layer l [J][chunk][H_l + 8]
     __nv_bfloat16* H1 = nullptr;     // [chunk_pad][J*H]
     __nv_bfloat16* dZT = nullptr;    // [J*H][chunk_pad]
     float* head_part = nullptr;      // [slices][J][C*H + C]

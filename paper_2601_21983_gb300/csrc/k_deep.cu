@@ -3,8 +3,8 @@
 // over the annealed subset D_k, on the deeper networks of Sec. 4).
 //
 // Per chunk of rows of D_k (J particles, layers 0..L-1, hidden widths H_l,
-// activations A_l = act(Z_l) stored BF16 [rows][J][H_l + 8], column H_l of
-// every row and particle held at 1):
+// activations A_l = act(Z_l) stored BF16 particle-major [J][rows][H_l + 8],
+// column H_l of every row and particle held at 1):
 //   K1  A_0 = act(X W_0^T + b_0)          shared input rows X, one GEMM per particle
 //                                         block of W_0 (tcgen05 CTA pairs, k_grouped.cu)
 //   K2  A_l = act(A_{l-1} W_l^T + b_l)     l = 1..L-2, batched over particles
@@ -36,6 +36,10 @@ using gk::GOperand;
 constexpr int ROWS_PER_SLICE = 4096;   // rows of one head block (one partial slot)
 constexpr int TILE = 64;               // rows of the head's shared-memory tile
 constexpr int DS = 24;                 // dlogits tile row stride (elements)
+// BF16-epilogue GEMMs (forward layers, adjoints): N tiles of 208 columns with
+// two TMEM accumulators, so a tile's epilogue (HBM-bound: it writes the layer's
+// activations or dZ) overlaps the next tile's MMAs
+constexpr int kBf16Half = 104;
 
 static inline int64_t rup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
@@ -64,7 +68,8 @@ struct HeadCfg {
 };
 
 // Head and adjoint of the last layer for one particle (blockIdx.y) over one
-// slice of a chunk's rows (blockIdx.x), 64-row tiles, four warps.
+// slice of a chunk's rows (blockIdx.x), 64-row tiles, four warps; row r of
+// particle j's activations is at A + j pitch + r lda.
 //   mode 0: log-likelihood sums, dW / db partials, dZ over the activations;
 //   mode 1: logits only, to logits[j][row][c] (prediction).
 // Warp w owns rows 16 w .. 16 w + 15 of a tile for the logits, dlogits and dZ,
@@ -300,7 +305,7 @@ __global__ void __launch_bounds__(128, 2) deep_head_kernel(
     }
 }
 
-// Column H of every row and particle of an activation array [rows][J][pitch] is
+// Column H of every row and particle of an activation array [J][rows][pitch] is
 // 1 (the ones column that turns the next layer's weight-gradient GEMM into one
 // that also yields the bias gradient); columns H+1 .. pitch-1 are 0.
 __global__ void ones_column_kernel(__nv_bfloat16* __restrict__ A, int64_t rows, int J, int H, int64_t pitch) {
@@ -365,19 +370,22 @@ static cudaError_t launch_head(smc_ctx* c, __nv_bfloat16* A, int64_t lda, int64_
 static int hid(const smc_ctx* c, size_t l) { return (int)c->layers[l].out_feat(); }
 static int64_t pitch_of(const smc_ctx* c, size_t l) { return hid(c, l) + 8; }
 
-// K-major operand: rows of layer l's activations [rows][J][pitch] (batch = particle).
+// Layer l's activations [J][chunk][pitch] (particle-major: one particle's rows
+// are contiguous, so a TMA box of rows reads nearby memory) as an operand:
+// K-major (rows x hidden, a forward or adjoint A) or MN-major (hidden x rows,
+// a weight gradient's operand); extra = 1 includes the ones column.
 static GOperand act_rows(const smc_ctx* c, const __nv_bfloat16* A, size_t l, int64_t rows, bool mn_major,
                          int extra) {
     GOperand o{};
     o.base = A;
     o.mn_major = mn_major ? 1 : 0;
-    o.perm = 1;
+    o.perm = 0;
     o.batched = 1;
     o.inner = (uint64_t)(hid(c, l) + extra);
     o.outer = (uint64_t)rows;
     o.batch = (uint64_t)c->J;
-    o.batch_pitch = (uint64_t)pitch_of(c, l) * 2;
-    o.outer_pitch = (uint64_t)c->J * pitch_of(c, l) * 2;
+    o.outer_pitch = (uint64_t)pitch_of(c, l) * 2;
+    o.batch_pitch = (uint64_t)c->chunk * pitch_of(c, l) * 2;
     return o;
 }
 
@@ -422,12 +430,13 @@ static cudaError_t forward_layer(smc_ctx* c, size_t l, const __nv_bfloat16* x, i
     }
     GArgs g = base_args(c, (int)rows, Hl, (int)L.in_feat(), c->J, gk::EPI_BF16_ACT);
     g.out = c->dact[l];
-    g.ldo = (int64_t)c->J * pitch_of(c, l);
-    g.out_bstride = pitch_of(c, l);
+    g.ldo = pitch_of(c, l);
+    g.out_bstride = c->chunk * pitch_of(c, l);
     g.bias = c->theta + c->segs[L.seg_b].off;
     g.bias_bstride = Hl;
     fam_begin(c, l == 0 ? F_FWD_GEMM : F_HIDDEN_GEMM);
-    cudaError_t e = grouped_gemm(A, weights(c, l, false), g, L.act, 200, c->stream, c->num_sms);
+    const GOperand O = act_rows(c, c->dact[l], l, rows, false, 0);
+    cudaError_t e = grouped_gemm(A, weights(c, l, false), &O, g, L.act, kBf16Half, c->stream, c->num_sms);
     c->launches++;
     fam_end(c, l == 0 ? F_FWD_GEMM : F_HIDDEN_GEMM);
     return e;
@@ -518,7 +527,7 @@ smc_status deep_eval(smc_ctx* c) {
         const int nsl = (int)((mc + ROWS_PER_SLICE - 1) / ROWS_PER_SLICE);
         if (slot + nsl > c->head_slices_cap) return fail(c, SMC_EINVAL, "head partial buffer too small");
         fam_begin(c, F_HEAD);
-        e = launch_head(c, c->dact[last], (int64_t)c->J * pitch_of(c, last), pitch_of(c, last), HL, (int)mc, lo, g0,
+        e = launch_head(c, c->dact[last], pitch_of(c, last), c->chunk * pitch_of(c, last), HL, (int)mc, lo, g0,
                         slot, nsl, 0, nullptr, 0);
         fam_end(c, F_HEAD);
         if (e != cudaSuccess) return cuda_check(c, e, "head kernel");
@@ -536,31 +545,33 @@ smc_status deep_eval(smc_ctx* c) {
             g.aug_col = Hp;
             g.aug_out = c->grad + c->segs[L.seg_b].off;
             g.aug_bstride = Hl;
-            fam_begin(c, F_WGRAD_GEMM);
+            fam_begin(c, F_HWGRAD_GEMM);
             e = grouped_gemm(act_rows(c, c->dact[l], l, mc, true, 0), act_rows(c, c->dact[l - 1], l - 1, mc, true, 1),
-                             g, SMC_ACT_IDENTITY, 208, c->stream, c->num_sms);
+                             nullptr, g, SMC_ACT_IDENTITY, 208, c->stream, c->num_sms);
             c->launches++;
-            fam_end(c, F_WGRAD_GEMM);
+            fam_end(c, F_HWGRAD_GEMM);
             if (e != cudaSuccess) return cuda_check(c, e, "tcgen05 hidden weight-gradient GEMM");
             // K6: dZ_{l-1} = (dZ_l W_l) * act'(A_{l-1})
             GArgs d = base_args(c, (int)mc, Hp, Hl, c->J, gk::EPI_BF16_DACT);
             d.aux = c->dact[l - 1];
-            d.aux_ld = (int64_t)c->J * pitch_of(c, l - 1);
-            d.aux_bstride = pitch_of(c, l - 1);
+            d.aux_ld = pitch_of(c, l - 1);
+            d.aux_bstride = c->chunk * pitch_of(c, l - 1);
+            GOperand O{};
             if (l - 1 == 0) {
-                d.out = c->dZT;                         // [rows][J H_0] for the first layer's weight gradient
-                d.ldo = (int64_t)c->J * H0;
-                d.out_bstride = H0;
+                // [rows][J H_0], row-interleaved, for the first layer's weight gradient
+                O.base = c->dZT;
+                O.perm = 1;
+                O.inner = (uint64_t)H0; O.outer = (uint64_t)mc; O.batch = (uint64_t)c->J;
+                O.outer_pitch = (uint64_t)c->J * H0 * 2;
+                O.batch_pitch = (uint64_t)H0 * 2;
             } else {
-                d.out = c->dact[l - 1];                 // over the activations it replaces
-                d.ldo = d.aux_ld;
-                d.out_bstride = d.aux_bstride;
+                O = act_rows(c, c->dact[l - 1], l - 1, mc, false, 0);   // over the activations it replaces
             }
-            fam_begin(c, F_HIDDEN_GEMM);
-            e = grouped_gemm(act_rows(c, c->dact[l], l, mc, false, 0), weights(c, l, true), d, c->layers[l - 1].act,
-                             200, c->stream, c->num_sms);
+            fam_begin(c, F_ADJ_GEMM);
+            e = grouped_gemm(act_rows(c, c->dact[l], l, mc, false, 0), weights(c, l, true), &O, d,
+                             c->layers[l - 1].act, kBf16Half, c->stream, c->num_sms);
             c->launches++;
-            fam_end(c, F_HIDDEN_GEMM);
+            fam_end(c, F_ADJ_GEMM);
             if (e != cudaSuccess) return cuda_check(c, e, "tcgen05 adjoint GEMM");
         }
         // ---- K5: dW_0 | db_0 = dZ_0^T [X, 1] (M = J H_0 flattened)
@@ -585,7 +596,7 @@ smc_status deep_eval(smc_ctx* c) {
             g.aug_col = (int)Din;
             g.aug_out = c->grad + c->segs[L0.seg_b].off;
             fam_begin(c, F_WGRAD_GEMM);
-            e = grouped_gemm(A, B, g, SMC_ACT_IDENTITY, 208, c->stream, c->num_sms);
+            e = grouped_gemm(A, B, nullptr, g, SMC_ACT_IDENTITY, 208, c->stream, c->num_sms);
             c->launches++;
             fam_end(c, F_WGRAD_GEMM);
             if (e != cudaSuccess) return cuda_check(c, e, "tcgen05 first-layer weight-gradient GEMM");
@@ -622,7 +633,7 @@ smc_status deep_predict(smc_ctx* c, const float* x, int64_t n, float* out) {
         for (size_t l = 0; l < nh && e == cudaSuccess; ++l) e = forward_layer(c, l, xb, mc);
         if (e != cudaSuccess) { st = cuda_check(c, e, "tcgen05 forward GEMM (predict)"); break; }
         const int nsl = (int)((mc + ROWS_PER_SLICE - 1) / ROWS_PER_SLICE);
-        e = launch_head(c, c->dact[last], (int64_t)c->J * pitch_of(c, last), pitch_of(c, last), hid(c, last),
+        e = launch_head(c, c->dact[last], pitch_of(c, last), c->chunk * pitch_of(c, last), hid(c, last),
                         (int)mc, 0, 0, 0, nsl, 1, logits, ch * C);
         if (e == cudaSuccess) e = launch_predict_reduce(c, logits, ch * C, C, mc, out + g0 * C, nullptr);
         if (e != cudaSuccess) st = cuda_check(c, e, "predict head / reduce");

@@ -34,6 +34,10 @@
 //   EPI_BF16_ACT  BF16 act(acc + bias[b][n]) (a forward layer);
 //   EPI_BF16_DACT BF16 acc * act'(aux) with aux the stored activation at the
 //                 same position (dZ of a hidden layer, act' from its output).
+// The BF16 epilogues stage each warp's 32 rows x 32 (or, at the end of a
+// half, 8) columns in shared memory and write them with TMA bulk-tensor
+// stores: a warp's thread-per-row registers would otherwise scatter every
+// store instruction over 32 rows.
 // Every wait is a bounded mbarrier wait; on timeout the kernel raises the
 // error flag, drains its own copies and MMAs, frees TMEM and returns.
 #include "internal.h"
@@ -70,25 +74,30 @@ static __device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr, uint32_t lbo
     return d;
 }
 
-template <int NHALF, bool AMN, bool BMN>
+template <int NHALF, bool AMN, bool BMN, bool BF16OUT>
 struct GCfg {
     static constexpr int N1 = NHALF > 128 ? 128 : NHALF;
     static constexpr int N2 = NHALF - N1;
     static constexpr int NB = (NHALF + 63) / 64;                 // MN-major B: 64-wide blocks per CTA
     static constexpr int A_BYTES = BM * BK * 2;
-    static constexpr int B_BYTES = BMN ? NB * 8192 : NHALF * BK * 2;
+    // K-major B: NHALF rows of 128 bytes, rounded up to whole 1024-byte atoms so
+    // every stage starts on a swizzle atom
+    static constexpr int B_BYTES = BMN ? NB * 8192 : (NHALF * BK * 2 + 1023) / 1024 * 1024;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int ACC = (2 * NHALF <= 256) ? 2 : 1;        // TMEM accumulators of 2 NHALF columns
     static constexpr uint32_t ACC_COLS = 256;
-    static constexpr int FIXED = 1024 /*align*/ + 256 /*barriers*/;
+    // BF16 outputs: per epilogue warp two [32 rows][32 cols] staging tiles
+    static constexpr int STAGING = BF16OUT ? EPI_WARPS * 2 * 2048 : 0;
+    static constexpr int FIXED = 1024 /*align*/ + 256 /*barriers*/ + STAGING;
     static constexpr int STAGES_FIT = (SMEM_LIMIT - FIXED) / STAGE_BYTES;
     static constexpr int STAGES = STAGES_FIT > 6 ? 6 : STAGES_FIT;
     static constexpr int SMEM = FIXED + STAGES * STAGE_BYTES;
     static_assert(NHALF % 8 == 0 && N1 % 8 == 0 && N2 % 8 == 0, "B halves in whole 8-row atoms");
     static_assert(N1 % 64 == 0 || N2 == 0, "the second MMA starts on a 64-wide MN block");
     static_assert(2 * NHALF <= 512, "TMEM columns");
-    static_assert(STAGE_BYTES % 1024 == 0 && (N1 * 128) % 1024 == 0, "swizzle atoms");
+    static_assert(STAGE_BYTES % 1024 == 0 && (N2 == 0 || (N1 * 128) % 1024 == 0), "swizzle atoms");
     static_assert(STAGES >= 2, "pipeline depth");
+    static_assert(!BF16OUT || NHALF <= 128, "BF16 outputs: TMEM column = tile column");
 };
 
 template <int ACT>
@@ -140,10 +149,9 @@ __device__ __forceinline__ int tile_col(int t) {
     return NHALF + N1 + (t - 2 * N1 - N2);
 }
 
-// Epilogue of one 8-column piece of one row.
-template <int EPI, int ACT>
-__device__ __forceinline__ void epi_piece(const GArgs& g, int b, int row, int col, const uint32_t* r) {
-    if (EPI == EPI_F32) {
+// FP32 epilogue of one 8-column piece of one row.
+__device__ __forceinline__ void f32_piece(const GArgs& g, int b, int row, int col, const uint32_t* r) {
+    {
         float* o = (float*)g.out + (int64_t)b * g.out_bstride + (int64_t)row * g.ldo;
         const int nmain = g.aug_col >= 0 ? g.aug_col : g.N;
         if (col + 8 <= nmain && ((reinterpret_cast<uintptr_t>(o + col) & 15) == 0)) {
@@ -173,20 +181,24 @@ __device__ __forceinline__ void epi_piece(const GArgs& g, int b, int row, int co
         }
         return;
     }
-    // BF16 epilogues: N is a multiple of 8, so a piece is all in or all out
-    if (col >= g.N) return;
-    const int64_t off = (int64_t)b * g.out_bstride + (int64_t)row * g.ldo + col;
+}
+
+// BF16 epilogues: the eight packed outputs of one piece (columns col..col+7).
+template <int EPI, int ACT>
+__device__ __forceinline__ uint4 bf16_piece(const GArgs& g, int b, int col, const uint32_t* r, uint4 hv) {
     float v[8];
     if (EPI == EPI_BF16_ACT) {
-        const float* bp = g.bias + (int64_t)b * g.bias_bstride + col;
-        const float4 b0 = *reinterpret_cast<const float4*>(bp);
-        const float4 b1 = *reinterpret_cast<const float4*>(bp + 4);
-        const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        float bb[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (col < g.N) {
+            const float* bp = g.bias + (int64_t)b * g.bias_bstride + col;
+            const float4 b0 = *reinterpret_cast<const float4*>(bp);
+            const float4 b1 = *reinterpret_cast<const float4*>(bp + 4);
+            bb[0] = b0.x; bb[1] = b0.y; bb[2] = b0.z; bb[3] = b0.w;
+            bb[4] = b1.x; bb[5] = b1.y; bb[6] = b1.z; bb[7] = b1.w;
+        }
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[e] = act_fwd<ACT>(__uint_as_float(r[e]) + bb[e]);
     } else {
-        const uint4 hv =
-            *reinterpret_cast<const uint4*>(g.aux + (int64_t)b * g.aux_bstride + (int64_t)row * g.aux_ld + col);
         const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&hv);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -198,19 +210,29 @@ __device__ __forceinline__ void epi_piece(const GArgs& g, int b, int row, int co
     __align__(16) __nv_bfloat162 pk[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) pk[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
-    *reinterpret_cast<uint4*>((__nv_bfloat16*)g.out + off) = *reinterpret_cast<const uint4*>(pk);
+    return *reinterpret_cast<const uint4*>(pk);
+}
+
+// TMA store of a staged tile at (column, row) of batch b; perm as load_box.
+__device__ __forceinline__ void store_box(const CUtensorMap* tm, int perm, const void* src, int col, int row, int b) {
+    if (perm == 0) tma_store_3d(tm, src, col, row, b);
+    else tma_store_3d(tm, src, col, b, row);
 }
 
 template <int NHALF, bool AMN, bool BMN, int EPI, int ACT>
 __global__ void __launch_bounds__(THREADS, 1)
-grouped_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GArgs g) {
-    using C = GCfg<NHALF, AMN, BMN>;
+grouped_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const __grid_constant__ CUtensorMap tmO32, const __grid_constant__ CUtensorMap tmO8,
+                    const GArgs g) {
+    constexpr bool BF16OUT = EPI != EPI_F32;
+    using C = GCfg<NHALF, AMN, BMN, BF16OUT>;
     constexpr int STAGES = C::STAGES;
     const int rank = (int)cluster_rank();
     const int cid = blockIdx.x / 2, ncl = gridDim.x / 2;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + STAGES * C::STAGE_BYTES);
+    uint8_t* staging = smem + STAGES * C::STAGE_BYTES;
+    uint64_t* full = (uint64_t*)(staging + C::STAGING);
     uint64_t* empty = full + STAGES;
     uint64_t* tfull = empty + STAGES;
     uint64_t* tempty = tfull + 2;
@@ -327,24 +349,44 @@ grouped_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
         const int ew = warp - 2;
         const int wq = warp & 3;             // TMEM lanes 32 wq .. 32 wq + 31
         const int half = ew >> 2;            // columns [half NHALF, (half + 1) NHALF) of TMEM
-        int acc = 0;
+        constexpr int NP = NHALF / 8;        // 8-column pieces of a half
+        constexpr int NG = (NHALF + 31) / 32;
+        constexpr int LAST_N8 = (NHALF - 32 * (NG - 1)) / 8;
+        // the adjoint's activations of a whole half are loaded before the
+        // accumulator wait (their latency hides behind the MMAs) when they fit
+        constexpr bool PREFETCH = EPI == EPI_BF16_DACT && NP <= 16;
+        uint8_t* my_stage = staging + (BF16OUT ? ew * 2 * 2048 : 0);   // two [32][32] BF16 tiles of this warp
+        int acc = 0, chunk_no = 0;
         uint32_t aph = 0;
         for (int64_t u = cid; u < g.units; u += ncl) {
             int b, tq, tn;
             decode(g, u, b, tq, tn);
+            const int row0 = (2 * tq + rank) * BM + wq * 32;
+            const int row = row0 + lane;
+            const bool row_ok = row < g.M;
+            const int c_begin = half * NHALF;
+            uint4 hv[PREFETCH ? NP : 1];
+#pragma unroll
+            for (int q = 0; q < (PREFETCH ? NP : 1); ++q) {
+                hv[q] = make_uint4(0u, 0u, 0u, 0u);
+                if (PREFETCH) {
+                    const int col = tn * 2 * NHALF + c_begin + 8 * q;
+                    if (row_ok && col < g.N)
+                        hv[q] = *reinterpret_cast<const uint4*>(g.aux + (int64_t)b * g.aux_bstride +
+                                                                (int64_t)row * g.aux_ld + col);
+                }
+            }
             if (!mbar_wait(tfull + acc, aph, abort_flag)) {
                 raise_abort(g, abort_flag, ERR_EPILOGUE);
                 break;
             }
             tc_fence_after();
-            const int row = (2 * tq + rank) * BM + wq * 32 + lane;
-            const bool row_ok = row < g.M;
             const uint32_t tb = tbase + (uint32_t)acc * C::ACC_COLS + ((uint32_t)(wq * 32) << 16);
-            const int c_begin = half * NHALF, c_end = c_begin + NHALF;
-#pragma unroll 1
-            for (int c0 = c_begin; c0 < c_end; c0 += 32) {
+#pragma unroll
+            for (int gi = 0; gi < NG; ++gi) {
+                const int c0 = c_begin + 32 * gi;
                 uint32_t r[32];
-                const int n8 = min(4, (c_end - c0) / 8);
+                const int n8 = gi < NG - 1 ? 4 : LAST_N8;
                 __syncwarp();
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -354,18 +396,66 @@ grouped_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                     }
                 }
                 tmem_ld_wait();
-                if (row_ok) {
+                if (!BF16OUT) {
+                    if (row_ok) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (q < n8)
-                            epi_piece<EPI, ACT>(g, b, row, tn * 2 * NHALF + tile_col<NHALF>(c0 + 8 * q), r + 8 * q);
+                        for (int q = 0; q < 4; ++q)
+                            if (q < n8) f32_piece(g, b, row, tn * 2 * NHALF + tile_col<NHALF>(c0 + 8 * q), r + 8 * q);
+                    }
+                    continue;
                 }
+                // ---- BF16: pack, stage [32 rows][8 n8 cols], TMA store (rows past M and
+                // columns past N are outside the tensor map and not written)
+                const int col0 = tn * 2 * NHALF + c0;
+                uint4 pk[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    pk[q] = make_uint4(0u, 0u, 0u, 0u);
+                    if (q < n8) {
+                        uint4 h = make_uint4(0u, 0u, 0u, 0u);
+                        if (EPI == EPI_BF16_DACT) {
+                            if (PREFETCH) h = hv[PREFETCH ? 4 * gi + q : 0];
+                            else if (row_ok && col0 + 8 * q < g.N)
+                                h = *reinterpret_cast<const uint4*>(g.aux + (int64_t)b * g.aux_bstride +
+                                                                    (int64_t)row * g.aux_ld + col0 + 8 * q);
+                        }
+                        pk[q] = bf16_piece<EPI, ACT>(g, b, col0 + 8 * q, r + 8 * q, h);
+                    }
+                }
+                uint8_t* buf = my_stage + (chunk_no & 1) * 2048;
+                // the store issued two tiles ago has finished reading this buffer
+                if (lane == 0 && chunk_no >= 2) bulk_wait_read1();
+                __syncwarp();
+                if (n8 == 4) {
+                    // row `lane` of a [32][32] tile: four 16-byte pieces, written in a
+                    // lane-rotated order so the 8 lanes of each phase hit distinct banks
+#pragma unroll
+                    for (int it = 0; it < 4; ++it) {
+                        const int pc = (it + (lane >> 1)) & 3;
+                        const uint4 v = pc == 0 ? pk[0] : (pc == 1 ? pk[1] : (pc == 2 ? pk[2] : pk[3]));
+                        *reinterpret_cast<uint4*>(buf + lane * 64 + pc * 16) = v;
+                    }
+                } else {
+                    // a [32][8 n8] tile, n8 < 4 (the end of a half)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                        if (q < n8) *reinterpret_cast<uint4*>(buf + lane * 16 * n8 + q * 16) = pk[q];
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    store_box(n8 == 4 ? &tmO32 : &tmO8, g.out_perm, buf, col0, row0, b);
+                    bulk_commit();
+                }
+                ++chunk_no;
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive_remote(mapa_shared(tempty + acc, 0));
             if (++acc == C::ACC) { acc = 0; aph ^= 1; }
         }
+        if (BF16OUT && lane == 0) bulk_wait_all();   // outstanding output stores complete before the CTA exits
+        __syncwarp();
     }
     tc_fence_before();
     __syncthreads();
@@ -379,7 +469,7 @@ grouped_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
 // ------------------------------------------------------------- host side
 template <int NHALF, bool AMN, bool BMN, int EPI, int ACT>
 static int max_clusters_for(int num_sms) {
-    using C = GCfg<NHALF, AMN, BMN>;
+    using C = GCfg<NHALF, AMN, BMN, EPI != EPI_F32>;
     static int cached = -1;
     if (cached < 0) {
         auto kern = grouped_pair_kernel<NHALF, AMN, BMN, EPI, ACT>;
@@ -412,12 +502,28 @@ static bool operand_map(CUtensorMap* m, const GOperand& o, uint32_t rows) {
     return make_tmap_3d(m, o.base, o.inner, o.batch, o.outer, o.batch_pitch, o.outer_pitch, 1, rows);
 }
 
+// Store map of a BF16 output: boxes of `cols` columns x 32 rows.
+static bool output_map(CUtensorMap* m, const GOperand& o, uint32_t cols) {
+    if (o.perm == 0)
+        return make_store_tmap_3d(m, o.base, o.inner, o.outer, o.batch, o.outer_pitch, o.batch_pitch, cols, 32, 1);
+    return make_store_tmap_3d(m, o.base, o.inner, o.batch, o.outer, o.batch_pitch, o.outer_pitch, cols, 1, 32);
+}
+
 template <int NHALF, bool AMN, bool BMN, int EPI, int ACT>
-static cudaError_t launch_t(const GOperand& A, const GOperand& B, GArgs g, cudaStream_t s, int num_sms) {
-    using C = GCfg<NHALF, AMN, BMN>;
-    CUtensorMap ta, tb;
+static cudaError_t launch_t(const GOperand& A, const GOperand& B, const GOperand* O, GArgs g, cudaStream_t s,
+                            int num_sms) {
+    using C = GCfg<NHALF, AMN, BMN, EPI != EPI_F32>;
+    CUtensorMap ta, tb, to32, to8;
     if (!operand_map(&ta, A, AMN ? 64u : (uint32_t)BM)) return cudaErrorInvalidValue;
     if (!operand_map(&tb, B, BMN ? 64u : (uint32_t)NHALF)) return cudaErrorInvalidValue;
+    if (EPI != EPI_F32) {
+        constexpr uint32_t tail = (uint32_t)(NHALF % 32 == 0 ? 32 : NHALF % 32);
+        if (O == nullptr || !output_map(&to32, *O, 32) || !output_map(&to8, *O, tail)) return cudaErrorInvalidValue;
+        g.out_perm = O->perm;
+    } else {
+        to32 = ta;   // unused by the FP32 epilogue
+        to8 = ta;
+    }
     g.a_perm = A.perm;
     g.b_perm = B.perm;
     g.a_batched = A.batched;
@@ -444,38 +550,39 @@ static cudaError_t launch_t(const GOperand& A, const GOperand& B, GArgs g, cudaS
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, kern, ta, tb, g);
+    e = cudaLaunchKernelEx(&cfg, kern, ta, tb, to32, to8, g);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 template <int NHALF, int EPI, int ACT>
-static cudaError_t launch_maj(const GOperand& A, const GOperand& B, const GArgs& g, cudaStream_t s, int num_sms) {
+static cudaError_t launch_maj(const GOperand& A, const GOperand& B, const GOperand* O, const GArgs& g,
+                              cudaStream_t s, int num_sms) {
     if (A.mn_major) {
-        if (B.mn_major) return launch_t<NHALF, true, true, EPI, ACT>(A, B, g, s, num_sms);
-        return launch_t<NHALF, true, false, EPI, ACT>(A, B, g, s, num_sms);
+        if (B.mn_major) return launch_t<NHALF, true, true, EPI, ACT>(A, B, O, g, s, num_sms);
+        return launch_t<NHALF, true, false, EPI, ACT>(A, B, O, g, s, num_sms);
     }
-    if (B.mn_major) return launch_t<NHALF, false, true, EPI, ACT>(A, B, g, s, num_sms);
-    return launch_t<NHALF, false, false, EPI, ACT>(A, B, g, s, num_sms);
+    if (B.mn_major) return launch_t<NHALF, false, true, EPI, ACT>(A, B, O, g, s, num_sms);
+    return launch_t<NHALF, false, false, EPI, ACT>(A, B, O, g, s, num_sms);
 }
 
 }  // namespace gk
 
-cudaError_t grouped_gemm(const gk::GOperand& A, const gk::GOperand& B, const gk::GArgs& g, int act, int nhalf,
-                         cudaStream_t s, int num_sms) {
+cudaError_t grouped_gemm(const gk::GOperand& A, const gk::GOperand& B, const gk::GOperand* O, const gk::GArgs& g,
+                         int act, int nhalf, cudaStream_t s, int num_sms) {
     using namespace gk;
     if (g.M < 1 || g.N < 1 || g.K < 1 || g.batch < 1) return cudaSuccess;
     if (g.epi == EPI_F32) {
-        if (nhalf == 128) return launch_maj<128, EPI_F32, SMC_ACT_IDENTITY>(A, B, g, s, num_sms);
-        if (nhalf == 208) return launch_maj<208, EPI_F32, SMC_ACT_IDENTITY>(A, B, g, s, num_sms);
+        if (nhalf == 128) return launch_maj<128, EPI_F32, SMC_ACT_IDENTITY>(A, B, O, g, s, num_sms);
+        if (nhalf == 208) return launch_maj<208, EPI_F32, SMC_ACT_IDENTITY>(A, B, O, g, s, num_sms);
         return cudaErrorInvalidValue;
     }
     // the BF16 epilogues follow a K-major A (rows of a layer), N a multiple of 8
-    if (A.mn_major || nhalf != 200 || (g.N % 8 != 0)) return cudaErrorInvalidValue;
+    if (A.mn_major || nhalf != 104 || (g.N % 8 != 0) || O == nullptr) return cudaErrorInvalidValue;
     auto run = [&](auto epi_tag, auto act_tag) -> cudaError_t {
         constexpr int E = decltype(epi_tag)::value, AC = decltype(act_tag)::value;
-        if (B.mn_major) return launch_t<200, false, true, E, AC>(A, B, g, s, num_sms);
-        return launch_t<200, false, false, E, AC>(A, B, g, s, num_sms);
+        if (B.mn_major) return launch_t<104, false, true, E, AC>(A, B, O, g, s, num_sms);
+        return launch_t<104, false, false, E, AC>(A, B, O, g, s, num_sms);
     };
     using EA = std::integral_constant<int, EPI_BF16_ACT>;
     using ED = std::integral_constant<int, EPI_BF16_DACT>;

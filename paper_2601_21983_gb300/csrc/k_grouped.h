@@ -41,7 +41,7 @@ struct GArgs {
     int64_t aug_bstride;
     int* err;                    // device error flag (timeouts)
     // filled by the launcher
-    int a_perm, b_perm, a_batched, b_batched;
+    int a_perm, b_perm, a_batched, b_batched, out_perm;
     int tiles_q, tiles_n, kb_total;
     int64_t units;
 };
@@ -50,9 +50,13 @@ struct GArgs {
 
 // Launch C_b = A_b B_b^T for every batch (see k_grouped.cu).  N tiles of
 // 2 nhalf columns: nhalf 128 (two TMEM accumulators) or 208 (one) for
-// EPI_F32, 200 for the BF16 epilogues (one hidden layer of up to 400 units per
-// tile).  act selects the activation of the BF16 epilogues.
-cudaError_t grouped_gemm(const gk::GOperand& A, const gk::GOperand& B, const gk::GArgs& g, int act, int nhalf,
-                         cudaStream_t s, int num_sms);
+// EPI_F32; 104 (two accumulators, so one tile's epilogue overlaps the next
+// tile's MMAs) for the BF16 epilogues.  act selects the activation of the
+// BF16 epilogues.
+// O: the BF16 epilogues' output as a 3-D array (inner = N columns, outer =
+// M rows, batch), written by TMA stores; NULL for EPI_F32 (out / ldo /
+// out_bstride of GArgs).
+cudaError_t grouped_gemm(const gk::GOperand& A, const gk::GOperand& B, const gk::GOperand* O, const gk::GArgs& g,
+                         int act, int nhalf, cudaStream_t s, int num_sms);
 
 }  // namespace smc

@@ -31,9 +31,9 @@ PROPOSAL_PLAIN, PROPOSAL_LEARNED, PROPOSAL_EXPLORE = 0, 1, 2
 LEARNED_NUM_PARAMS = 706
 STATUS = {0: "SMC_OK", 1: "SMC_EINVAL", 2: "SMC_ENOMEM", 3: "SMC_ECUDA", 4: "SMC_ESTATE",
           5: "SMC_ENUMERIC", 6: "SMC_ETIMEOUT", 7: "SMC_EUNSUPPORTED"}
-N_FAMILIES = 10
+N_FAMILIES = 12
 FAMILIES = ["fwd_gemm", "head", "wgrad_gemm", "hidden_gemm", "leapfrog", "weights", "resample",
-            "simt_net", "reduce", "fused_fwd_head"]
+            "simt_net", "reduce", "fused_fwd_head", "adjoint_gemm", "hidden_wgrad_gemm"]
 
 
 class SMCError(RuntimeError):
