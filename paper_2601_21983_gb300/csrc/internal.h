@@ -152,6 +152,12 @@ struct smc_ctx {
     float* conv_part = nullptr;      // SIMT: per-slice partial weight gradients of the largest conv layer
     // BF16 engine workspace
     std::vector<__nv_bfloat16*> dact;  // deeper networks: activations of hidden layer l [J][chunk][H_l + 8]
+    struct CnnBuffers {              // BF16 CNN engine (k_cnn.cu), per chunk of images
+        __nv_bfloat16 *I1 = nullptr, *Z1 = nullptr, *P1 = nullptr, *I2 = nullptr, *Z2 = nullptr, *P2 = nullptr;
+        uint8_t *idx1 = nullptr, *idx2 = nullptr;
+        __nv_bfloat16 *W1p = nullptr, *W2p = nullptr;
+        float *dW2T = nullptr, *zeros = nullptr, *dW1P = nullptr;
+    } cnn;
     __nv_bfloat16* H1 = nullptr;     // [chunk_pad][J*H]
     __nv_bfloat16* dZT = nullptr;    // [J*H][chunk_pad]
     float* head_part = nullptr;      // [slices][J][C*H + C]
@@ -319,6 +325,21 @@ smc_status deep_alloc(smc_ctx* c);
 void deep_free(smc_ctx* c);
 smc_status deep_eval(smc_ctx* c);
 smc_status deep_predict(smc_ctx* c, const float* x, int64_t n, float* out);
+// ----- BF16 engine for conv -> pool -> conv -> pool -> dense networks (k_cnn.cu)
+bool cnn_model(const smc_ctx* c);
+smc_status cnn_check_model(const smc_ctx* c, std::string* why);
+smc_status cnn_alloc(smc_ctx* c);
+void cnn_free(smc_ctx* c);
+smc_status cnn_eval(smc_ctx* c);
+smc_status cnn_predict(smc_ctx* c, const float* x, int64_t n, float* out);
+// The head kernel of k_deep.cu on activations A (row r of particle j at
+// A + j pitch + r lda, H wide): mode 0 log-likelihood sums, last-layer weight
+// gradient partials to slots [slot_base, slot_base + nslices) and dZ = (dl W)
+// * act' written over A; mode 1 logits to logits[j logits_sj + r C + c].
+cudaError_t deep_launch_head(smc_ctx* c, int act, __nv_bfloat16* A, int64_t lda, int64_t pitch, int H, int rows,
+                             int lo, int64_t g0, int slot_base, int nslices, int mode, float* logits,
+                             int64_t logits_sj);
+constexpr int kHeadRowsPerSlice = 4096;   // rows of one head block (one partial slot)
 cudaError_t tc_gemm_public(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
                            int64_t M, int64_t N, int64_t K, int accumulate, cudaStream_t s, int* err_dev,
                            int num_sms);

@@ -59,12 +59,12 @@ __device__ __forceinline__ uint32_t act_bwd2(float d0, float d1, uint32_t h) {
     return pack2(act_bwd(ACT, d0, hf.x), act_bwd(ACT, d1, hf.y));
 }
 
-template <int KT>
+template <int KT, int NW>
 struct HeadCfg {
     static constexpr int HP = 16 * KT;              // padded hidden width
     static constexpr int HS = HP + 8;               // tile row stride (elements): conflict-free fragments
     static constexpr int FRAG = KT * 32 * 16;       // bytes of one fragment table
-    static constexpr int SMEM = 2 * FRAG + 16 * 4 + TILE * HS * 2 + TILE * DS * 2 + (8 + 4 * 16) * 8;
+    static constexpr int SMEM = 2 * FRAG + 16 * 4 + TILE * HS * 2 + TILE * DS * 2 + (2 * NW + NW * 16) * 8;
 };
 
 // Head and adjoint of the last layer for one particle (blockIdx.y) over one
@@ -72,30 +72,32 @@ struct HeadCfg {
 // particle j's activations is at A + j pitch + r lda.
 //   mode 0: log-likelihood sums, dW / db partials, dZ over the activations;
 //   mode 1: logits only, to logits[j][row][c] (prediction).
-// Warp w owns rows 16 w .. 16 w + 15 of a tile for the logits, dlogits and dZ,
-// and hidden tiles w, w + 4, ... for the weight gradient over all 64 rows.
-template <int KT, int ACT>
-__global__ void __launch_bounds__(128, 2) deep_head_kernel(
+// Warp w < 4 owns rows 16 w .. 16 w + 15 of a tile for the logits, dlogits and
+// dZ; all NW warps share the weight gradient over the tile's 64 rows (warp w:
+// hidden tiles w, w + NW, ...), so a wide layer can use more warps for it.
+template <int KT, int ACT, int NW>
+__global__ void __launch_bounds__(32 * NW, NW == 4 ? 2 : 1) deep_head_kernel(
     __nv_bfloat16* __restrict__ A, int64_t lda, int64_t pitch, int H, int C, int rows, int lo, int64_t g0,
     int64_t rows_a, float ca, float cb, const int32_t* __restrict__ Y, const float* __restrict__ W,
     const float* __restrict__ bvec, float* __restrict__ part_w, double* __restrict__ part_l, int slot_base, int J,
     int mode, float* __restrict__ logits, int64_t logits_sj) {
-    using F = HeadCfg<KT>;
-    constexpr int HP = F::HP, HS = F::HS, NT2 = 2 * KT, MH = (KT + 3) / 4;
+    using F = HeadCfg<KT, NW>;
+    constexpr int HP = F::HP, HS = F::HS, NT2 = 2 * KT, MH = (KT + NW - 1) / NW;
+    constexpr int NT = 32 * NW;
     extern __shared__ __align__(16) uint8_t smraw[];
     uint4* W2F = reinterpret_cast<uint4*>(smraw);                       // logits B fragments [KT][32]
     uint4* W2TF = W2F + KT * 32;                                         // dH B fragments [KT][32]
     float* bs = reinterpret_cast<float*>(W2TF + KT * 32);                // [16]
     __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(bs + 16);       // [TILE][HS]
     __nv_bfloat16* Dl = As + TILE * HS;                                  // [TILE][DS]
-    double* red = reinterpret_cast<double*>(Dl + TILE * DS);             // [4][2] LL sums, [4][16] db
+    double* red = reinterpret_cast<double*>(Dl + TILE * DS);             // [NW][2] LL sums, [NW][16] db
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, q4 = lane & 3;
     const int j = blockIdx.y, sl = blockIdx.x;
 
     // ---- fragment tables of this particle's W [C][H] (zero padded), bias
     const float* Wj = W + (int64_t)j * C * H;
     auto w = [&](int c, int k) { return (c < C && k < H) ? Wj[c * H + k] : 0.0f; };
-    for (int i = t; i < KT * 32; i += 128) {
+    for (int i = t; i < KT * 32; i += NT) {
         const int kt = i / 32, ln = i % 32, gg = ln >> 2, qq = ln & 3;
         const int k0 = 16 * kt + 2 * qq;
         W2F[i] = make_uint4(pack2(w(gg, k0), w(gg, k0 + 1)), pack2(w(gg, k0 + 8), w(gg, k0 + 9)),
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(128, 2) deep_head_kernel(
     }
     if (t < 16) bs[t] = (t < C) ? bvec[(int64_t)j * C + t] : 0.0f;
     // pad columns [H, HP) of the tile stay zero for the whole kernel
-    for (int i = t; i < TILE * (HP - H); i += 128) As[(i / (HP - H)) * HS + H + i % (HP - H)] = __float2bfloat16_rn(0.0f);
+    for (int i = t; i < TILE * (HP - H); i += NT) As[(i / (HP - H)) * HS + H + i % (HP - H)] = __float2bfloat16_rn(0.0f);
     __syncthreads();
 
     const int cls[4] = {2 * q4, 2 * q4 + 1, 8 + 2 * q4, 9 + 2 * q4};
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(128, 2) deep_head_kernel(
     for (int r0 = r_begin; r0 < r_end; r0 += TILE) {
         __syncthreads();   // the previous tile's dZ rows have been copied out
         // ---- (0) the tile's activations (rows past the chunk read as zeros)
-        for (int i = t; i < TILE * pieces; i += 128) {
+        for (int i = t; i < TILE * pieces; i += NT) {
             const int r = i / pieces, pc = i % pieces;
             const int row = r0 + r;
             const bool in = row < r_end;
@@ -139,10 +141,14 @@ __global__ void __launch_bounds__(128, 2) deep_head_kernel(
         cp_async_wait0();
         __syncthreads();
 
-        // ---- (1) logits, log-softmax, dlogits of this warp's 16 rows
-        const int rw = 16 * warp;                      // tile row of the warp's m-tile
+        // ---- (1) logits, log-softmax, dlogits of this warp's 16 rows (warps 0..3)
+        const bool rows_w = warp < 4;
+        const int rw = 16 * (warp & 3);                // tile row of the warp's m-tile
         __nv_bfloat16* Hm = As + rw * HS;
         float cz[2][2][4] = {};
+        float dl[2][4] = {};
+        uint32_t adl[4] = {0u, 0u, 0u, 0u};
+        if (rows_w) {
 #pragma unroll
         for (int kt = 0; kt < KT; ++kt) {
             uint32_t af[4];
@@ -151,7 +157,6 @@ __global__ void __launch_bounds__(128, 2) deep_head_kernel(
             mma16816(cz[kt & 1][0], af, bf.x, bf.y);
             mma16816(cz[kt & 1][1], af, bf.z, bf.w);
         }
-        float dl[2][4];
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             const int m = r0 + rw + g + 8 * half;      // chunk row
@@ -199,16 +204,21 @@ __global__ void __launch_bounds__(128, 2) deep_head_kernel(
                 }
             }
         }
-        if (mode == 1) continue;
+        if (mode != 1) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) db2[e] += dl[e >> 1][e & 1] + dl[e >> 1][2 + (e & 1)];
-        const uint32_t adl[4] = {pack2(dl[0][0], dl[0][1]), pack2(dl[0][2], dl[0][3]), pack2(dl[1][0], dl[1][1]),
-                                 pack2(dl[1][2], dl[1][3])};
-        __nv_bfloat16* Dm = Dl + rw * DS;
-        *reinterpret_cast<uint32_t*>(Dm + g * DS + 2 * q4) = adl[0];
-        *reinterpret_cast<uint32_t*>(Dm + (g + 8) * DS + 2 * q4) = adl[1];
-        *reinterpret_cast<uint32_t*>(Dm + g * DS + 8 + 2 * q4) = adl[2];
-        *reinterpret_cast<uint32_t*>(Dm + (g + 8) * DS + 8 + 2 * q4) = adl[3];
+            for (int e = 0; e < 4; ++e) db2[e] += dl[e >> 1][e & 1] + dl[e >> 1][2 + (e & 1)];
+            adl[0] = pack2(dl[0][0], dl[0][1]);
+            adl[1] = pack2(dl[0][2], dl[0][3]);
+            adl[2] = pack2(dl[1][0], dl[1][1]);
+            adl[3] = pack2(dl[1][2], dl[1][3]);
+            __nv_bfloat16* Dm = Dl + rw * DS;
+            *reinterpret_cast<uint32_t*>(Dm + g * DS + 2 * q4) = adl[0];
+            *reinterpret_cast<uint32_t*>(Dm + (g + 8) * DS + 2 * q4) = adl[1];
+            *reinterpret_cast<uint32_t*>(Dm + g * DS + 8 + 2 * q4) = adl[2];
+            *reinterpret_cast<uint32_t*>(Dm + (g + 8) * DS + 8 + 2 * q4) = adl[3];
+        }
+        }   // rows_w
+        if (mode == 1) continue;
         __syncthreads();   // every warp's dlogits are in the tile
 
         // ---- (2) dW^T [HP x 16] += A^T dl over the tile's 64 rows, this warp's hidden tiles
@@ -220,7 +230,7 @@ __global__ void __launch_bounds__(128, 2) deep_head_kernel(
                 ldsm_x4_t(bd, Dl + (16 * kk + (mi & 1) * 8 + i) * DS + (mi >> 1) * 8);
 #pragma unroll
                 for (int a = 0; a < MH; ++a) {
-                    const int mh = warp + 4 * a;
+                    const int mh = warp + NW * a;
                     if (mh < KT) {
                         uint32_t at[4];
                         ldsm_x4_t(at, As + (16 * kk + (mi >> 1) * 8 + i) * HS + 16 * mh + (mi & 1) * 8);
@@ -233,6 +243,7 @@ __global__ void __launch_bounds__(128, 2) deep_head_kernel(
         __syncthreads();   // every warp has read the whole tile: dZ may overwrite it
 
         // ---- (3) dH = dl W, dZ = dH * act'(A) over this warp's rows, in place
+        if (!rows_w) continue;
 #pragma unroll
         for (int n2 = 0; n2 < NT2; n2 += 2) {
             const uint4 bt = W2TF[(n2 >> 1) * 32 + lane];
@@ -264,7 +275,7 @@ __global__ void __launch_bounds__(128, 2) deep_head_kernel(
     float* pw = part_w + ((int64_t)(slot_base + sl) * J + j) * per;
 #pragma unroll
     for (int a = 0; a < MH; ++a) {
-        const int mh = warp + 4 * a;
+        const int mh = warp + NW * a;
         if (mh >= KT) continue;
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt)
@@ -285,16 +296,17 @@ __global__ void __launch_bounds__(128, 2) deep_head_kernel(
         sa += __shfl_xor_sync(0xffffffffu, sa, o);
         sb += __shfl_xor_sync(0xffffffffu, sb, o);
     }
-    // fixed-order block reduction: red[w][0..1] LL sums, red[8 + w * 16 + c] db
-    if (lane == 0) { red[2 * warp] = sa; red[2 * warp + 1] = sb; }
-    if (g == 0) {
+    // fixed-order block reduction over the row warps: red[w][0..1] LL sums,
+    // red[2 NW + w * 16 + c] db
+    if (lane == 0 && warp < 4) { red[2 * warp] = sa; red[2 * warp + 1] = sb; }
+    if (g == 0 && warp < 4) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) red[8 + warp * 16 + cls[e]] = (double)db2[e];
+        for (int e = 0; e < 4; ++e) red[2 * NW + warp * 16 + cls[e]] = (double)db2[e];
     }
     __syncthreads();
     if (t < 16 && t < C) {
         double s = 0.0;
-        for (int w2 = 0; w2 < 4; ++w2) s += red[8 + w2 * 16 + t];
+        for (int w2 = 0; w2 < 4; ++w2) s += red[2 * NW + w2 * 16 + t];
         pw[C * H + t] = (float)s;
     }
     if (t == 0) {
@@ -324,14 +336,14 @@ __global__ void to_bf16_kernel(const float* __restrict__ x, int64_t n, __nv_bflo
 // ------------------------------------------------------------------ host side
 static int kt_of(int H) {
     const int kt = (H + 15) / 16;
-    return kt <= 8 ? 8 : kt <= 16 ? 16 : kt <= 25 ? 25 : 32;
+    return kt <= 8 ? 8 : kt <= 16 ? 16 : kt <= 25 ? 25 : kt <= 32 ? 32 : 50;
 }
 
-template <int KT, int ACT>
+template <int KT, int ACT, int NW>
 static cudaError_t head_t(smc_ctx* c, dim3 grid, __nv_bfloat16* A, int64_t lda, int64_t pitch, int H, int rows,
                           int lo, int64_t g0, int slot_base, int mode, float* logits, int64_t logits_sj) {
-    using F = HeadCfg<KT>;
-    auto kern = deep_head_kernel<KT, ACT>;
+    using F = HeadCfg<KT, NW>;
+    auto kern = deep_head_kernel<KT, ACT, NW>;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, F::SMEM);
@@ -339,31 +351,44 @@ static cudaError_t head_t(smc_ctx* c, dim3 grid, __nv_bfloat16* A, int64_t lda, 
         attr = true;
     }
     const Layer& LL = c->layers.back();
-    SMC_LAUNCH(c, kern<<<grid, 128, F::SMEM, c->stream>>>(
+    SMC_LAUNCH(c, kern<<<grid, 32 * NW, F::SMEM, c->stream>>>(
                       A, lda, pitch, H, c->n_out, rows, lo, g0, split_row(c), (float)c->coef_a, (float)c->coef_b,
                       c->Y, c->theta + c->segs[LL.seg_w].off, c->theta + c->segs[LL.seg_b].off, c->head_part,
                       c->head_ll, slot_base, c->J, mode, logits, logits_sj));
     return cudaGetLastError();
 }
 
-template <int KT>
+template <int KT, int NW>
 static cudaError_t head_k(smc_ctx* c, int act, dim3 grid, __nv_bfloat16* A, int64_t lda, int64_t pitch, int H,
                           int rows, int lo, int64_t g0, int slot_base, int mode, float* logits, int64_t logits_sj) {
-    if (act == SMC_ACT_RELU) return head_t<KT, SMC_ACT_RELU>(c, grid, A, lda, pitch, H, rows, lo, g0, slot_base, mode, logits, logits_sj);
-    if (act == SMC_ACT_TANH) return head_t<KT, SMC_ACT_TANH>(c, grid, A, lda, pitch, H, rows, lo, g0, slot_base, mode, logits, logits_sj);
-    return head_t<KT, SMC_ACT_IDENTITY>(c, grid, A, lda, pitch, H, rows, lo, g0, slot_base, mode, logits, logits_sj);
+    if (act == SMC_ACT_RELU) return head_t<KT, SMC_ACT_RELU, NW>(c, grid, A, lda, pitch, H, rows, lo, g0, slot_base, mode, logits, logits_sj);
+    if (act == SMC_ACT_TANH) return head_t<KT, SMC_ACT_TANH, NW>(c, grid, A, lda, pitch, H, rows, lo, g0, slot_base, mode, logits, logits_sj);
+    return head_t<KT, SMC_ACT_IDENTITY, NW>(c, grid, A, lda, pitch, H, rows, lo, g0, slot_base, mode, logits, logits_sj);
 }
+
+}  // namespace dp
+
+using namespace dp;
+
+cudaError_t deep_launch_head(smc_ctx* c, int act, __nv_bfloat16* A, int64_t lda, int64_t pitch, int H, int rows,
+                             int lo, int64_t g0, int slot_base, int nslices, int mode, float* logits,
+                             int64_t logits_sj) {
+    const dim3 grid((unsigned)nslices, (unsigned)c->J);
+    switch (kt_of(H)) {
+        case 8: return head_k<8, 4>(c, act, grid, A, lda, pitch, H, rows, lo, g0, slot_base, mode, logits, logits_sj);
+        case 16: return head_k<16, 4>(c, act, grid, A, lda, pitch, H, rows, lo, g0, slot_base, mode, logits, logits_sj);
+        case 25: return head_k<25, 4>(c, act, grid, A, lda, pitch, H, rows, lo, g0, slot_base, mode, logits, logits_sj);
+        case 32: return head_k<32, 4>(c, act, grid, A, lda, pitch, H, rows, lo, g0, slot_base, mode, logits, logits_sj);
+        default: return head_k<50, 8>(c, act, grid, A, lda, pitch, H, rows, lo, g0, slot_base, mode, logits, logits_sj);
+    }
+}
+
+namespace dp {
 
 static cudaError_t launch_head(smc_ctx* c, __nv_bfloat16* A, int64_t lda, int64_t pitch, int H, int rows, int lo,
                                int64_t g0, int slot_base, int nslices, int mode, float* logits, int64_t logits_sj) {
-    const int act = c->layers[c->layers.size() - 2].act;
-    const dim3 grid((unsigned)nslices, (unsigned)c->J);
-    switch (kt_of(H)) {
-        case 8: return head_k<8>(c, act, grid, A, lda, pitch, H, rows, lo, g0, slot_base, mode, logits, logits_sj);
-        case 16: return head_k<16>(c, act, grid, A, lda, pitch, H, rows, lo, g0, slot_base, mode, logits, logits_sj);
-        case 25: return head_k<25>(c, act, grid, A, lda, pitch, H, rows, lo, g0, slot_base, mode, logits, logits_sj);
-        default: return head_k<32>(c, act, grid, A, lda, pitch, H, rows, lo, g0, slot_base, mode, logits, logits_sj);
-    }
+    return deep_launch_head(c, c->layers[c->layers.size() - 2].act, A, lda, pitch, H, rows, lo, g0, slot_base,
+                            nslices, mode, logits, logits_sj);
 }
 
 // Hidden width of layer l (l < L - 1) and the pitch of its activation rows.
@@ -446,7 +471,12 @@ static cudaError_t forward_layer(smc_ctx* c, size_t l, const __nv_bfloat16* x, i
 
 using namespace dp;
 
-bool deep_model(const smc_ctx* c) { return c->layers.size() > 2; }
+bool deep_model(const smc_ctx* c) {
+    if (c->layers.size() <= 2) return false;
+    for (const Layer& L : c->layers)
+        if (L.kind != SMC_LAYER_DENSE) return false;
+    return true;
+}
 
 smc_status deep_check_model(const smc_ctx* c, std::string* why) {
     for (size_t l = 0; l < c->layers.size(); ++l) {

@@ -575,12 +575,18 @@ cudaError_t grouped_gemm(const gk::GOperand& A, const gk::GOperand& B, const gk:
     if (g.epi == EPI_F32) {
         if (nhalf == 128) return launch_maj<128, EPI_F32, SMC_ACT_IDENTITY>(A, B, O, g, s, num_sms);
         if (nhalf == 208) return launch_maj<208, EPI_F32, SMC_ACT_IDENTITY>(A, B, O, g, s, num_sms);
+        // narrow weight gradients (convolution layers), both operands MN-major
+        if (!A.mn_major || !B.mn_major) return cudaErrorInvalidValue;
+        if (nhalf == 16) return launch_t<16, true, true, EPI_F32, SMC_ACT_IDENTITY>(A, B, O, g, s, num_sms);
+        if (nhalf == 48) return launch_t<48, true, true, EPI_F32, SMC_ACT_IDENTITY>(A, B, O, g, s, num_sms);
         return cudaErrorInvalidValue;
     }
     // the BF16 epilogues follow a K-major A (rows of a layer), N a multiple of 8
-    if (A.mn_major || nhalf != 104 || (g.N % 8 != 0) || O == nullptr) return cudaErrorInvalidValue;
+    if (A.mn_major || (nhalf != 104 && nhalf != 16) || (g.N % 8 != 0) || O == nullptr) return cudaErrorInvalidValue;
+    if (nhalf == 16 && B.mn_major) return cudaErrorInvalidValue;
     auto run = [&](auto epi_tag, auto act_tag) -> cudaError_t {
         constexpr int E = decltype(epi_tag)::value, AC = decltype(act_tag)::value;
+        if (nhalf == 16) return launch_t<16, false, false, E, AC>(A, B, O, g, s, num_sms);
         if (B.mn_major) return launch_t<104, false, true, E, AC>(A, B, O, g, s, num_sms);
         return launch_t<104, false, false, E, AC>(A, B, O, g, s, num_sms);
     };

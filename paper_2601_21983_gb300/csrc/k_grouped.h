@@ -50,9 +50,11 @@ struct GArgs {
 
 // Launch C_b = A_b B_b^T for every batch (see k_grouped.cu).  N tiles of
 // 2 nhalf columns: nhalf 128 (two TMEM accumulators) or 208 (one) for
-// EPI_F32; 104 (two accumulators, so one tile's epilogue overlaps the next
-// tile's MMAs) for the BF16 epilogues.  act selects the activation of the
-// BF16 epilogues.
+// EPI_F32, or 16 / 48 with both operands MN-major (the narrow weight
+// gradients of convolution layers); 104 (two accumulators, so one tile's
+// epilogue overlaps the next tile's MMAs) or 16 (a 32-channel convolution,
+// K-major operands) for the BF16 epilogues.  act selects the activation of
+// the BF16 epilogues.
 // O: the BF16 epilogues' output as a 3-D array (inner = N columns, outer =
 // M rows, batch), written by TMA stores; NULL for EPI_F32 (out / ldo /
 // out_bstride of GArgs).

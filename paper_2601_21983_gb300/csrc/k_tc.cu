@@ -767,6 +767,7 @@ __global__ void to_bf16_rows_kernel(const float* __restrict__ x, int64_t n, int6
 
 // ---------------------------------------------------------------- engine
 smc_status tc_check_model(const smc_ctx* c, std::string* why) {
+    if (cnn_model(c)) return cnn_check_model(c, why);
     if (deep_model(c)) return deep_check_model(c, why);
     if (c->layers.size() != 2 || c->layers[0].kind != SMC_LAYER_DENSE || c->layers[1].kind != SMC_LAYER_DENSE) {
         *why = "BF16 tensor-core path needs a dense network with one hidden layer";
@@ -787,6 +788,7 @@ static inline int64_t rup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 static int64_t ldh_of(const smc_ctx* c) { return rup((int64_t)c->J * c->layers[0].out_feat(), 8); }
 
 smc_status tc_alloc(smc_ctx* c) {
+    if (cnn_model(c)) return cnn_alloc(c);
     if (deep_model(c)) return deep_alloc(c);
     const int64_t H = c->layers[0].out_feat();
     const int64_t JH = (int64_t)c->J * H;
@@ -819,6 +821,10 @@ smc_status tc_alloc(smc_ctx* c) {
 }
 
 void tc_free(smc_ctx* c) {
+    if (cnn_model(c)) {
+        cnn_free(c);
+        return;
+    }
     if (deep_model(c)) {
         deep_free(c);
         return;
@@ -901,6 +907,7 @@ static cudaError_t launch_wgrad(smc_ctx* c, int64_t g0, int64_t mc, bool with_b1
 }
 
 smc_status tc_eval(smc_ctx* c) {
+    if (cnn_model(c)) return cnn_eval(c);
     if (deep_model(c)) return deep_eval(c);
     const Layer& L0 = c->layers[0];
     const Layer& L1 = c->layers[1];
@@ -968,6 +975,7 @@ smc_status tc_eval(smc_ctx* c) {
 }
 
 smc_status tc_predict(smc_ctx* c, const float* x, int64_t n, float* out) {
+    if (cnn_model(c)) return cnn_predict(c, x, n, out);
     if (deep_model(c)) return deep_predict(c, x, n, out);
     const Layer& L0 = c->layers[0];
     const Layer& L1 = c->layers[1];
