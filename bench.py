@@ -180,10 +180,14 @@ def _oracle_eval_rate(seconds, J_s, M_s, seed, scale=False):
     scale: the 784-400-400-10 network instead of 784-100-10."""
     import synthetic
     from oracle import nn
-    layers = [("dense", DIN, 400), ("dense", 400, 400), ("dense", 400, NCLS)] if scale else \
-        [("dense", DIN, H), ("dense", H, NCLS)]
-    spec = nn.Spec(layers, (DIN,), nn.RELU)
-    X, y = synthetic.template_images(M_s, seed=3)
+    if scale == "cnn":
+        spec = nn.Spec(CNN_LAYERS, (3, 32, 32), nn.TANH)
+        X, y = synthetic.smooth_field_images(M_s, seed=3)
+    else:
+        layers = [("dense", DIN, 400), ("dense", 400, 400), ("dense", 400, NCLS)] if scale else \
+            [("dense", DIN, H), ("dense", H, NCLS)]
+        spec = nn.Spec(layers, (DIN,), nn.RELU)
+        X, y = synthetic.template_images(M_s, seed=3)
     X = X.astype(np.float64)
     th = synthetic.particles(J_s, spec.n_params, seed, std=0.05).astype(np.float64)
     coef = np.full(M_s, N_TRAIN / M_s)
@@ -276,26 +280,50 @@ def scale_cpu_baseline(seconds=6.0, M_s=500):
             "all_cores": {"value": evn * M_s / eln, "unit": UNIT, "cores": cores}}
 
 
-def run_scale_config(steps, warmup, J=SCALE_J, n=N_TRAIN, e2e=True, roofline=True, cpu=True):
+CNN_LAYERS = [("conv", 3, 16, 5), ("pool2",), ("conv", 16, 32, 5), ("pool2",), ("dense", 800, NCLS)]
+CNN_J, CNN_N = 128, 50000
+CNN_FLOP = 11.49e6         # per particle-sample gradient evaluation (4,457,600 forward + 7,033,600 backward)
+
+
+def cnn_workload(J, n):
+    return {"workload": (f"CNN conv5x5 3->16, tanh, pool, conv5x5 16->32, tanh, pool, fc 800->{NCLS} (D = 22,058), "
+                         f"J={J} particles, synthetic {n} 3x32x32 10-class smooth-field images, full data |D_k|={n} "
+                         f"(the end of SDA's annealing), HMC S={S_LF}, h={STEP_H}, BF16 tcgen05 convolutions with "
+                         f"FP32 accumulation"),
+            "particles": J, "rows": n, "schedule": "fb", "leapfrog_steps": S_LF,
+            "l2": "no flush: per-step working set (im2col and activation arrays of ~16 GB per chunk) above the L2"}
+
+
+def _section(kind, steps, warmup, J, n, e2e=True, roofline=True, cpu=True):
     """One SMC iteration (anneal, resample, HMC move with S = 3 gradient
-    evaluations over all n rows, reweight) of the scale configuration
-    (784-400-400-10, J = 1024) through the C ABI, device-timed with CUDA events
-    on the library's stream; then the same end to end with the rows streamed
-    from pinned host memory each step; then per-kernel times for the roofline."""
+    evaluations over all n rows, reweight) of another configuration through
+    the C ABI, device-timed with CUDA events on the library's stream; then the
+    same end to end with the rows streamed from pinned host memory each step;
+    then per-kernel-family times for the roofline.  kind: "scale" (MLP
+    784-400-400-10, the engine for two or more hidden layers) or "cnn" (the
+    CIFAR-shaped CNN)."""
     import torch
+    import synthetic
     from paper_2601_21983_gb300 import smc as S
     S.load()
     stream = torch.cuda.current_stream()
-    X, y = make_data(n, seed=0)
+    if kind == "scale":
+        X, y = make_data(n, seed=0)
+        model = S.make_model(SCALE_LAYERS, (DIN,), S.ACT_RELU)
+        flop_unit, workload = SCALE_FLOP, scale_workload(J, n)
+    else:
+        X, y = synthetic.smooth_field_images(n, seed=0)
+        model = S.make_model(CNN_LAYERS, (3, 32, 32), S.ACT_TANH)
+        flop_unit, workload = CNN_FLOP, cnn_workload(J, n)
     Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
-    model = S.make_model(SCALE_LAYERS, (DIN,), S.ACT_RELU)
     sched = S.make_schedule("fb", n, n, K_SCHED)
 
     def new_ctx(timing=0):
         ctx = S.smc_init(model, Xd, y_class=yd, cfg=S.make_config(J, 4321, S.PREC_BF16, stream=stream, timing=timing))
         D = S.smc_num_params(ctx)
-        S.smc_set_state_device(ctx, 0.05 * torch.randn(J, D, device="cuda",
-                                                         generator=torch.Generator(device="cuda").manual_seed(5)))
+        std = 0.05 if kind == "scale" else 0.1
+        S.smc_set_state_device(ctx, std * torch.randn(J, D, device="cuda",
+                                                        generator=torch.Generator(device="cuda").manual_seed(5)))
         S.smc_set_schedule(ctx, sched)
         return ctx
 
@@ -323,7 +351,7 @@ def run_scale_config(steps, warmup, J=SCALE_J, n=N_TRAIN, e2e=True, roofline=Tru
     ms = ev0.elapsed_time(ev1)
     n1, _, _ = S.smc_get_counters(ctx)
     out = {"metric": METRIC, "value": evals[0] / (ms / 1e3), "unit": UNIT, "steps": steps, "warmup": warmup,
-           "ms_per_step": ms / steps, "dtype": "bf16", "data": "synthetic", "config": scale_workload(J, n),
+           "ms_per_step": ms / steps, "dtype": "bf16", "data": "synthetic", "config": workload,
            "gpu_launches": n1 - n0, "last_ess": st["ess"]}
     if e2e:
         perm = S.smc_get_permutation(ctx, n)
@@ -355,14 +383,26 @@ def run_scale_config(steps, warmup, J=SCALE_J, n=N_TRAIN, e2e=True, roofline=Tru
         S.smc_destroy(ctx)
         hbm, tf_burst, tf_sus, src = peaks()
         units = float(n) * J                           # particle-sample pairs per evaluation
-        H = SCALE_H
-        work = {"fwd_gemm": ("tensor", 2.0 * units * H * DIN),
-                "hidden_gemm": ("tensor", 2.0 * units * H * H),
-                "adjoint_gemm": ("tensor", 2.0 * units * H * H),
-                "hidden_wgrad_gemm": ("tensor", 2.0 * units * H * (H + 1)),
-                "wgrad_gemm": ("tensor", 2.0 * units * H * (DIN + 1)),
-                # the head reads the last hidden activations and writes dZ over them (BF16)
-                "head": ("hbm", 2.0 * units * H * 2.0)}
+        if kind == "scale":
+            H = SCALE_H
+            work = {"fwd_gemm": ("tensor", 2.0 * units * H * DIN),
+                    "hidden_gemm": ("tensor", 2.0 * units * H * H),
+                    "adjoint_gemm": ("tensor", 2.0 * units * H * H),
+                    "hidden_wgrad_gemm": ("tensor", 2.0 * units * H * (H + 1)),
+                    "wgrad_gemm": ("tensor", 2.0 * units * H * (DIN + 1)),
+                    # the head reads the last hidden activations and writes dZ over them (BF16)
+                    "head": ("hbm", 2.0 * units * H * 2.0)}
+        else:
+            # conv 1 (784 positions x 16 x 75), conv 2 (100 x 32 x 400), their weight
+            # gradients (with the bias column) and the conv-2 data gradient
+            work = {"fwd_gemm": ("tensor", 2.0 * units * 784 * 16 * 75),
+                    "hidden_gemm": ("tensor", 2.0 * units * 100 * 32 * 400),
+                    "hidden_wgrad_gemm": ("tensor", 2.0 * units * 100 * 32 * 401),
+                    "adjoint_gemm": ("tensor", 2.0 * units * 100 * 32 * 400),
+                    "wgrad_gemm": ("tensor", 2.0 * units * 784 * 16 * 76),
+                    # pooling, im2col of the pooled maps and col2im move at least the conv-2
+                    # im2col rows (written once, read by two GEMMs) and the data gradient once
+                    "simt_net": ("hbm", units * (100 * 408 * 2.0 + 100 * 400 * 2.0))}
         kern = {}
         gemm_flop, gemm_ms = 0.0, 0.0
         for k, (bound, amount) in work.items():
@@ -388,16 +428,51 @@ def run_scale_config(steps, warmup, J=SCALE_J, n=N_TRAIN, e2e=True, roofline=Tru
         roof["peak_kind"] = f"{src} " + ("bf16_tflops (burst)" if roof["bound"] == "tensor" else "hbm_gbs")
         roof["all_gemms"] = {"achieved": gemm_flop / (gemm_ms / 1e3) / 1e12, "unit": "TFLOP/s",
                              "frac": gemm_flop / (gemm_ms / 1e3) / 1e12 / tf_burst, "ms_per_eval": gemm_ms}
-        roof["whole_step"] = {"achieved": units * SCALE_FLOP * S_LF / (out["ms_per_step"] / 1e3) / 1e12,
+        roof["whole_step"] = {"achieved": units * flop_unit * S_LF / (out["ms_per_step"] / 1e3) / 1e12,
                               "unit": "TFLOP/s",
-                              "frac": units * SCALE_FLOP * S_LF / (out["ms_per_step"] / 1e3) / 1e12 / tf_burst}
+                              "frac": units * flop_unit * S_LF / (out["ms_per_step"] / 1e3) / 1e12 / tf_burst}
         roof["others"] = {k: {"frac": round(v["frac"], 4), "achieved": round(v["achieved"], 1), "unit": v["unit"],
                               "ms_per_eval": round(v["ms_per_eval"], 3)} for k, v in kern.items() if k != dom}
         out["roofline"] = roof
         out["families_ms"] = {k: {"ms": times[k], "calls": calls[k]} for k in times if calls[k]}
     if cpu:
-        out["cpu_baseline"] = scale_cpu_baseline()
+        out["cpu_baseline"] = scale_cpu_baseline() if kind == "scale" else cnn_cpu_baseline()
     return out
+
+
+def run_scale_config(steps, warmup, J=SCALE_J, n=N_TRAIN, e2e=True, roofline=True, cpu=True):
+    return _section("scale", steps, warmup, J, n, e2e, roofline, cpu)
+
+
+def run_cnn_config(steps, warmup, J=CNN_J, n=CNN_N, e2e=True, roofline=True, cpu=True):
+    return _section("cnn", steps, warmup, J, n, e2e, roofline, cpu)
+
+
+def cnn_cpu_baseline(seconds=6.0, M_s=20):
+    """The FP64 oracle on a bounded sample of the CNN configuration: single
+    particles over M_s images, one single-threaded process and one per core."""
+    cores = host_threads()
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+
+    def workers(nw):
+        cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", str(seconds), "1", str(M_s)]
+        procs = [subprocess.Popen(cmd + [str(30 + w), "--cnn"], env=env, stdout=subprocess.PIPE,
+                                  stderr=subprocess.DEVNULL, text=True) for w in range(nw)]
+        total, longest = 0, 0.0
+        for p in procs:
+            o, _ = p.communicate(timeout=300)
+            ev, el = json.loads(o.strip().splitlines()[-1])
+            total, longest = total + ev, max(longest, el)
+        return total, longest
+
+    ev1, el1 = workers(1)
+    evn, eln = workers(cores)
+    return {"value": evn * M_s / eln, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle gradient evaluations of single particles of the CNN over {M_s} images, "
+                      f"{seconds:.0f} s per run: {cores} single-threaded processes ({evn} evaluations) and one "
+                      f"({ev1} evaluations)",
+            "single_thread": {"value": ev1 * M_s / el1, "unit": UNIT, "cores": 1},
+            "all_cores": {"value": evn * M_s / eln, "unit": UNIT, "cores": cores}}
 
 
 def run_reference(args):
@@ -667,11 +742,17 @@ def main():
     ap.add_argument("--scale-steps", type=int, default=5)
     ap.add_argument("--scale-J", type=int, default=SCALE_J, help="particles of the scale section (profiling runs)")
     ap.add_argument("--scale-n", type=int, default=N_TRAIN, help="rows of the scale section (profiling runs)")
+    ap.add_argument("--no-cnn", action="store_true", help="leave the CNN section out")
+    ap.add_argument("--cnn-only", action="store_true", help="only the CNN section")
+    ap.add_argument("--cnn-steps", type=int, default=3)
+    ap.add_argument("--cnn-J", type=int, default=CNN_J, help="particles of the CNN section (profiling runs)")
+    ap.add_argument("--cnn-n", type=int, default=CNN_N, help="images of the CNN section (profiling runs)")
     ap.add_argument("--tta-explore", type=int, default=30)
     ap.add_argument("--tta-every", type=int, default=4)
     if len(sys.argv) >= 6 and sys.argv[1] == "--oracle-worker":
         sec, j_s, m_s, seed = float(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]), int(sys.argv[5])
-        print(json.dumps(list(_oracle_eval_rate(sec, j_s, m_s, seed, scale="--scale" in sys.argv[6:]))), flush=True)
+        which = "cnn" if "--cnn" in sys.argv[6:] else ("--scale" in sys.argv[6:])
+        print(json.dumps(list(_oracle_eval_rate(sec, j_s, m_s, seed, scale=which))), flush=True)
         return
     args = ap.parse_args()
     args.steps = max(1, args.steps)
@@ -683,6 +764,12 @@ def main():
         return run_tta(args)
     if args.grid:
         return run_grid(args)
+    if args.cnn_only:
+        line = run_cnn_config(args.cnn_steps, max(3, args.warmup), J=args.cnn_J, n=args.cnn_n,
+                              cpu=not args.no_cpu_baseline, e2e=not args.no_e2e, roofline=not args.no_roofline)
+        line["n_gpus"] = 1
+        print(json.dumps(line), flush=True)
+        return
     if args.scale_only:
         line = run_scale_config(args.scale_steps, max(3, args.warmup), J=args.scale_J, n=args.scale_n,
                                 cpu=not args.no_cpu_baseline, e2e=not args.no_e2e, roofline=not args.no_roofline)
@@ -849,6 +936,8 @@ def main():
         if world == 1 and not args.no_scale:
             line["scale_config"] = run_scale_config(args.scale_steps, max(3, args.warmup),
                                                     cpu=not args.no_cpu_baseline)
+        if world == 1 and not args.no_cnn:
+            line["cnn_config"] = run_cnn_config(args.cnn_steps, max(3, args.warmup), cpu=not args.no_cpu_baseline)
         if world == 1 and not args.no_tta:
             line["tta"] = tta_compare(args.J, args.n, args.tta_iters, list(range(args.tta_seeds)), args.tta_every,
                                       args.tta_explore)
