@@ -667,24 +667,36 @@ def run_tta(args):
 
 
 def run_grid(args):
-    """The scheme grid of Sec. 4 (Table 1) on the MNIST-shaped stand-in: every
+    """The scheme grid of Sec. 4 (Table 1) on a synthetic stand-in: every
     data-annealing scheme (Sec. 3.1: Constant, FB, CTR, Linear, Automated, SDA,
     and Constant / CTR with a fresh mini-batch per iteration) x {LD (S = 1),
     HMC (S = 3)} from the same seed for K iterations, C = kappa = the
     mini-batch size.  Runtime = GPU-synchronous wall time over the
     iterations (test evaluation excluded); then the posterior-predictive
-    accuracy and NLL on a separate test draw."""
+    accuracy and NLL on a separate test draw.  --grid-model mlp: the
+    MNIST-shaped images with MLP 784-100-10; cnn: the CIFAR-shaped images with
+    the CNN (BF16 CNN engine)."""
     import torch
     from paper_2601_21983_gb300 import smc as S
     S.load()
     stream = torch.cuda.current_stream()
     import synthetic
-    X, y = make_data(args.n, seed=0)
-    Xt, yt = synthetic.template_images(10000, seed=0, test=True)
+    if args.grid_model == "cnn":
+        n = args.grid_n or 10000
+        X, y = synthetic.smooth_field_images(n, seed=0)
+        Xt, yt = synthetic.smooth_field_images(2000, seed=0, test=True)
+        model = S.make_model(CNN_LAYERS, (3, 32, 32), S.ACT_TANH)
+        desc = (f"CNN conv5x5 3->16, pool, conv5x5 16->32, pool, fc 800->{NCLS} (tanh), J={args.J}, {n} synthetic "
+                f"3x32x32 smooth-field images")
+    else:
+        n = args.grid_n or args.n
+        X, y = make_data(n, seed=0)
+        Xt, yt = synthetic.template_images(10000, seed=0, test=True)
+        model = S.make_model([("dense", DIN, H), ("dense", H, NCLS)], (DIN,), S.ACT_RELU)
+        desc = f"MLP {DIN}-{H}-{NCLS} ReLU, J={args.J}, {n} synthetic images"
     Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
     Xtd = torch.from_numpy(Xt).cuda()
-    probs = torch.empty((10000, NCLS), device="cuda", dtype=torch.float32)
-    model = S.make_model([("dense", DIN, H), ("dense", H, NCLS)], (DIN,), S.ACT_RELU)
+    probs = torch.empty((len(yt), NCLS), device="cuda", dtype=torch.float32)
     K, mb = args.grid_iters, args.grid_mb
     rows = []
     for kernel, steps in [("LD", 1), ("HMC", S_LF)]:
@@ -712,9 +724,8 @@ def run_grid(args):
         fb = next(q for q in rows if q["kernel"] == r["kernel"] and q["scheme"] == "fb")
         r["speedup_vs_fb"] = fb["seconds"] / r["seconds"]
     print(json.dumps({"metric": "scheme grid (Sec. 4 Table 1 on synthetic stand-ins)", "rows": rows,
-                      "config": {"workload": f"MLP {DIN}-{H}-{NCLS} ReLU, J={args.J}, {args.n} synthetic images, "
-                                             f"C=kappa={mb}, K={K}, h={STEP_H}, BF16, seed 7",
-                                 "test_rows": 10000}}), flush=True)
+                      "config": {"workload": f"{desc}, C=kappa={mb}, K={K}, h={STEP_H}, BF16, seed 7",
+                                 "test_rows": len(yt)}}), flush=True)
 
 
 def main():
@@ -733,7 +744,11 @@ def main():
                     help="gradient-evaluation throughput of another configuration (FP32 engine)")
     ap.add_argument("--grid", action="store_true", help="every DA scheme x {LD, HMC}: runtime and test accuracy")
     ap.add_argument("--grid-iters", type=int, default=200)
+    ap.add_argument("--grid-model", choices=["mlp", "cnn"], default="mlp")
+    ap.add_argument("--grid-n", type=int, default=0, help="training rows of the grid (0: 60000 mlp, 10000 cnn)")
     ap.add_argument("--grid-mb", type=int, default=500)
+    ap.add_argument("--dist-backend", default="nccl", help="collective backend of multi-rank runs (gloo: tests)")
+    ap.add_argument("--trace", action="store_true", help="add each timed step's global ESS and ancestors")
     ap.add_argument("--tta-iters", type=int, default=200)
     ap.add_argument("--tta-seeds", type=int, default=5)
     ap.add_argument("--no-tta", action="store_true", help="leave the time-to-accuracy comparison out of the line")
@@ -783,32 +798,59 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
+    torch.cuda.set_device(local % max(1, torch.cuda.device_count()))
     dist = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group(args.dist_backend)
     S.load()
     stream = torch.cuda.current_stream()
 
-    X, y = make_data(args.n, seed=rank)
+    # One sampler of J particles per rank (weak scaling): on N ranks the J N
+    # particles are sharded J per rank over replicated data; the ranks gather
+    # the log-weights for the global normalisation and ESS after every move,
+    # add the SDA moments, and exchange particle rows when the global ESS falls
+    # below J N / 2 (shard.py).
+    X, y = make_data(args.n, seed=0)
     Xd = torch.from_numpy(X).cuda()
     yd = torch.from_numpy(y).cuda()
     model = S.make_model([("dense", DIN, H), ("dense", H, NCLS)], (DIN,), S.ACT_RELU)
-    cfg = S.make_config(args.J, 1234 + rank, S.PREC_BF16, stream=stream)
-    ctx = S.smc_init(model, Xd, y_class=yd, cfg=cfg)
+    cfg = S.make_config(args.J, 1234, S.PREC_BF16, stream=stream)
     sched = S.make_schedule("linear", MB, MB, K_SCHED, k_start=K_START)
-    S.smc_set_schedule(ctx, sched)
+    sharded = None
+    if world > 1:
+        from paper_2601_21983_gb300.shard import ShardedSampler
+        sharded = ShardedSampler(model, Xd, args.J * world, cfg, y_class=yd)
+        ctx = sharded.ctx
+        sharded.set_schedule(sched)
+    else:
+        ctx = S.smc_init(model, Xd, y_class=yd, cfg=cfg)
+        S.smc_set_schedule(ctx, sched)
     evals = [0]
+    trace = []          # (global ESS, resampled?, ancestors) per step when --trace
+
+    def iteration(upload_next=None):
+        """anneal -> resample -> move, on one context or on the sharded sampler;
+        upload_next: pinned rows to stream in for the following iteration."""
+        if sharded is not None:
+            sharded.anneal_next()
+            did, anc = sharded.resample()
+        else:
+            S.smc_anneal_next(ctx)
+            did = S.smc_resample(ctx)
+            anc = S.smc_get_ancestors(ctx, args.J) if (did and args.trace) else None
+        if upload_next is not None:
+            S.smc_upload_rows_async(ctx, 0, upload_next[0], upload_next[1])
+        st = sharded.step(STEP_H, S_LF) if sharded is not None else S.smc_step(ctx, STEP_H, S_LF)
+        evals[0] += st["grad_evals"] * st["rows"] * args.J
+        if args.trace:
+            trace.append([float(st["ess"]), bool(did), None if anc is None else [int(a) for a in anc]])
+        return st
 
     def one_step(upload=None):
         if upload is not None:
             S.smc_upload_rows(ctx, 0, upload[0], upload[1])
-        info = S.smc_anneal_next(ctx)
-        S.smc_resample(ctx)
-        st = S.smc_step(ctx, STEP_H, S_LF)
-        evals[0] += st["grad_evals"] * st["rows"] * args.J
-        return st
+        return iteration()
 
     clocks = Clocks(local) if rank == 0 else None
     for _ in range(args.warmup):
@@ -818,6 +860,7 @@ def main():
         dist.barrier()
     n0, _, _ = S.smc_get_counters(ctx)
     evals[0] = 0
+    trace.clear()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     h0 = time.time()
@@ -833,8 +876,10 @@ def main():
         clocks.mark(h0, h1)
     clk = clocks.stop() if clocks else None
     my_evals = evals[0]
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    e = torch.tensor([float(my_evals)], dtype=torch.float64, device="cuda")
+    timed_trace = list(trace)
+    red_dev = "cpu" if args.dist_backend == "gloo" else "cuda"     # gloo reduces host tensors
+    t = torch.tensor([ms], dtype=torch.float64, device=red_dev)
+    e = torch.tensor([float(my_evals)], dtype=torch.float64, device=red_dev)
     if dist:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.all_reduce(e, op=dist.ReduceOp.SUM)
@@ -857,18 +902,13 @@ def main():
         # i computes and takes effect at step i+1's smc_anneal_next
         S.smc_upload_rows_async(ctx, 0, hxn, hyn)
         for i in range(args.steps):
-            S.smc_anneal_next(ctx)
-            S.smc_resample(ctx)
-            if i + 1 < args.steps:
-                S.smc_upload_rows_async(ctx, 0, hxn, hyn)
-            st = S.smc_step(ctx, STEP_H, S_LF)
-            evals[0] += st["grad_evals"] * st["rows"] * args.J
+            iteration((hxn, hyn) if i + 1 < args.steps else None)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         e2e_evals = evals[0]
         if dist:   # whole job: every rank's evaluations over the slowest rank's time
-            te = torch.tensor([el], dtype=torch.float64, device="cuda")
-            ee = torch.tensor([float(e2e_evals)], dtype=torch.float64, device="cuda")
+            te = torch.tensor([el], dtype=torch.float64, device=red_dev)
+            ee = torch.tensor([float(e2e_evals)], dtype=torch.float64, device=red_dev)
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
             dist.all_reduce(ee, op=dist.ReduceOp.SUM)
             el, e2e_evals = te.item(), ee.item()
@@ -880,6 +920,7 @@ def main():
     fam = None
     if not args.no_roofline:
         S.smc_destroy(ctx)
+        sharded = None          # per-rank kernel times come from a plain context of J particles
         cfg_t = S.make_config(args.J, 1234 + rank, S.PREC_BF16, stream=stream, timing=1)
         ctx = S.smc_init(model, Xd, y_class=yd, cfg=cfg_t)
         S.smc_set_schedule(ctx, sched)
@@ -933,6 +974,11 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
                 "config": workload_config(args), "e2e": e2e, "gpu_launches": n1 - n0,
                 "clocks": clk, "roofline": roof, "families_ms": fam}
+        line["config"]["parallelism"] = (f"particles sharded {args.J} per rank over {world} ranks ({args.dist_backend}):"
+                                         f" global log-weight normalisation, SDA moments and resampling exchange"
+                                         if world > 1 else "one GPU")
+        if args.trace:
+            line["trace"] = timed_trace
         if world == 1 and not args.no_scale:
             line["scale_config"] = run_scale_config(args.scale_steps, max(3, args.warmup),
                                                     cpu=not args.no_cpu_baseline)

@@ -74,7 +74,7 @@ static __device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr, uint32_t lbo
     return d;
 }
 
-template <int NHALF, bool AMN, bool BMN, bool BF16OUT>
+template <int NHALF, bool AMN, bool BMN, bool BF16OUT, bool AUXST = false>
 struct GCfg {
     static constexpr int N1 = NHALF > 128 ? 128 : NHALF;
     static constexpr int N2 = NHALF - N1;
@@ -88,7 +88,13 @@ struct GCfg {
     static constexpr uint32_t ACC_COLS = 256;
     // BF16 outputs: per epilogue warp two [32 rows][32 cols] staging tiles
     static constexpr int STAGING = BF16OUT ? EPI_WARPS * 2 * 2048 : 0;
-    static constexpr int FIXED = 1024 /*align*/ + 256 /*barriers*/ + STAGING;
+    // the adjoint's activations: per epilogue warp its 32 rows x NHALF columns,
+    // rows AUXC 16-byte chunks apart (odd, so thread-per-row reads of a chunk
+    // hit distinct banks)
+    static constexpr int NPC = NHALF / 8;
+    static constexpr int AUXC = NPC + ((NPC & 1) ? 2 : 1);
+    static constexpr int AUX = AUXST ? EPI_WARPS * 32 * AUXC * 16 : 0;
+    static constexpr int FIXED = 1024 /*align*/ + 256 /*barriers*/ + STAGING + AUX;
     static constexpr int STAGES_FIT = (SMEM_LIMIT - FIXED) / STAGE_BYTES;
     static constexpr int STAGES = STAGES_FIT > 6 ? 6 : STAGES_FIT;
     static constexpr int SMEM = FIXED + STAGES * STAGE_BYTES;
@@ -98,7 +104,17 @@ struct GCfg {
     static_assert(STAGE_BYTES % 1024 == 0 && (N2 == 0 || (N1 * 128) % 1024 == 0), "swizzle atoms");
     static_assert(STAGES >= 2, "pipeline depth");
     static_assert(!BF16OUT || NHALF <= 128, "BF16 outputs: TMEM column = tile column");
+    static_assert(!AUXST || NHALF <= 128, "staged activations: one half of a tile per warp");
 };
+
+// 16-byte asynchronous copy global -> shared bypassing L1; src_bytes = 0 fills
+// zeros without reading.
+static __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(su32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+static __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+static __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 template <int ACT>
 __device__ __forceinline__ float act_fwd(float z) {
@@ -225,14 +241,16 @@ grouped_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                     const __grid_constant__ CUtensorMap tmO32, const __grid_constant__ CUtensorMap tmO8,
                     const GArgs g) {
     constexpr bool BF16OUT = EPI != EPI_F32;
-    using C = GCfg<NHALF, AMN, BMN, BF16OUT>;
+    constexpr bool AUXST = EPI == EPI_BF16_DACT;
+    using C = GCfg<NHALF, AMN, BMN, BF16OUT, AUXST>;
     constexpr int STAGES = C::STAGES;
     const int rank = (int)cluster_rank();
     const int cid = blockIdx.x / 2, ncl = gridDim.x / 2;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* staging = smem + STAGES * C::STAGE_BYTES;
-    uint64_t* full = (uint64_t*)(staging + C::STAGING);
+    uint8_t* aux_stage = staging + C::STAGING;
+    uint64_t* full = (uint64_t*)(aux_stage + C::AUX);
     uint64_t* empty = full + STAGES;
     uint64_t* tfull = empty + STAGES;
     uint64_t* tempty = tfull + 2;
@@ -352,10 +370,11 @@ grouped_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
         constexpr int NP = NHALF / 8;        // 8-column pieces of a half
         constexpr int NG = (NHALF + 31) / 32;
         constexpr int LAST_N8 = (NHALF - 32 * (NG - 1)) / 8;
-        // the adjoint's activations of a whole half are loaded before the
-        // accumulator wait (their latency hides behind the MMAs) when they fit
-        constexpr bool PREFETCH = EPI == EPI_BF16_DACT && NP <= 16;
+        // the adjoint's activations of this warp's 32 rows and half tile are
+        // copied to shared memory with coalesced 16-byte copies before the
+        // accumulator wait (their latency hides behind the MMAs)
         uint8_t* my_stage = staging + (BF16OUT ? ew * 2 * 2048 : 0);   // two [32][32] BF16 tiles of this warp
+        uint8_t* my_aux = aux_stage + (AUXST ? ew * 32 * C::AUXC * 16 : 0);
         int acc = 0, chunk_no = 0;
         uint32_t aph = 0;
         for (int64_t u = cid; u < g.units; u += ncl) {
@@ -365,22 +384,28 @@ grouped_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
             const int row = row0 + lane;
             const bool row_ok = row < g.M;
             const int c_begin = half * NHALF;
-            uint4 hv[PREFETCH ? NP : 1];
-#pragma unroll
-            for (int q = 0; q < (PREFETCH ? NP : 1); ++q) {
-                hv[q] = make_uint4(0u, 0u, 0u, 0u);
-                if (PREFETCH) {
-                    const int col = tn * 2 * NHALF + c_begin + 8 * q;
-                    if (row_ok && col < g.N)
-                        hv[q] = *reinterpret_cast<const uint4*>(g.aux + (int64_t)b * g.aux_bstride +
-                                                                (int64_t)row * g.aux_ld + col);
+            if (AUXST) {
+                // lane l copies pieces l, l + 32, ... of the [32 rows][NP pieces] block:
+                // consecutive lanes read consecutive 16-byte pieces of a row
+                for (int i = lane; i < 32 * NP; i += 32) {
+                    const int r = i / NP, q = i % NP;
+                    const int rg = row0 + r, col = tn * 2 * NHALF + c_begin + 8 * q;
+                    const bool in = rg < g.M && col < g.N;
+                    const __nv_bfloat16* src =
+                        in ? g.aux + (int64_t)b * g.aux_bstride + (int64_t)rg * g.aux_ld + col : g.aux;
+                    cp_async16(my_aux + (r * C::AUXC + q) * 16, src, in ? 16 : 0);
                 }
+                cp_async_commit();
             }
             if (!mbar_wait(tfull + acc, aph, abort_flag)) {
                 raise_abort(g, abort_flag, ERR_EPILOGUE);
                 break;
             }
             tc_fence_after();
+            if (AUXST) {
+                cp_async_wait0();
+                __syncwarp();
+            }
             const uint32_t tb = tbase + (uint32_t)acc * C::ACC_COLS + ((uint32_t)(wq * 32) << 16);
 #pragma unroll
             for (int gi = 0; gi < NG; ++gi) {
@@ -413,12 +438,7 @@ grouped_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                     pk[q] = make_uint4(0u, 0u, 0u, 0u);
                     if (q < n8) {
                         uint4 h = make_uint4(0u, 0u, 0u, 0u);
-                        if (EPI == EPI_BF16_DACT) {
-                            if (PREFETCH) h = hv[PREFETCH ? 4 * gi + q : 0];
-                            else if (row_ok && col0 + 8 * q < g.N)
-                                h = *reinterpret_cast<const uint4*>(g.aux + (int64_t)b * g.aux_bstride +
-                                                                    (int64_t)row * g.aux_ld + col0 + 8 * q);
-                        }
+                        if (AUXST) h = *reinterpret_cast<const uint4*>(my_aux + (lane * C::AUXC + 4 * gi + q) * 16);
                         pk[q] = bf16_piece<EPI, ACT>(g, b, col0 + 8 * q, r + 8 * q, h);
                     }
                 }
@@ -450,10 +470,11 @@ grouped_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                 ++chunk_no;
             }
             tc_fence_before();
-            __syncwarp();
+            __syncwarp();   // (also: every lane's reads of the staged activations are done)
             if (lane == 0) mbar_arrive_remote(mapa_shared(tempty + acc, 0));
             if (++acc == C::ACC) { acc = 0; aph ^= 1; }
         }
+        if (AUXST) cp_async_wait0();   // no copy of ours lands after the CTA exits
         if (BF16OUT && lane == 0) bulk_wait_all();   // outstanding output stores complete before the CTA exits
         __syncwarp();
     }
@@ -469,7 +490,7 @@ grouped_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
 // ------------------------------------------------------------- host side
 template <int NHALF, bool AMN, bool BMN, int EPI, int ACT>
 static int max_clusters_for(int num_sms) {
-    using C = GCfg<NHALF, AMN, BMN, EPI != EPI_F32>;
+    using C = GCfg<NHALF, AMN, BMN, EPI != EPI_F32, EPI == EPI_BF16_DACT>;
     static int cached = -1;
     if (cached < 0) {
         auto kern = grouped_pair_kernel<NHALF, AMN, BMN, EPI, ACT>;
@@ -512,7 +533,7 @@ static bool output_map(CUtensorMap* m, const GOperand& o, uint32_t cols) {
 template <int NHALF, bool AMN, bool BMN, int EPI, int ACT>
 static cudaError_t launch_t(const GOperand& A, const GOperand& B, const GOperand* O, GArgs g, cudaStream_t s,
                             int num_sms) {
-    using C = GCfg<NHALF, AMN, BMN, EPI != EPI_F32>;
+    using C = GCfg<NHALF, AMN, BMN, EPI != EPI_F32, EPI == EPI_BF16_DACT>;
     CUtensorMap ta, tb, to32, to8;
     if (!operand_map(&ta, A, AMN ? 64u : (uint32_t)BM)) return cudaErrorInvalidValue;
     if (!operand_map(&tb, B, BMN ? 64u : (uint32_t)NHALF)) return cudaErrorInvalidValue;

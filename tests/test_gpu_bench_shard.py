@@ -1,0 +1,48 @@
+"""bench.py's multi-rank path (the particle-sharded sampler of shard.py) against
+its one-rank path: two ranks of 8 particles each (on one GPU, collectives over
+gloo on host tensors: no kernel waits on another rank) must follow the same
+trajectory as one rank of 16 - the same global ESS after every timed step and
+the same resampling decisions and ancestors."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+COMMON = ["--n", "2048", "--steps", "6", "--warmup", "3", "--no-cpu-baseline", "--no-e2e", "--no-roofline",
+          "--no-tta", "--no-scale", "--no-cnn", "--trace"]
+
+
+def _line(cmd):
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=900,
+                       env=dict(os.environ, MASTER_ADDR="127.0.0.1"))
+    assert r.returncode == 0, r.stderr[-3000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    return json.loads(lines[0])
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_two_rank_bench_follows_the_one_rank_trajectory():
+    one = _line([sys.executable, "bench.py", "--J", "16"] + COMMON)
+    two = _line([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                 "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py", "--gpus", "2",
+                 "--J", "8", "--dist-backend", "gloo"] + COMMON)
+    assert two["n_gpus"] == 2 and two["scaling"] == "weak" and "sharded" in two["config"]["parallelism"]
+    assert len(one["trace"]) == len(two["trace"]) == 6
+    for (e1, d1, a1), (e2, d2, a2) in zip(one["trace"], two["trace"]):
+        assert d1 == d2 and a1 == a2
+        assert e2 == pytest.approx(e1, rel=1e-12)
+    # the workload is the same, so the evaluations per step are too
+    assert two["value"] > 0 and one["value"] > 0
