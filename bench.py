@@ -735,7 +735,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--J", type=int, default=J_DEFAULT)
-    ap.add_argument("--n", type=int, default=N_TRAIN)
+    ap.add_argument("--rows", "--n", dest="n", type=int, default=N_TRAIN, help="training rows (images)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-roofline", action="store_true")

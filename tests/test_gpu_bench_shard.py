@@ -1,8 +1,13 @@
 """bench.py's multi-rank path (the particle-sharded sampler of shard.py) against
 its one-rank path: two ranks of 8 particles each (on one GPU, collectives over
 gloo on host tensors: no kernel waits on another rank) must follow the same
-trajectory as one rank of 16 - the same global ESS after every timed step and
-the same resampling decisions and ancestors."""
+trajectory as one rank of 16: the same resampling decisions and ancestors
+after every timed step, and the same global ESS up to reduction order.  The
+BF16 first-layer kernel sums each particle's per-row log-likelihoods in partial
+slots whose grouping follows its grid, which depends on the particles per
+context, so log pi may differ in the last FP32 bits (about 1e-7 relative of
+values of order 1e3, i.e. E of a few 1e-4 nats); the normalisation then bounds
+|ESS / ESS_1 - 1| by e^{4E} - 1 (eqs. normalise, jeff), so 1e-3."""
 import json
 import os
 import socket
@@ -15,7 +20,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-COMMON = ["--n", "2048", "--steps", "6", "--warmup", "3", "--no-cpu-baseline", "--no-e2e", "--no-roofline",
+COMMON = ["--rows", "2048", "--steps", "6", "--warmup", "3", "--no-cpu-baseline", "--no-e2e", "--no-roofline",
           "--no-tta", "--no-scale", "--no-cnn", "--trace"]
 
 
@@ -43,6 +48,6 @@ def test_two_rank_bench_follows_the_one_rank_trajectory():
     assert len(one["trace"]) == len(two["trace"]) == 6
     for (e1, d1, a1), (e2, d2, a2) in zip(one["trace"], two["trace"]):
         assert d1 == d2 and a1 == a2
-        assert e2 == pytest.approx(e1, rel=1e-12)
+        assert e2 == pytest.approx(e1, rel=1e-3)
     # the workload is the same, so the evaluations per step are too
     assert two["value"] > 0 and one["value"] > 0
