@@ -156,7 +156,10 @@ struct smc_ctx {
         __nv_bfloat16 *I1 = nullptr, *Z1 = nullptr, *P1 = nullptr, *I2 = nullptr, *Z2 = nullptr, *P2 = nullptr;
         uint8_t *idx1 = nullptr, *idx2 = nullptr;
         __nv_bfloat16 *W1p = nullptr, *W2p = nullptr;
-        float *dW2T = nullptr, *zeros = nullptr, *dW1P = nullptr;
+        __nv_bfloat16 *dZ2c = nullptr;   // dZ2 channel-blocked on the pooled conv-1 grid (zero padded)
+        __nv_bfloat16 *W2t = nullptr;    // per-tap conv-2 weights as the data gradient's B operand
+        int64_t dz_rows = 0;             // rows of one dZ2c channel plane
+        float *dW2T = nullptr, *dW1P = nullptr;
     } cnn;
     __nv_bfloat16* H1 = nullptr;     // [chunk_pad][J*H]
     __nv_bfloat16* dZT = nullptr;    // [J*H][chunk_pad]
