@@ -11,7 +11,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsmc.so")
-SOURCES = ["api.cu", "k_smc.cu", "k_simt.cu", "k_tc.cu", "k_head.cu", "k_fused.cu", "k_learned.cu", "k_conv.cu", "k_grouped.cu", "k_deep.cu", "k_cnn.cu"]
+SOURCES = ["api.cu", "k_smc.cu", "k_simt.cu", "k_tc.cu", "k_head.cu", "k_fused.cu", "k_learned.cu", "k_conv.cu", "k_grouped.cu", "k_deep.cu", "k_cnn.cu", "k_cnn_conv2.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -152,14 +152,15 @@ struct smc_ctx {
     float* conv_part = nullptr;      // SIMT: per-slice partial weight gradients of the largest conv layer
     // BF16 engine workspace
     std::vector<__nv_bfloat16*> dact;  // deeper networks: activations of hidden layer l [J][chunk][H_l + 8]
-    struct CnnBuffers {              // BF16 CNN engine (k_cnn.cu), per chunk of images
-        __nv_bfloat16 *I1 = nullptr, *Z1 = nullptr, *P1 = nullptr, *I2 = nullptr, *Z2 = nullptr, *P2 = nullptr;
+    struct CnnBuffers {              // BF16 CNN engine (k_cnn.cu, k_cnn_conv2.cu), per chunk of images
+        __nv_bfloat16 *I1 = nullptr, *Z1 = nullptr, *P1 = nullptr, *Z2 = nullptr, *P2 = nullptr;
         uint8_t *idx1 = nullptr, *idx2 = nullptr;
-        __nv_bfloat16 *W1p = nullptr, *W2p = nullptr;
+        __nv_bfloat16 *W1p = nullptr;    // conv-1 filters of all particles [J C1][K1p]
+        __nv_bfloat16 *W2f = nullptr;    // per-tap conv-2 weights, the forward's B operand
+        __nv_bfloat16 *W2t = nullptr;    // per-tap conv-2 weights, the data gradient's B operand
         __nv_bfloat16 *dZ2c = nullptr;   // dZ2 channel-blocked on the pooled conv-1 grid (zero padded)
-        __nv_bfloat16 *W2t = nullptr;    // per-tap conv-2 weights as the data gradient's B operand
-        int64_t dz_rows = 0;             // rows of one dZ2c channel plane
-        float *dW2T = nullptr, *dW1P = nullptr;
+        int64_t p1_rows = 0, dz_rows = 0;   // rows of one P1 / dZ2c channel plane
+        float *dW2P = nullptr, *dW1P = nullptr;   // FP32 weight-gradient partials
     } cnn;
     __nv_bfloat16* H1 = nullptr;     // [chunk_pad][J*H]
     __nv_bfloat16* dZT = nullptr;    // [J*H][chunk_pad]
