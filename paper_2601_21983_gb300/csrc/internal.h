@@ -153,7 +153,7 @@ struct smc_ctx {
     // BF16 engine workspace
     std::vector<__nv_bfloat16*> dact;  // deeper networks: activations of hidden layer l [J][chunk][H_l + 8]
     struct CnnBuffers {              // BF16 CNN engine (k_cnn.cu, k_cnn_conv2.cu), per chunk of images
-        __nv_bfloat16 *I1 = nullptr, *Z1 = nullptr, *P1 = nullptr, *Z2 = nullptr, *P2 = nullptr;
+        __nv_bfloat16 *I1 = nullptr, *Z1 = nullptr, *P1 = nullptr, *Z2 = nullptr, *P2 = nullptr;   // Z1: dZ1
         uint8_t *idx1 = nullptr, *idx2 = nullptr;
         __nv_bfloat16 *W1p = nullptr;    // conv-1 filters of all particles [J C1][K1p]
         __nv_bfloat16 *W2f = nullptr;    // per-tap conv-2 weights, the forward's B operand

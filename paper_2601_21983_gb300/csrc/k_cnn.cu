@@ -8,9 +8,10 @@
 //   im2col1     I1 [B R1][K1p]: one row per conv-1 output position, rows ordered
 //               so each 2x2 pool window is four consecutive rows, columns
 //               (c, ky, kx), column K1 = 1 (the bias gradient's ones column)
-//   conv 1      Z1 = tanh(I1 W1^T + b1) [B R1][J C1]: ONE tcgen05 GEMM for all
-//               particles (the input rows are shared), N = J C1
-//   pool 1      P1 (8-channel planes on the pooled grid) and each window's argmax
+//   conv 1      tanh(I1 W1^T + b1): ONE tcgen05 GEMM for all particles (the
+//               input rows are shared), N = J C1, with pool 1 in its epilogue:
+//               P1 (8-channel planes on the pooled grid) and each window's
+//               argmax; the conv-1 activations themselves are never stored
 //   conv 2      Z2 = tanh(conv(P1, W2) + b2) on the same grid: implicit GEMM on
 //               tcgen05 (k_cnn_conv2.cu), no im2col array
 //   pool 2      P2 [J][B][F] in the dense layer's (c, h, w) order, argmax
@@ -89,29 +90,6 @@ __global__ void im2col1_kernel(const __nv_bfloat16* __restrict__ X, int64_t din,
     *reinterpret_cast<uint4*>(I1 + row * s.K1p + k0) = *reinterpret_cast<const uint4*>(v);
 }
 
-// 2x2 max pool of Z1 [nimg R1][J C1] into the P1 planes [J][C1 / 8][p1_rows][8]
-// and idx1 [J][B NW1][C1] (first maximum wins, window order (0,0), (0,1),
-// (1,0), (1,1)).
-__global__ void pool1_kernel(const __nv_bfloat16* __restrict__ Z1, int nimg, int B, int J, Shape s, int64_t p1_rows,
-                             __nv_bfloat16* __restrict__ P1, uint8_t* __restrict__ idx1) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int JC = J * s.C1;
-    if (t >= (int64_t)nimg * s.NW1 * JC) return;
-    const int jc = (int)(t % JC);
-    const int64_t p = t / JC;   // grid row img NW1 + w
-    const int img = (int)(p / s.NW1), w = (int)(p % s.NW1);
-    const int j = jc / s.C1, ch = jc % s.C1;
-    const __nv_bfloat16* z = Z1 + ((int64_t)img * s.R1 + 4 * w) * JC + jc;
-    float best = __bfloat162float(z[0]);
-    int bi = 0;
-    for (int d = 1; d < 4; ++d) {
-        const float v = __bfloat162float(z[(int64_t)d * JC]);
-        if (v > best) { best = v; bi = d; }
-    }
-    P1[((int64_t)(j * (s.C1 / 8) + ch / 8) * p1_rows + p) * 8 + ch % 8] = __float2bfloat16_rn(best);
-    idx1[((int64_t)j * B * s.NW1 + p) * s.C1 + ch] = (uint8_t)bi;
-}
-
 // Grid row of the conv-2 output (oy, ox) of image img.
 __host__ __device__ inline int64_t grid_row(const Shape& s, int img, int oy, int ox) {
     return (int64_t)img * s.NW1 + oy * s.WP1 + ox;
@@ -170,9 +148,10 @@ __global__ void pool2_bwd_kernel(const __nv_bfloat16* __restrict__ dP2, const ui
 }
 
 // Per-evaluation BF16 weight images: W1p [J C1][K1p] (zero padded) and two
-// per-tap images of W2 [J][tap][1 KB] in K-major 8 x 8 core matrices: W2f,
-// the forward's B operand (N = C2 outputs, K = C1 inputs: [C2 / 8][C1 / 8][8][8]),
-// and W2t, the data gradient's (N = C1, K = C2: [C1 / 8][C2 / 8][8][8]).
+// images of W2 as B operands of the implicit conv-2 kernels, in K-major 8 x 8
+// core matrices: W2f [J][tap][co / 8][ci / 8][8 co][8 ci] (the forward, one
+// MMA per tap: N = co, K = ci) and W2t [J][ky][(kx, ci) / 8][co / 8][8 ci]
+// [8 co] (the data gradient, one MMA pair per ky: N = (kx, ci), K = co).
 __global__ void pack_weights_kernel(const float* __restrict__ W1, const float* __restrict__ W2, int J, Shape s,
                                     __nv_bfloat16* __restrict__ W1p, __nv_bfloat16* __restrict__ W2f,
                                     __nv_bfloat16* __restrict__ W2t) {
@@ -186,22 +165,27 @@ __global__ void pack_weights_kernel(const float* __restrict__ W1, const float* _
     }
     const int64_t u = t - n1;
     const int taps = s.k2 * s.k2;
-    const int64_t n2 = (int64_t)J * s.C2 * s.K2;
+    const int64_t n2 = (int64_t)J * s.C2 * s.K2;   // = J taps C1 C2: 512 elements per tap
     if (u >= 2 * n2) return;
     const int64_t v = u < n2 ? u : u - n2;
-    const int e = (int)(v & 7), row = (int)((v >> 3) & 7);
-    const int64_t jt = v >> 9;
-    const int tp = (int)(jt % taps);
-    const int64_t j = jt / taps;
-    int co, ci;
-    if (u < n2) {   // W2f: bits 6 = input-channel group, 7..8 = output-channel group
-        ci = (int)((v >> 6) & 1) * 8 + e;
-        co = (int)((v >> 7) & 3) * 8 + row;
-    } else {        // W2t: bits 6..7 = output-channel group, 8 = input-channel group
-        co = (int)((v >> 6) & 3) * 8 + e;
-        ci = (int)((v >> 8) & 1) * 8 + row;
+    const int64_t j = v / (taps * 512);
+    const int rem = (int)(v % (taps * 512));
+    const int e = rem & 7, row = (rem >> 3) & 7;
+    int co, ci, ky, kx;
+    if (u < n2) {   // W2f: bit 6 = ci / 8, bits 7..8 = co / 8, then the tap
+        const int tp = rem >> 9;
+        ky = tp / s.k2;
+        kx = tp % s.k2;
+        co = ((rem >> 7) & 3) * 8 + row;
+        ci = ((rem >> 6) & 1) * 8 + e;
+    } else {        // W2t: bits 6..7 = co / 8, then groups (ky, kx, ci / 8)
+        const int g = rem >> 8;
+        ky = g / (2 * s.k2);
+        kx = (g % (2 * s.k2)) / 2;
+        ci = (g % 2) * 8 + row;
+        co = ((rem >> 6) & 3) * 8 + e;
     }
-    const float w = W2[(j * s.C2 + co) * s.K2 + (int64_t)ci * taps + tp];
+    const float w = W2[(j * s.C2 + co) * s.K2 + (int64_t)ci * taps + ky * s.k2 + kx];
     (u < n2 ? W2f : W2t)[v] = __float2bfloat16_rn(w);
 }
 
@@ -321,26 +305,23 @@ static cudaError_t cnn_forward(smc_ctx* c, const Shape& s, const __nv_bfloat16* 
     auto& b = c->cnn;
     SMC_LAUNCH(c, im2col1_kernel<<<blocks((int64_t)nimg * s.R1 * (s.K1p / 8)), 256, 0, c->stream>>>(
                       x, c->in_feat, nimg, s, b.I1));
-    // conv 1: one GEMM over all particles' filters
+    // conv 1 and pool 1: one GEMM over all particles' filters whose epilogue
+    // pools each window's four rows (only P1 and idx1 are written)
     {
         const int64_t M = (int64_t)nimg * s.R1;
         const GOperand A = op3(b.I1, 0, 0, 0, s.K1, M, 1, s.K1p, M * s.K1p);
         const GOperand W = op3(b.W1p, 0, 0, 0, s.K1, J * s.C1, 1, s.K1p, J * s.C1 * s.K1p);
-        const GOperand O = op3(b.Z1, 0, 0, 0, J * s.C1, M, 1, J * s.C1, M * J * s.C1);
         GArgs g{};
-        g.M = (int)M; g.N = (int)(J * s.C1); g.K = s.K1; g.batch = 1; g.epi = gk::EPI_BF16_ACT;
+        g.M = (int)M; g.N = (int)(J * s.C1); g.K = s.K1; g.batch = 1; g.epi = gk::EPI_BF16_POOL;
         g.bias = c->theta + c->segs[c->layers[0].seg_b].off;
+        g.pool_out = b.P1; g.pool_idx = b.idx1; g.pool_rows = b.p1_rows; g.pool_ch = s.C1;
         g.aug_col = -1; g.err = c->err_dev;
         fam_begin(c, F_FWD_GEMM);
-        cudaError_t e = grouped_gemm(A, W, &O, g, SMC_ACT_TANH, 104, c->stream, c->num_sms);
+        cudaError_t e = grouped_gemm(A, W, nullptr, g, SMC_ACT_TANH, 104, c->stream, c->num_sms);
         c->launches++;
         fam_end(c, F_FWD_GEMM);
         if (e != cudaSuccess) return e;
     }
-    fam_begin(c, F_SIMT_NET);
-    SMC_LAUNCH(c, pool1_kernel<<<blocks((int64_t)nimg * s.NW1 * J * s.C1), 256, 0, c->stream>>>(
-                      b.Z1, nimg, (int)B, (int)J, s, b.p1_rows, b.P1, b.idx1));
-    fam_end(c, F_SIMT_NET);
     // conv 2: implicit GEMM per particle over the pooled grid
     fam_begin(c, F_HIDDEN_GEMM);
     cudaError_t e2 = conv2_forward(c, s, nimg);

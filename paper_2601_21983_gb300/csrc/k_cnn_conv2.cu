@@ -9,8 +9,10 @@
 //   forward      Z2[p] = tanh(b2 + sum_t P1[p + s_t] W2_t^T): M = 128 grid rows,
 //                N = C2, K = C1 per tap (K-major A: rows 16 bytes apart, the two
 //                channel planes one K step apart), k2^2 MMAs per tile
-//   data grad    dP1[p] = sum_t dZ2[p - s_t] W2_t: M = 128, N = C1, K = C2 per
-//                tap (2 MMAs), then pool-1 backward in the epilogue
+//   data grad    dP1[p] = sum_t dZ2[p - s_t] W2_t, with kx folded into N:
+//                E[q][(kx, ci)] = sum_ky dZ2[q - ky WP1] W2_(ky, kx) (M = 128,
+//                N = 16 k2, K = C2: 2 k2 MMAs per tile), dP1[p] = sum_kx
+//                E[p - kx][kx] across lanes, then pool-1 backward
 //   weight grad  dW2_t = sum_p P1[p + s_t]^T dZ2[p], db2 = sum_p dZ2[p]:
 //                M = 128 rows = 16 consecutive shifts x 8 channels of one
 //                plane (MN-major A whose 8-row groups are 16 bytes apart, so
@@ -119,6 +121,10 @@ static __device__ void role_abort(volatile int* abort_flag, int* err, int code, 
 }
 
 // ------------------------------------------------------------------ forward
+// Z2[p] = tanh(b2 + sum_t P1[p + s_t] W2_t^T) for the 128 grid rows of a tile:
+// one MMA per tap (M = 128, N = C2, K = C1).  (Folding kx into N would cut the
+// MMAs' operand reads from shared memory, which bound this kernel, but the
+// cross-lane sum over kx it needs then bounds the epilogue harder.)
 struct FwdArgs {
     int S, k2, WP1, shift_max, taps;
     int64_t T, units, nvalid, rows_per_particle;   // rows_per_particle: B NW1 (Z2's per-particle block)
@@ -262,12 +268,20 @@ __global__ void __launch_bounds__(192, 4) conv2_fwd_kernel(const __grid_constant
     }
 }
 
+constexpr int kOut = kTile - 4;   // outputs per tile of the data gradient (k2 <= 5)
+constexpr int kEpiGroups = 2;     // its epilogue warp groups, one per TMEM accumulator
+
 // ------------------------------------------------------------ data gradient
+// E[q][(kx, ci)] = sum_ky sum_co dZ2[q - ky WP1][co] W2[co][ci][ky][kx] for the
+// 128 grid rows q = r0 - 4 .. r0 + 123 of a tile (2 k2 MMAs, N = 16 k2), then
+// dP1[p][ci] = sum_kx E[p - kx][(kx, ci)] for p = r0 .. r0 + 123: row p - kx
+// is kx lanes back (a warp shuffle), or in the previous warp's last four rows,
+// published in shared memory first; pool-1 backward follows.
 struct DgArgs {
-    int S, k2, WP1, shift_max, taps, R1, JC;
+    int S, k2, WP1, R1, JC;
     int64_t T, units, nvalid, rows_per_particle, p1_rows;
     int NW1;
-    const __nv_bfloat16* W;   // [J][taps][kTapB bytes]: [C1 / 8][C2 / 8][8][8] per tap
+    const __nv_bfloat16* W;   // [J][ky][(kx, ci) / 8][co / 8][8][8] (K-major per ky)
     const __nv_bfloat16* P1;
     const uint8_t* idx1;
     __nv_bfloat16* Z1;        // dZ1 out: [B R1][J C1]
@@ -279,9 +293,9 @@ struct DgArgs {
 struct DgAux {
     uint4 p0, p1, bi;
 };
-static __device__ __forceinline__ DgAux dg_aux(const DgArgs& a, int j, int64_t p) {
+static __device__ __forceinline__ DgAux dg_aux(const DgArgs& a, int j, int64_t p, bool valid) {
     DgAux x;
-    if (p < a.nvalid) {
+    if (valid && p < a.nvalid) {
         x.p0 = *reinterpret_cast<const uint4*>(a.P1 + ((int64_t)(2 * j) * a.p1_rows + p) * 8);
         x.p1 = *reinterpret_cast<const uint4*>(a.P1 + ((int64_t)(2 * j + 1) * a.p1_rows + p) * 8);
         x.bi = *reinterpret_cast<const uint4*>(a.idx1 + ((int64_t)j * a.rows_per_particle + p) * 16);
@@ -291,35 +305,41 @@ static __device__ __forceinline__ DgAux dg_aux(const DgArgs& a, int j, int64_t p
     return x;
 }
 
-__global__ void __launch_bounds__(192, 3) conv2_dgrad_kernel(const __grid_constant__ CUtensorMap tmD, const DgArgs a) {
+__global__ void __launch_bounds__(320, 2) conv2_dgrad_kernel(const __grid_constant__ CUtensorMap tmD, const DgArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = align128(smem_raw);
+    const int ncols = 16 * a.k2;                      // accumulator columns (kx, ci)
+    const uint32_t wky = (uint32_t)a.k2 * 1024u;      // bytes of one ky's B operand
     uint8_t* wbuf = smem;
-    uint8_t* stages = wbuf + a.taps * kTapB;
-    uint64_t* full = (uint64_t*)(stages + kDgStages * 4 * kPlane);
+    uint8_t* stages = wbuf + a.k2 * wky;
+    float* xbuf = (float*)(stages + kDgStages * 4 * kPlane);   // [group][2][warp][4 rows][4 kx][16]
+    uint64_t* full = (uint64_t*)(xbuf + kEpiGroups * 2 * 4 * 256);
     uint64_t* empty = full + kDgStages;
     uint64_t* tfull = empty + kDgStages;
     uint64_t* tempty = tfull + 2;
     uint64_t* wfull = tempty + 2;
     uint64_t* wempty = wfull + 1;
     uint64_t* drain = wempty + 1;
-    uint32_t* tslot = (uint32_t*)(drain + 1);
+    uint64_t* xfull = drain + 1;
+    uint32_t* tslot = (uint32_t*)(xfull + 2 * kEpiGroups);
     volatile int* abort_flag = (volatile int*)(tslot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int q = 0; q < kDgStages; ++q) { mbar_init(full + q, 1); mbar_init(empty + q, 1); }
         for (int q = 0; q < 2; ++q) { mbar_init(tfull + q, 1); mbar_init(tempty + q, 4); }
         mbar_init(wfull, 1); mbar_init(wempty, 1); mbar_init(drain, 1);
+        for (int q = 0; q < 2 * kEpiGroups; ++q) mbar_init(xfull + q, 4);
         *abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == 1) tmem_alloc(tslot, 32);
+    if (warp == 1) tmem_alloc(tslot, 256);   // two accumulators of 16 k2 <= 80 columns, 128 apart
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tslot;
-    const uint32_t win_bytes = 4u * (uint32_t)(kTile + a.shift_max) * 16u;
-    const uint32_t w_bytes = (uint32_t)a.taps * kTapB;
+    const int shift_rows = (a.k2 - 1) * a.WP1;
+    const uint32_t win_bytes = 4u * (uint32_t)(kTile + shift_rows) * 16u;
+    const uint32_t w_bytes = (uint32_t)a.k2 * wky;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -332,14 +352,14 @@ __global__ void __launch_bounds__(192, 3) conv2_dgrad_kernel(const __grid_consta
                 if (it.fresh) {
                     if (!mbar_wait(wempty, wph ^ 1, abort_flag)) { ok = false; break; }
                     mbar_expect_tx(wfull, w_bytes);
-                    bulk_load(wbuf, a.W + (int64_t)it.j * a.taps * (kTapB / 2), w_bytes, wfull);
+                    bulk_load(wbuf, a.W + (int64_t)it.j * (w_bytes / 2), w_bytes, wfull);
                     wph ^= 1;
                 }
                 if (!mbar_wait(empty + stage, ph ^ 1, abort_flag)) { ok = false; break; }
                 mbar_expect_tx(full + stage, win_bytes);
                 uint8_t* st = stages + stage * 4 * kPlane;
-                // rows p - shift_max .. p + 127 of the tile (dZ2c rows start kDzMarg >= shift_max late)
-                const int y = kDzMarg + (int)(it.t * kTile) - a.shift_max;
+                // dZ2 rows r0 - 4 - shift_rows .. r0 + 123 (dZ2c rows start kDzMarg > 4 + shift_rows late)
+                const int y = kDzMarg + (int)(it.t * kOut) - (a.k2 - 1) - shift_rows;
                 for (int cb = 0; cb < 4; ++cb) tma_load_3d(st + cb * kPlane, &tmD, 0, y, 4 * it.j + cb, full + stage);
                 if (++stage == kDgStages) { stage = 0; ph ^= 1; }
             }
@@ -348,7 +368,7 @@ __global__ void __launch_bounds__(192, 3) conv2_dgrad_kernel(const __grid_consta
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t ID = idesc_bf16(128, 16);
+            const uint32_t ID = idesc_bf16(128, ncols);
             TileIter it;
             it.init();
             int stage = 0, acc = 0, units_seen = 0;
@@ -365,14 +385,14 @@ __global__ void __launch_bounds__(192, 3) conv2_dgrad_kernel(const __grid_consta
                 tc_fence_after();
                 const uint32_t sa = su32(stages + stage * 4 * kPlane);
                 const uint32_t sw = su32(wbuf);
-                const uint32_t dt = tbase + (uint32_t)acc * 16;
-                for (int t = 0; t < a.taps; ++t) {
-                    const int row_off = a.shift_max - ((t / a.k2) * a.WP1 + t % a.k2);   // dZ2 at p - s_t
+                const uint32_t dt = tbase + (uint32_t)acc * 128;
+                for (int ky = 0; ky < a.k2; ++ky) {
+                    const int row_off = shift_rows - ky * a.WP1;   // E row m reads dZ2 window row m + row_off
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
                         const uint64_t ad = sdesc_ns(sa + 2 * q * kPlane + row_off * 16, kPlane, 128);
-                        const uint64_t bd = sdesc_ns(sw + t * kTapB + 2 * q * 128, 128, 512);
-                        umma_bf16(dt, ad, bd, ID, (t > 0 || q > 0) ? 1u : 0u);
+                        const uint64_t bd = sdesc_ns(sw + ky * wky + q * 256, 128, 512);
+                        umma_bf16(dt, ad, bd, ID, (ky > 0 || q > 0) ? 1u : 0u);
                     }
                 }
                 umma_commit(empty + stage);
@@ -386,35 +406,81 @@ __global__ void __launch_bounds__(192, 3) conv2_dgrad_kernel(const __grid_consta
         }
         __syncwarp();
     } else {
+        const int grp = (warp - 2) >> 2;
         const int wq = warp & 3;
-        int acc = 0;
-        uint32_t aph = 0;
+        const int m = wq * 32 + lane;   // E row r0 - 4 + m; output row p = r0 - 4 + m for m >= 4
         TileIter it;
         it.init();
-        bool have = it.next(a.units, a.S, a.T);
-        DgAux cur = have ? dg_aux(a, it.j, it.t * kTile + wq * 32 + lane) : DgAux{};
+        int local = 0, mine = 0;
+        uint32_t aph = 0;
+        // this group's tiles: every other tile of the CTA's sequence
+        auto next_mine = [&](TileIter& t) -> bool {
+            while (t.next(a.units, a.S, a.T))
+                if ((local++ & 1) == grp) return true;
+            return false;
+        };
+        bool have = next_mine(it);
+        DgAux cur = have ? dg_aux(a, it.j, it.t * kOut - 4 + m, m >= 4) : DgAux{};
         while (have) {
             // the next tile's loads go out before this tile's accumulator is drained
             TileIter nx = it;
-            const bool hn = nx.next(a.units, a.S, a.T);
-            const DgAux nxt = hn ? dg_aux(a, nx.j, nx.t * kTile + wq * 32 + lane) : DgAux{};
-            if (!mbar_wait(tfull + acc, aph, abort_flag)) {
+            const bool hn = next_mine(nx);
+            const DgAux nxt = hn ? dg_aux(a, nx.j, nx.t * kOut - 4 + m, m >= 4) : DgAux{};
+            if (!mbar_wait(tfull + grp, aph, abort_flag)) {
                 role_abort(abort_flag, a.err, ERR_DG, false);
                 break;
             }
+            aph ^= 1;
             tc_fence_after();
+            const uint32_t tb = tbase + (uint32_t)grp * 128 + ((uint32_t)(wq * 32) << 16);
+            const int buf = mine & 1;
+            float* xb = xbuf + (grp * 2 + buf) * 1024;   // [warp][4 rows][4 kx][16]
             uint32_t r[16];
+            // the last four rows of the warp, for the next warp's first four outputs
+            if (wq < 3) {
+                for (int kx = 1; kx < a.k2; ++kx) {
+                    __syncwarp();
+                    TMEM_LD8(tb + (uint32_t)(kx * 16), r);
+                    TMEM_LD8(tb + (uint32_t)(kx * 16 + 8), (r + 8));
+                    tmem_ld_wait();
+                    if (lane >= 28) {
+                        float4* d = reinterpret_cast<float4*>(xb + ((wq * 4 + lane - 28) * 4 + kx - 1) * 16);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            d[c] = make_float4(__uint_as_float(r[4 * c]), __uint_as_float(r[4 * c + 1]),
+                                               __uint_as_float(r[4 * c + 2]), __uint_as_float(r[4 * c + 3]));
+                    }
+                }
+            }
             __syncwarp();
-            const uint32_t tb = tbase + (uint32_t)acc * 16 + ((uint32_t)(wq * 32) << 16);
-            TMEM_LD8(tb, r);
-            TMEM_LD8(tb + 8, (r + 8));
-            tmem_ld_wait();
+            if (lane == 0) mbar_arrive(xfull + grp * 2 + buf);
+            if (!mbar_wait(xfull + grp * 2 + buf, (mine >> 1) & 1, abort_flag)) {
+                role_abort(abort_flag, a.err, ERR_DG, false);
+                break;
+            }
+            ++mine;
+            float acc[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[c] = 0.0f;
+            for (int kx = 0; kx < a.k2; ++kx) {
+                __syncwarp();
+                TMEM_LD8(tb + (uint32_t)(kx * 16), r);
+                TMEM_LD8(tb + (uint32_t)(kx * 16 + 8), (r + 8));
+                tmem_ld_wait();
+                const bool own = lane >= kx;
+                const bool far = !own && wq > 0;   // row in the previous warp's published rows
+                const float* xs = xb + (((wq - 1) * 4 + (far ? lane - kx + 4 : 0)) * 4 + (far ? kx - 1 : 0)) * 16;
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const float v = __shfl_up_sync(0xffffffffu, __uint_as_float(r[c]), kx);
+                    acc[c] += own ? v : (far ? xs[c] : 0.0f);
+                }
+            }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(tempty + acc);
-            if (++acc == 2) { acc = 0; aph ^= 1; }
-            const int64_t p = it.t * kTile + wq * 32 + lane;
-            if (p < a.nvalid) {
+            if (lane == 0) mbar_arrive(tempty + grp);
+            const int64_t p = it.t * kOut - 4 + m;
+            if (m >= 4 && p < a.nvalid) {
                 const int img = (int)(p / a.NW1), w = (int)(p % a.NW1);
                 const __nv_bfloat16* pv = reinterpret_cast<const __nv_bfloat16*>(&cur.p0);
                 const __nv_bfloat16* pw = reinterpret_cast<const __nv_bfloat16*>(&cur.p1);
@@ -423,7 +489,7 @@ __global__ void __launch_bounds__(192, 3) conv2_dgrad_kernel(const __grid_consta
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
                     const float h = __bfloat162float(c < 8 ? pv[c] : pw[c - 8]);
-                    const float v = __uint_as_float(r[c]) * (1.0f - h * h);
+                    const float v = acc[c] * (1.0f - h * h);
 #pragma unroll
                     for (int d = 0; d < 4; ++d) out[d][c] = __float2bfloat16_rn(d == bi[c] ? v : 0.0f);
                 }
@@ -444,7 +510,7 @@ __global__ void __launch_bounds__(192, 3) conv2_dgrad_kernel(const __grid_consta
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tbase, 32);
+        tmem_dealloc(tbase, 256);
     }
 }
 
@@ -628,17 +694,15 @@ int64_t conv2_wgrad_partial_elems(const smc_ctx* c, const Shape& s) {
     return (int64_t)c->J * conv2_splits(c->J, c->num_sms) * (s.K2 + 1) * s.C2;
 }
 
-static int shift_max_of(const Shape& s) { return (s.k2 - 1) * s.WP1 + (s.k2 - 1); }
-
 // Work split of a launch with at most `grid_max` CTAs over J particles' T tiles.
 struct Plan {
     int S;
     int64_t T, units;
     int grid;
 };
-static Plan plan(const smc_ctx* c, int nimg, const Shape& s, int grid_max) {
+static Plan plan(const smc_ctx* c, int nimg, const Shape& s, int grid_max, int rows_per_tile) {
     Plan p;
-    p.T = ((int64_t)nimg * s.NW1 + kTile - 1) / kTile;
+    p.T = ((int64_t)nimg * s.NW1 + rows_per_tile - 1) / rows_per_tile;
     p.S = (int)std::min<int64_t>(conv2_splits(c->J, grid_max), p.T);
     p.units = (int64_t)c->J * p.S;
     p.grid = (int)std::min<int64_t>(p.units, grid_max);
@@ -653,10 +717,10 @@ static bool planes_map(CUtensorMap* m, const void* base, int64_t rows_extent, in
 
 cudaError_t conv2_forward(smc_ctx* c, const Shape& s, int nimg) {
     const auto& b = c->cnn;
-    const int shift = shift_max_of(s);
+    const int shift = (s.k2 - 1) * s.WP1 + (s.k2 - 1);
     CUtensorMap tm;
     if (!planes_map(&tm, b.P1, b.p1_rows, b.p1_rows, 2 * (int64_t)c->J, kTile + shift)) return cudaErrorInvalidValue;
-    const Plan pl = plan(c, nimg, s, 4 * c->num_sms);
+    const Plan pl = plan(c, nimg, s, 4 * c->num_sms, kTile);
     FwdArgs a{};
     a.S = pl.S; a.k2 = s.k2; a.WP1 = s.WP1; a.shift_max = shift; a.taps = s.k2 * s.k2;
     a.T = pl.T; a.units = pl.units; a.nvalid = (int64_t)nimg * s.NW1; a.rows_per_particle = b.p1_rows;
@@ -671,20 +735,21 @@ cudaError_t conv2_forward(smc_ctx* c, const Shape& s, int nimg) {
 
 cudaError_t conv2_dgrad(smc_ctx* c, const Shape& s, int nimg) {
     const auto& b = c->cnn;
-    const int shift = shift_max_of(s);
+    const int shift_rows = (s.k2 - 1) * s.WP1;
     CUtensorMap tm;
-    if (!planes_map(&tm, b.dZ2c, b.dz_rows, b.dz_rows, 4 * (int64_t)c->J, kTile + shift)) return cudaErrorInvalidValue;
-    const Plan pl = plan(c, nimg, s, 3 * c->num_sms);
+    if (!planes_map(&tm, b.dZ2c, b.dz_rows, b.dz_rows, 4 * (int64_t)c->J, kTile + shift_rows))
+        return cudaErrorInvalidValue;
+    const Plan pl = plan(c, nimg, s, 2 * c->num_sms, kOut);
     DgArgs a{};
-    a.S = pl.S; a.k2 = s.k2; a.WP1 = s.WP1; a.shift_max = shift; a.taps = s.k2 * s.k2; a.R1 = s.R1;
-    a.JC = c->J * s.C1; a.NW1 = s.NW1;
+    a.S = pl.S; a.k2 = s.k2; a.WP1 = s.WP1; a.R1 = s.R1; a.JC = c->J * s.C1; a.NW1 = s.NW1;
     a.T = pl.T; a.units = pl.units; a.nvalid = (int64_t)nimg * s.NW1; a.rows_per_particle = b.p1_rows;
     a.p1_rows = b.p1_rows;
     a.W = b.W2t; a.P1 = b.P1; a.idx1 = b.idx1; a.Z1 = b.Z1; a.err = c->err_dev;
-    const size_t smem = 128 + (size_t)a.taps * kTapB + (size_t)kDgStages * 4 * kPlane + 256;
+    const size_t smem = 128 + (size_t)s.k2 * s.k2 * 1024 + (size_t)kDgStages * 4 * kPlane +
+                        (size_t)kEpiGroups * 2 * 4 * 256 * 4 + 256;
     cudaError_t e = cudaFuncSetAttribute(conv2_dgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    conv2_dgrad_kernel<<<pl.grid, 192, smem, c->stream>>>(tm, a);
+    conv2_dgrad_kernel<<<pl.grid, 320, smem, c->stream>>>(tm, a);
     c->launches++;
     return cudaGetLastError();
 }
@@ -699,7 +764,7 @@ cudaError_t conv2_wgrad(smc_ctx* c, const Shape& s, int nimg, int accumulate) {
     if (!planes_map(&tmP, b.P1, b.p1_rows, b.p1_rows, 2 * (int64_t)c->J, kPlane / 16) ||
         !planes_map(&tmZ, b.dZ2c, kDzMarg + nvalid, b.dz_rows, 4 * (int64_t)c->J, kTile))
         return cudaErrorInvalidValue;
-    const Plan pl = plan(c, nimg, s, c->num_sms);
+    const Plan pl = plan(c, nimg, s, c->num_sms, kTile);
     WgArgs a{};
     a.S = pl.S; a.k2 = s.k2; a.WP1 = s.WP1; a.K2 = s.K2;
     a.T = pl.T; a.units = pl.units; a.part = b.dW2P; a.err = c->err_dev;

@@ -33,7 +33,12 @@
 //                 the bias gradient);
 //   EPI_BF16_ACT  BF16 act(acc + bias[b][n]) (a forward layer);
 //   EPI_BF16_DACT BF16 acc * act'(aux) with aux the stored activation at the
-//                 same position (dZ of a hidden layer, act' from its output).
+//                 same position (dZ of a hidden layer, act' from its output);
+//   EPI_BF16_POOL four consecutive rows (one 2x2 pooling window) reduced to
+//                 their maximum and its index by warp shuffles, then BF16
+//                 act(max + bias); only the pooled values (8-column planes)
+//                 and the argmaxes are stored (a convolution layer followed
+//                 by max pooling, rows ordered window by window).
 // The BF16 epilogues stage each warp's 32 rows x 32 (or, at the end of a
 // half, 8) columns in shared memory and write them with TMA bulk-tensor
 // stores: a warp's thread-per-row registers would otherwise scatter every
@@ -235,12 +240,72 @@ __device__ __forceinline__ void store_box(const CUtensorMap* tm, int perm, const
     else tma_store_3d(tm, src, col, b, row);
 }
 
+// Epilogues that stage their BF16 output tiles for TMA stores.
+__host__ __device__ constexpr bool staged_out(int epi) { return epi == EPI_BF16_ACT || epi == EPI_BF16_DACT; }
+
+// EPI_BF16_POOL on one 32-column group: lanes 4w' .. 4w' + 3 of a warp hold the
+// four rows of pooling window w' (r: this lane's 32 FP32 accumulators, n8 of
+// its four 8-column pieces in use).  act is increasing and one bias is shared
+// by a column's four rows, so the window's maximum is taken on the
+// accumulators (a butterfly over the four lanes) and its index is the first
+// row that attains it; lane 4w' + q then finishes piece q alone: bias, act,
+// BF16, one 16-byte store into the piece's plane and 8 index bytes.
+template <int ACT>
+__device__ __forceinline__ void pool_group(const GArgs& g, int b, int row0, int col0, int n8, const uint32_t* r) {
+    const int lane = threadIdx.x & 31, d = lane & 3;
+    float mx[32];
+    uint32_t mask = 0;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        const float own = c < 8 * n8 ? __uint_as_float(r[c]) : 0.0f;   // pieces past n8 were not loaded
+        float v = own;
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 1));
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 2));
+        mx[c] = v;
+        mask |= (own == v ? 1u : 0u) << c;
+    }
+    uint32_t mk[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) mk[e] = __shfl_sync(0xffffffffu, mask, (lane & ~3) + e);
+    const int win_row = row0 + (lane & ~3);   // first row of this lane's window
+    const int col = col0 + 8 * d;
+    if (d >= n8 || win_row >= g.M || col >= g.N) return;
+    float v8[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v8[e] = mx[e];
+#pragma unroll
+    for (int q = 1; q < 4; ++q)
+        if (d == q) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v8[e] = mx[8 * q + e];
+        }
+    const float* bp = g.bias + (int64_t)b * g.bias_bstride + col;
+    const float4 b0 = *reinterpret_cast<const float4*>(bp);
+    const float4 b1 = *reinterpret_cast<const float4*>(bp + 4);
+    const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    __align__(16) __nv_bfloat16 best[8];
+    __align__(8) uint8_t bi[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int bit = 8 * d + e;
+        const int first = ((mk[0] >> bit) & 1u) ? 0 : ((mk[1] >> bit) & 1u) ? 1 : ((mk[2] >> bit) & 1u) ? 2 : 3;
+        best[e] = __float2bfloat16_rn(act_fwd<ACT>(v8[e] + bb[e]));
+        bi[e] = (uint8_t)first;
+    }
+    const int64_t win = win_row >> 2;
+    *reinterpret_cast<uint4*>(g.pool_out + ((int64_t)(col >> 3) * g.pool_rows + win) * 8) =
+        *reinterpret_cast<const uint4*>(best);
+    *reinterpret_cast<uint2*>(g.pool_idx + ((int64_t)(col / g.pool_ch) * g.pool_rows + win) * g.pool_ch +
+                              col % g.pool_ch) = *reinterpret_cast<const uint2*>(bi);
+}
+
 template <int NHALF, bool AMN, bool BMN, int EPI, int ACT>
 __global__ void __launch_bounds__(THREADS, 1)
 grouped_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const __grid_constant__ CUtensorMap tmO32, const __grid_constant__ CUtensorMap tmO8,
                     const GArgs g) {
-    constexpr bool BF16OUT = EPI != EPI_F32;
+    constexpr bool BF16OUT = staged_out(EPI);
+    constexpr bool POOL = EPI == EPI_BF16_POOL;
     constexpr bool AUXST = EPI == EPI_BF16_DACT;
     using C = GCfg<NHALF, AMN, BMN, BF16OUT, AUXST>;
     constexpr int STAGES = C::STAGES;
@@ -421,6 +486,10 @@ grouped_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                     }
                 }
                 tmem_ld_wait();
+                if (POOL) {
+                    pool_group<ACT>(g, b, row0, tn * 2 * NHALF + c0, n8, r);
+                    continue;
+                }
                 if (!BF16OUT) {
                     if (row_ok) {
 #pragma unroll
@@ -490,7 +559,7 @@ grouped_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
 // ------------------------------------------------------------- host side
 template <int NHALF, bool AMN, bool BMN, int EPI, int ACT>
 static int max_clusters_for(int num_sms) {
-    using C = GCfg<NHALF, AMN, BMN, EPI != EPI_F32, EPI == EPI_BF16_DACT>;
+    using C = GCfg<NHALF, AMN, BMN, staged_out(EPI), EPI == EPI_BF16_DACT>;
     static int cached = -1;
     if (cached < 0) {
         auto kern = grouped_pair_kernel<NHALF, AMN, BMN, EPI, ACT>;
@@ -533,11 +602,11 @@ static bool output_map(CUtensorMap* m, const GOperand& o, uint32_t cols) {
 template <int NHALF, bool AMN, bool BMN, int EPI, int ACT>
 static cudaError_t launch_t(const GOperand& A, const GOperand& B, const GOperand* O, GArgs g, cudaStream_t s,
                             int num_sms) {
-    using C = GCfg<NHALF, AMN, BMN, EPI != EPI_F32, EPI == EPI_BF16_DACT>;
+    using C = GCfg<NHALF, AMN, BMN, staged_out(EPI), EPI == EPI_BF16_DACT>;
     CUtensorMap ta, tb, to32, to8;
     if (!operand_map(&ta, A, AMN ? 64u : (uint32_t)BM)) return cudaErrorInvalidValue;
     if (!operand_map(&tb, B, BMN ? 64u : (uint32_t)NHALF)) return cudaErrorInvalidValue;
-    if (EPI != EPI_F32) {
+    if (staged_out(EPI)) {
         constexpr uint32_t tail = (uint32_t)(NHALF % 32 == 0 ? 32 : NHALF % 32);
         if (O == nullptr || !output_map(&to32, *O, 32) || !output_map(&to8, *O, tail)) return cudaErrorInvalidValue;
         g.out_perm = O->perm;
@@ -603,7 +672,16 @@ cudaError_t grouped_gemm(const gk::GOperand& A, const gk::GOperand& B, const gk:
         return cudaErrorInvalidValue;
     }
     // the BF16 epilogues follow a K-major A (rows of a layer), N a multiple of 8
-    if (A.mn_major || (nhalf != 104 && nhalf != 16) || (g.N % 8 != 0) || O == nullptr) return cudaErrorInvalidValue;
+    if (A.mn_major || (nhalf != 104 && nhalf != 16) || (g.N % 8 != 0)) return cudaErrorInvalidValue;
+    if (g.epi == EPI_BF16_POOL) {
+        if (nhalf != 104 || B.mn_major || g.batch != 1 || g.M % 4 != 0 || g.pool_ch % 8 != 0 ||
+            g.pool_out == nullptr || g.pool_idx == nullptr)
+            return cudaErrorInvalidValue;
+        if (act == SMC_ACT_RELU) return launch_t<104, false, false, EPI_BF16_POOL, SMC_ACT_RELU>(A, B, O, g, s, num_sms);
+        if (act == SMC_ACT_TANH) return launch_t<104, false, false, EPI_BF16_POOL, SMC_ACT_TANH>(A, B, O, g, s, num_sms);
+        return launch_t<104, false, false, EPI_BF16_POOL, SMC_ACT_IDENTITY>(A, B, O, g, s, num_sms);
+    }
+    if (O == nullptr) return cudaErrorInvalidValue;
     if (nhalf == 16 && B.mn_major) return cudaErrorInvalidValue;
     auto run = [&](auto epi_tag, auto act_tag) -> cudaError_t {
         constexpr int E = decltype(epi_tag)::value, AC = decltype(act_tag)::value;

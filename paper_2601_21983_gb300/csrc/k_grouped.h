@@ -8,7 +8,7 @@
 namespace smc {
 namespace gk {
 
-enum { EPI_F32 = 0, EPI_BF16_ACT = 1, EPI_BF16_DACT = 2 };
+enum { EPI_F32 = 0, EPI_BF16_ACT = 1, EPI_BF16_DACT = 2, EPI_BF16_POOL = 3 };
 
 // One BF16 operand as a 3-D array: `inner` contiguous elements (k for a K-major
 // operand, m or n for an MN-major one), `outer` rows `outer_pitch` bytes apart
@@ -39,6 +39,12 @@ struct GArgs {
     float* aug_out;              // EPI_F32: column aug_col goes to aug_out[b aug_bstride + m];
     int aug_col;                 //          columns past it are dropped (-1: none)
     int64_t aug_bstride;
+    __nv_bfloat16* pool_out;     // EPI_BF16_POOL: the 2x2 max of rows 4w .. 4w + 3 of column n at
+                                 //   pool_out[((n / 8) pool_rows + w) 8 + n % 8] (8-channel planes)
+    uint8_t* pool_idx;           //   and its argmax (0..3, first maximum) at
+                                 //   pool_idx[((n / pool_ch) pool_rows + w) pool_ch + n % pool_ch]
+    int64_t pool_rows;
+    int pool_ch;                 //   columns per batch of planes (a multiple of 8)
     int* err;                    // device error flag (timeouts)
     // filled by the launcher
     int a_perm, b_perm, a_batched, b_batched, out_perm;
@@ -57,7 +63,9 @@ struct GArgs {
 // the BF16 epilogues.
 // O: the BF16 epilogues' output as a 3-D array (inner = N columns, outer =
 // M rows, batch), written by TMA stores; NULL for EPI_F32 (out / ldo /
-// out_bstride of GArgs).
+// out_bstride of GArgs) and for EPI_BF16_POOL (nhalf 104, one batch: the
+// activations are pooled in the epilogue and only the pooled planes and the
+// argmaxes are written).
 cudaError_t grouped_gemm(const gk::GOperand& A, const gk::GOperand& B, const gk::GOperand* O, const gk::GArgs& g,
                          int act, int nhalf, cudaStream_t s, int num_sms);
 
