@@ -291,7 +291,7 @@ def cnn_workload(J, n):
                          f"(the end of SDA's annealing), HMC S={S_LF}, h={STEP_H}, BF16 tcgen05 convolutions with "
                          f"FP32 accumulation"),
             "particles": J, "rows": n, "schedule": "fb", "leapfrog_steps": S_LF,
-            "l2": "no flush: per-step working set (im2col and activation arrays of ~16 GB per chunk) above the L2"}
+            "l2": "no flush: per-step working set (pooled maps, conv-2 outputs, dZ2 and dZ1 of ~15 GB per chunk of 2048 images) far above the L2"}
 
 
 def _section(kind, steps, warmup, J, n, e2e=True, roofline=True, cpu=True):
@@ -393,16 +393,21 @@ def _section(kind, steps, warmup, J, n, e2e=True, roofline=True, cpu=True):
                     # the head reads the last hidden activations and writes dZ over them (BF16)
                     "head": ("hbm", 2.0 * units * H * 2.0)}
         else:
-            # conv 1 (784 positions x 16 x 75), conv 2 (100 x 32 x 400), their weight
-            # gradients (with the bias column) and the conv-2 data gradient
+            # conv 1 (784 positions x 16 x 75, pool 1 in its epilogue), conv 2 (100 x 32
+            # x 400), their weight gradients (with the bias column) and the conv-2 data
+            # gradient: the valid convolutions' multiply-adds
             work = {"fwd_gemm": ("tensor", 2.0 * units * 784 * 16 * 75),
                     "hidden_gemm": ("tensor", 2.0 * units * 100 * 32 * 400),
                     "hidden_wgrad_gemm": ("tensor", 2.0 * units * 100 * 32 * 401),
                     "adjoint_gemm": ("tensor", 2.0 * units * 100 * 32 * 400),
                     "wgrad_gemm": ("tensor", 2.0 * units * 784 * 16 * 76),
-                    # pooling, im2col of the pooled maps and col2im move at least the conv-2
-                    # im2col rows (written once, read by two GEMMs) and the data gradient once
-                    "simt_net": ("hbm", units * (100 * 408 * 2.0 + 100 * 400 * 2.0))}
+                    # im2col of the images (written once per image, shared by the particles)
+                    # and pool 2 forward / backward: Z2 read, P2 + idx2 written, dP2 + idx2
+                    # read, Z2 at each argmax read, dZ2 written (BF16, per particle-image)
+                    "simt_net": ("hbm", float(n) * (784 * 80 * 2.0 + 3 * 32 * 32 * 2.0) +
+                                 units * (6400.0 + 2400.0 + 2400.0 + 1600.0 + 6400.0)),
+                    # the head reads P2 and writes dP2 over it
+                    "head": ("hbm", units * 800 * 2 * 2.0)}
         kern = {}
         gemm_flop, gemm_ms = 0.0, 0.0
         for k, (bound, amount) in work.items():

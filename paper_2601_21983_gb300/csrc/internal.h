@@ -161,6 +161,7 @@ struct smc_ctx {
         __nv_bfloat16 *dZ2c = nullptr;   // dZ2 channel-blocked on the pooled conv-1 grid (zero padded)
         int64_t p1_rows = 0, dz_rows = 0;   // rows of one P1 / dZ2c channel plane
         float *dW2P = nullptr, *dW1P = nullptr;   // FP32 weight-gradient partials
+        float *db2P = nullptr;                    // per-image db2 partials [J][B][C2]
     } cnn;
     __nv_bfloat16* H1 = nullptr;     // [chunk_pad][J*H]
     __nv_bfloat16* dZT = nullptr;    // [J*H][chunk_pad]

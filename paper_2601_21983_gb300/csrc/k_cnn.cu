@@ -63,31 +63,38 @@ Shape shape_of(const smc_ctx* c) {
 }
 
 // ---------------------------------------------------------------- kernels
-// I1 [nimg R1][K1p], 8 columns per thread.
-__global__ void im2col1_kernel(const __nv_bfloat16* __restrict__ X, int64_t din, int nimg, Shape s,
+// I1 [nimg R1][K1p]: one block per image, staged in shared memory; each
+// column's source offset (c, ky, kx) comes from a table, and consecutive
+// threads write consecutive 16-byte pieces of the rows.
+__global__ void im2col1_kernel(const __nv_bfloat16* __restrict__ X, int64_t din, Shape s,
                                __nv_bfloat16* __restrict__ I1) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int q8 = s.K1p / 8;
-    if (t >= (int64_t)nimg * s.R1 * q8) return;
-    const int64_t row = t / q8;
-    const int k0 = (int)(t % q8) * 8;
-    const int img = (int)(row / s.R1), rr = (int)(row % s.R1);
-    const int w = rr >> 2, d = rr & 3;
-    const int oy = 2 * (w / s.WP1) + (d >> 1), ox = 2 * (w % s.WP1) + (d & 1);
+    extern __shared__ uint8_t sm_raw[];
+    int* off = reinterpret_cast<int*>(sm_raw);                              // [K1p]
+    __nv_bfloat16* xs = reinterpret_cast<__nv_bfloat16*>(off + s.K1p);    // [C0 H0 W0]
+    const int img = blockIdx.x;
+    const int npix = s.C0 * s.H0 * s.W0;
     const __nv_bfloat16* x = X + (int64_t)img * din;
-    __align__(16) __nv_bfloat16 v[8];
-    for (int e = 0; e < 8; ++e) {
-        const int k = k0 + e;
-        float f = 0.0f;
-        if (k < s.K1) {
-            const int ch = k / (s.k1 * s.k1), tp = k % (s.k1 * s.k1);
-            f = __bfloat162float(x[((int64_t)ch * s.H0 + oy + tp / s.k1) * s.W0 + ox + tp % s.k1]);
-        } else if (k == s.K1) {
-            f = 1.0f;
-        }
-        v[e] = __float2bfloat16_rn(f);
+    for (int i = threadIdx.x; i < npix; i += blockDim.x) xs[i] = x[i];
+    for (int k = threadIdx.x; k < s.K1p; k += blockDim.x) {
+        const int kk = s.k1 * s.k1;
+        off[k] = k < s.K1 ? (k / kk) * s.H0 * s.W0 + ((k % kk) / s.k1) * s.W0 + (k % kk) % s.k1
+                          : (k == s.K1 ? -1 : -2);
     }
-    *reinterpret_cast<uint4*>(I1 + row * s.K1p + k0) = *reinterpret_cast<const uint4*>(v);
+    __syncthreads();
+    const int q8 = s.K1p / 8;
+    const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), zero = __float2bfloat16_rn(0.0f);
+    for (int t = threadIdx.x; t < s.R1 * q8; t += blockDim.x) {
+        const int rr = t / q8, k0 = (t % q8) * 8;
+        const int w = rr >> 2, d = rr & 3;
+        const int base = (2 * (w / s.WP1) + (d >> 1)) * s.W0 + 2 * (w % s.WP1) + (d & 1);
+        __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int o = off[k0 + e];
+            v[e] = o >= 0 ? xs[base + o] : (o == -1 ? one : zero);
+        }
+        *reinterpret_cast<uint4*>(I1 + ((int64_t)img * s.R1 + rr) * s.K1p + k0) = *reinterpret_cast<const uint4*>(v);
+    }
 }
 
 // Grid row of the conv-2 output (oy, ox) of image img.
@@ -96,55 +103,93 @@ __host__ __device__ inline int64_t grid_row(const Shape& s, int img, int oy, int
 }
 
 // 2x2 max pool of Z2 [J][B NW1][C2] (grid rows) into P2 [J][B][F] ((c, h, w)
-// order) and idx2.
-__global__ void pool2_kernel(const __nv_bfloat16* __restrict__ Z2, int nimg, int B, int J, Shape s,
+// order) and idx2 (first maximum wins, window order (0,0), (0,1), (1,0),
+// (1,1)): one block per (particle, image); a thread pools 8 channels of one
+// window from 16-byte reads, the block writes its F outputs contiguously.
+__global__ void pool2_kernel(const __nv_bfloat16* __restrict__ Z2, int nimg, int B, Shape s,
                              __nv_bfloat16* __restrict__ P2, uint8_t* __restrict__ idx2) {
-    const int NW2 = s.HP2 * s.WP2;
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= (int64_t)J * nimg * NW2 * s.C2) return;
-    const int ch = (int)(t % s.C2);
-    const int64_t r = t / s.C2;
-    const int w = (int)(r % NW2);
-    const int64_t ji = r / NW2;
-    const int img = (int)(ji % nimg), j = (int)(ji / nimg);
-    const int oy = 2 * (w / s.WP2), ox = 2 * (w % s.WP2);
-    const __nv_bfloat16* z = Z2 + ((int64_t)j * B * s.NW1 + grid_row(s, img, oy, ox)) * s.C2 + ch;
-    const int64_t off[4] = {0, s.C2, (int64_t)s.WP1 * s.C2, (int64_t)(s.WP1 + 1) * s.C2};
-    float best = __bfloat162float(z[0]);
-    int bi = 0;
-    for (int d = 1; d < 4; ++d) {
-        const float v = __bfloat162float(z[off[d]]);
-        if (v > best) { best = v; bi = d; }
+    extern __shared__ uint8_t sm_raw[];
+    __nv_bfloat16* pv = reinterpret_cast<__nv_bfloat16*>(sm_raw);   // [F]
+    uint8_t* pi = reinterpret_cast<uint8_t*>(pv + s.F);               // [F]
+    const int img = blockIdx.x % nimg, j = blockIdx.x / nimg;
+    const int NW2 = s.HP2 * s.WP2, G8 = s.C2 / 8;
+    for (int t = threadIdx.x; t < NW2 * G8; t += blockDim.x) {
+        const int w = t / G8, cg = t % G8;
+        const int oy = 2 * (w / s.WP2), ox = 2 * (w % s.WP2);
+        const __nv_bfloat16* z = Z2 + ((int64_t)j * B * s.NW1 + grid_row(s, img, oy, ox)) * s.C2 + cg * 8;
+        const int64_t step[4] = {0, s.C2, (int64_t)s.WP1 * s.C2, (int64_t)(s.WP1 + 1) * s.C2};
+        uint4 r[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) r[d] = *reinterpret_cast<const uint4*>(z + step[d]);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            float best = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(&r[0])[e]);
+            int bi = 0;
+#pragma unroll
+            for (int d = 1; d < 4; ++d) {
+                const float v = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(&r[d])[e]);
+                if (v > best) { best = v; bi = d; }
+            }
+            const int f = (cg * 8 + e) * NW2 + w;
+            pv[f] = __float2bfloat16_rn(best);
+            pi[f] = (uint8_t)bi;
+        }
     }
-    const int64_t o = ((int64_t)j * B + img) * s.F + ch * NW2 + w;
-    P2[o] = __float2bfloat16_rn(best);
-    idx2[o] = (uint8_t)bi;
+    __syncthreads();
+    const int64_t o = ((int64_t)j * B + img) * s.F;
+    for (int i = threadIdx.x; i < s.F / 8; i += blockDim.x)
+        reinterpret_cast<uint4*>(P2 + o)[i] = reinterpret_cast<const uint4*>(pv)[i];
+    for (int i = threadIdx.x; i < s.F / 8; i += blockDim.x)
+        reinterpret_cast<uint2*>(idx2 + o)[i] = reinterpret_cast<const uint2*>(pi)[i];
 }
 
 // dZ2 into dZ2c: each window's gradient dP2 goes to its argmax, times tanh'(z)
 // = 1 - tanh(z)^2 from the stored activation; the other three outputs get 0.
+// One block per (particle, image): dP2 and idx2 staged in shared memory; the
+// threads of warp cb write 8-channel plane cb of every conv-2 output (16-byte
+// stores) and sum its BF16 values per channel, in a fixed order, into the
+// image's db2 partial [J][B][C2].
 __global__ void pool2_bwd_kernel(const __nv_bfloat16* __restrict__ dP2, const uint8_t* __restrict__ idx2, int nimg,
-                                 int B, int J, Shape s, int64_t dz_rows, const __nv_bfloat16* __restrict__ Z2,
-                                 __nv_bfloat16* __restrict__ dZ2c) {
+                                 int B, Shape s, int64_t dz_rows, const __nv_bfloat16* __restrict__ Z2,
+                                 __nv_bfloat16* __restrict__ dZ2c, float* __restrict__ db2part) {
+    extern __shared__ uint8_t sm_raw[];
+    __nv_bfloat16* dps = reinterpret_cast<__nv_bfloat16*>(sm_raw);   // [F]
+    uint8_t* bis = reinterpret_cast<uint8_t*>(dps + s.F);             // [F]
+    const int img = blockIdx.x % nimg, j = blockIdx.x / nimg;
     const int NW2 = s.HP2 * s.WP2;
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= (int64_t)J * nimg * NW2 * s.C2) return;
-    const int ch = (int)(t % s.C2);
-    const int64_t r = t / s.C2;
-    const int w = (int)(r % NW2);
-    const int64_t ji = r / NW2;
-    const int img = (int)(ji % nimg), j = (int)(ji / nimg);
-    const int64_t o = ((int64_t)j * B + img) * s.F + ch * NW2 + w;
-    const float dp = __bfloat162float(dP2[o]);
-    const int bi = idx2[o];
-    const int oy = 2 * (w / s.WP2), ox = 2 * (w % s.WP2);
-    const int64_t g = grid_row(s, img, oy, ox);
-    const int64_t gb = g + (bi >> 1) * s.WP1 + (bi & 1);
-    const float a = __bfloat162float(Z2[((int64_t)j * B * s.NW1 + gb) * s.C2 + ch]);
-    const __nv_bfloat16 v = __float2bfloat16_rn(dp * (1.0f - a * a));
-    const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
-    __nv_bfloat16* zc = dZ2c + ((int64_t)(4 * j + ch / 8) * dz_rows + kDzMarg + g) * 8 + ch % 8;
-    for (int d = 0; d < 4; ++d) zc[((d >> 1) * s.WP1 + (d & 1)) * 8] = d == bi ? v : zero;
+    const int64_t o = ((int64_t)j * B + img) * s.F;
+    for (int i = threadIdx.x; i < s.F / 8; i += blockDim.x)
+        reinterpret_cast<uint4*>(dps)[i] = reinterpret_cast<const uint4*>(dP2 + o)[i];
+    for (int i = threadIdx.x; i < s.F / 8; i += blockDim.x)
+        reinterpret_cast<uint2*>(bis)[i] = reinterpret_cast<const uint2*>(idx2 + o)[i];
+    __syncthreads();
+    const int cb = threadIdx.x >> 5, lane = threadIdx.x & 31;   // blockDim = 32 C2 / 8
+    float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int pos = lane; pos < s.H2 * s.W2; pos += 32) {
+        const int oy = pos / s.W2, ox = pos % s.W2;
+        const int w = (oy >> 1) * s.WP2 + (ox >> 1), d = (oy & 1) * 2 + (ox & 1);
+        const int64_t g = grid_row(s, img, oy, ox);
+        const uint4 zr = *reinterpret_cast<const uint4*>(Z2 + ((int64_t)j * B * s.NW1 + g) * s.C2 + cb * 8);
+        __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int f = (cb * 8 + e) * NW2 + w;
+            const float a = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(&zr)[e]);
+            v[e] = __float2bfloat16_rn(bis[f] == d ? __bfloat162float(dps[f]) * (1.0f - a * a) : 0.0f);
+            sum[e] += __bfloat162float(v[e]);
+        }
+        *reinterpret_cast<uint4*>(dZ2c + ((int64_t)(4 * j + cb) * dz_rows + kDzMarg + g) * 8) =
+            *reinterpret_cast<const uint4*>(v);
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) sum[e] += __shfl_xor_sync(0xffffffffu, sum[e], sh);
+    if (lane == 0) {
+        float* dst = db2part + ((int64_t)j * B + img) * s.C2 + cb * 8;
+        reinterpret_cast<float4*>(dst)[0] = make_float4(sum[0], sum[1], sum[2], sum[3]);
+        reinterpret_cast<float4*>(dst)[1] = make_float4(sum[4], sum[5], sum[6], sum[7]);
+    }
 }
 
 // Per-evaluation BF16 weight images: W1p [J C1][K1p] (zero padded) and two
@@ -243,6 +288,7 @@ smc_status cnn_check_model(const smc_ctx* c, std::string* why) {
     if (s.H1 % 2 || s.W1 % 2 || s.H2 % 2 || s.W2 % 2) { *why = "BF16 CNN path: even convolution outputs"; return SMC_EUNSUPPORTED; }
     if (s.R1 % kDW1Slices) { *why = "BF16 CNN path: conv-1 positions a multiple of 16"; return SMC_EUNSUPPORTED; }
     if (s.K1 + 1 > 96) { *why = "BF16 CNN path: C0 k1^2 < 96"; return SMC_EUNSUPPORTED; }
+    if (s.C0 * s.H0 * s.W0 > 16384) { *why = "BF16 CNN path: at most 16384 input values per image"; return SMC_EUNSUPPORTED; }
     if (s.F % 8 != 0 || s.F > 800) { *why = "BF16 CNN path: at most 800 features, a multiple of 8"; return SMC_EUNSUPPORTED; }
     if ((s.k2 - 1) * (s.WP1 + 1) > kMaxShift || s.k2 > 5) {
         *why = "BF16 CNN path: (k2 - 1)(WP1 + 1) <= 63 and k2 <= 5";
@@ -273,7 +319,7 @@ smc_status cnn_alloc(smc_ctx* c) {
               al(b.idx1, J * b.p1_rows * s.C1) && al(b.Z2, J * b.p1_rows * s.C2) && al(b.P2, J * B * s.F) &&
               al(b.idx2, J * B * s.F) && al(b.W1p, J * s.C1 * s.K1p) && al(b.W2f, J * s.C2 * s.K2) &&
               al(b.W2t, J * s.C2 * s.K2) && al(b.dZ2c, J * s.C2 * b.dz_rows) &&
-              al(b.dW2P, conv2_wgrad_partial_elems(c, s)) &&
+              al(b.dW2P, conv2_wgrad_partial_elems(c, s)) && al(b.db2P, J * B * s.C2) &&
               al(b.dW1P, (int64_t)kDW1Slices * J * s.C1 * (s.K1 + 1));
     if (!ok) return SMC_ENOMEM;
     const int64_t per = (int64_t)s.C * s.F + s.C;
@@ -293,6 +339,7 @@ void cnn_free(smc_ctx* c) {
     auto& b = c->cnn;
     cudaFree(b.I1); cudaFree(b.Z1); cudaFree(b.P1); cudaFree(b.idx1); cudaFree(b.Z2); cudaFree(b.P2);
     cudaFree(b.idx2); cudaFree(b.W1p); cudaFree(b.W2f); cudaFree(b.W2t); cudaFree(b.dZ2c); cudaFree(b.dW2P);
+    cudaFree(b.db2P);
     cudaFree(b.dW1P);
     c->cnn = smc_ctx::CnnBuffers{};
     cudaFree(c->head_part); cudaFree(c->head_ll);
@@ -303,8 +350,8 @@ void cnn_free(smc_ctx* c) {
 static cudaError_t cnn_forward(smc_ctx* c, const Shape& s, const __nv_bfloat16* x, int nimg) {
     const int64_t B = c->chunk, J = c->J;
     auto& b = c->cnn;
-    SMC_LAUNCH(c, im2col1_kernel<<<blocks((int64_t)nimg * s.R1 * (s.K1p / 8)), 256, 0, c->stream>>>(
-                      x, c->in_feat, nimg, s, b.I1));
+    SMC_LAUNCH(c, im2col1_kernel<<<nimg, 256, (size_t)s.K1p * 4 + (size_t)s.C0 * s.H0 * s.W0 * 2, c->stream>>>(
+                      x, c->in_feat, s, b.I1));
     // conv 1 and pool 1: one GEMM over all particles' filters whose epilogue
     // pools each window's four rows (only P1 and idx1 are written)
     {
@@ -328,8 +375,8 @@ static cudaError_t cnn_forward(smc_ctx* c, const Shape& s, const __nv_bfloat16* 
     fam_end(c, F_HIDDEN_GEMM);
     if (e2 != cudaSuccess) return e2;
     fam_begin(c, F_SIMT_NET);
-    SMC_LAUNCH(c, pool2_kernel<<<blocks(J * nimg * s.HP2 * s.WP2 * s.C2), 256, 0, c->stream>>>(
-                      b.Z2, nimg, (int)B, (int)J, s, b.P2, b.idx2));
+    SMC_LAUNCH(c, pool2_kernel<<<(unsigned)(J * nimg), 128, (size_t)s.F * 3, c->stream>>>(
+                      b.Z2, nimg, (int)B, s, b.P2, b.idx2));
     fam_end(c, F_SIMT_NET);
     return cudaGetLastError();
 }
@@ -367,8 +414,8 @@ smc_status cnn_eval(smc_ctx* c) {
         if (e != cudaSuccess) return cuda_check(c, e, "head kernel");
         slot += nsl;
         fam_begin(c, F_SIMT_NET);
-        SMC_LAUNCH(c, pool2_bwd_kernel<<<blocks(J * nimg * s.HP2 * s.WP2 * s.C2), 256, 0, c->stream>>>(
-                          b.P2, b.idx2, nimg, (int)B, (int)J, s, b.dz_rows, b.Z2, b.dZ2c));
+        SMC_LAUNCH(c, pool2_bwd_kernel<<<(unsigned)(J * nimg), 32 * (s.C2 / 8), (size_t)s.F * 3, c->stream>>>(
+                          b.P2, b.idx2, nimg, (int)B, s, b.dz_rows, b.Z2, b.dZ2c, b.db2P));
         fam_end(c, F_SIMT_NET);
         // [dW2 | db2] (+)= the chunk's sums (implicit GEMM over dZ2c and P1)
         fam_begin(c, F_HWGRAD_GEMM);

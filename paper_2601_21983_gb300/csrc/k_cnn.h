@@ -38,7 +38,7 @@ constexpr int kTile = 128;
 
 // Splits of a particle's tiles so that J * splits is a multiple of the grid.
 int conv2_splits(int J, int grid);
-// FP32 partials of the conv-2 weight gradient: J * splits * (K2 + 1) * C2 floats.
+// FP32 partials of the conv-2 weight gradient: J * splits * K2 * C2 floats.
 int64_t conv2_wgrad_partial_elems(const smc_ctx* c, const Shape& s);
 
 // conv 2 forward: Z2 = tanh(conv(P1, W2) + b2) for the chunk's nimg images.

@@ -18,9 +18,9 @@
 //                plane (MN-major A whose 8-row groups are 16 bytes apart, so
 //                group g reads the window g rows further on), N = C2 (MN-major
 //                B from the dZ2 planes), K = 16 grid rows; shifts 0..63 in four
-//                blocks per plane cover every tap (s <= 60), plus a block on a
-//                plane of ones for db2; FP32 accumulators stay in TMEM over a
-//                particle's run of tiles.
+//                blocks per plane cover every tap (s <= 60); FP32 accumulators
+//                stay in TMEM over a particle's run of tiles (db2 comes from
+//                the pool-2 backward's per-image sums).
 // Rows a valid convolution does not produce (x >= W2 or y >= H2 on the grid)
 // are computed by the forward and dropped by pooling; dZ2c holds zeros there,
 // so they add nothing to either gradient.
@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(320, 2) conv2_dgrad_kernel(const __grid_consta
 struct WgArgs {
     int S, k2, WP1, K2;
     int64_t T, units;
-    float* part;   // [J][S][K2 + 1][32]: rows tap * 16 + input channel, then db2
+    float* part;   // [J][S][K2][32]: rows tap * 16 + input channel
     int* err;
 };
 
@@ -528,8 +528,7 @@ __global__ void __launch_bounds__(192, 1) conv2_wgrad_kernel(const __grid_consta
                                                              const __grid_constant__ CUtensorMap tmZ, const WgArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = align128(smem_raw);
-    uint8_t* ones = smem;   // rows of (1, 0, ..., 0): the db2 block's A operand
-    uint8_t* stages = ones + kPlane;
+    uint8_t* stages = smem;
     uint64_t* full = (uint64_t*)(stages + kWgStages * kWgStage);
     uint64_t* empty = full + kWgStages;
     uint64_t* tfull = empty + kWgStages;
@@ -538,16 +537,13 @@ __global__ void __launch_bounds__(192, 1) conv2_wgrad_kernel(const __grid_consta
     uint32_t* tslot = (uint32_t*)(drain + 1);
     volatile int* abort_flag = (volatile int*)(tslot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < kPlane / 16; i += blockDim.x)
-        reinterpret_cast<uint4*>(ones)[i] = make_uint4(0x3F80u, 0u, 0u, 0u);   // BF16 1.0 in element 0
-    fence_proxy_async_smem();
     if (threadIdx.x == 0) {
         for (int q = 0; q < kWgStages; ++q) { mbar_init(full + q, 1); mbar_init(empty + q, 1); }
         mbar_init(tfull, 1); mbar_init(tempty, 4); mbar_init(drain, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == 1) tmem_alloc(tslot, 512);   // 9 accumulators of 32 columns
+    if (warp == 1) tmem_alloc(tslot, 256);   // 8 accumulators of 32 columns
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -581,7 +577,6 @@ __global__ void __launch_bounds__(192, 1) conv2_wgrad_kernel(const __grid_consta
             int stage = 0, units_seen = 0;
             uint32_t ph = 0, uph = 0;
             bool ok = true;
-            const uint32_t so = su32(ones);
             while (ok && it.next(a.units, a.S, a.T)) {
                 if (it.fresh) {
                     if (units_seen++ > 0) umma_commit(tfull);   // the previous unit's sums are complete
@@ -602,7 +597,6 @@ __global__ void __launch_bounds__(192, 1) conv2_wgrad_kernel(const __grid_consta
                         const uint64_t ad = sdesc_ns(sp + (q >> 2) * kPlane + (16 * (q & 3) + 16 * ks) * 16, 128, 16);
                         umma_bf16(tbase + (uint32_t)q * 32, ad, bd, ID, acc_on);
                     }
-                    umma_bf16(tbase + 256, sdesc_ns(so + ks * 256, 128, 16), bd, ID, acc_on);
                 }
                 umma_commit(empty + stage);
                 if (++stage == kWgStages) { stage = 0; ph ^= 1; }
@@ -620,7 +614,7 @@ __global__ void __launch_bounds__(192, 1) conv2_wgrad_kernel(const __grid_consta
         for (int64_t u = blockIdx.x; u < a.units; u += gridDim.x) {
             const int s = (int)(u % a.S), j = (int)(u / a.S);
             const bool empty_unit = (s * a.T / a.S) == ((s + 1) * a.T / a.S);
-            float* base = a.part + ((int64_t)j * a.S + s) * (a.K2 + 1) * 32;
+            float* base = a.part + ((int64_t)j * a.S + s) * a.K2 * 32;
             if (!empty_unit) {
                 if (!mbar_wait(tfull, uph, abort_flag)) {
                     role_abort(abort_flag, a.err, ERR_WG, false);
@@ -629,7 +623,7 @@ __global__ void __launch_bounds__(192, 1) conv2_wgrad_kernel(const __grid_consta
                 uph ^= 1;
                 tc_fence_after();
             }
-            for (int q = 0; q < 9; ++q) {
+            for (int q = 0; q < 8; ++q) {
                 uint32_t r[32];
                 __syncwarp();
                 if (!empty_unit) {
@@ -640,13 +634,9 @@ __global__ void __launch_bounds__(192, 1) conv2_wgrad_kernel(const __grid_consta
                     for (int c = 0; c < 32; ++c) r[c] = 0u;
                 }
                 int row = -1;
-                if (q < 8) {
-                    const int shift = 16 * (q & 3) + (m >> 3);
-                    const int ky = shift / a.WP1, kx = shift % a.WP1;
-                    if (ky < a.k2 && kx < a.k2) row = (ky * a.k2 + kx) * 16 + (q >> 2) * 8 + (m & 7);
-                } else if (m == 0) {
-                    row = a.K2;
-                }
+                const int shift = 16 * (q & 3) + (m >> 3);
+                const int ky = shift / a.WP1, kx = shift % a.WP1;
+                if (ky < a.k2 && kx < a.k2) row = (ky * a.k2 + kx) * 16 + (q >> 2) * 8 + (m & 7);
                 if (row >= 0) {
                     float4* dst = reinterpret_cast<float4*>(base + (int64_t)row * 32);
 #pragma unroll
@@ -666,23 +656,29 @@ __global__ void __launch_bounds__(192, 1) conv2_wgrad_kernel(const __grid_consta
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tbase, 512);
+        tmem_dealloc(tbase, 256);
     }
 }
 
-// gW2 [J][C2][C1 taps] and gb2 [J][C2] (+)= the sum over splits (in order) of
-// the partials [J][S][K2 + 1][C2] (rows tap * C1 + channel, then db2).
-__global__ void conv2_wgrad_reduce_kernel(const float* __restrict__ part, int J, int S, int C1, int C2, int taps,
-                                          int accumulate, float* __restrict__ gW2, float* __restrict__ gb2) {
+// gW2 [J][C2][C1 taps] (+)= the sum over splits (in order) of the partials
+// [J][S][K2][C2] (rows tap * C1 + channel); gb2 [J][C2] (+)= the sum over the
+// chunk's images (in order) of the per-image partials db2part [J][B][C2].
+__global__ void conv2_wgrad_reduce_kernel(const float* __restrict__ part, const float* __restrict__ db2part, int J,
+                                          int S, int B, int nimg, int C1, int C2, int taps, int accumulate,
+                                          float* __restrict__ gW2, float* __restrict__ gb2) {
     const int K2 = C1 * taps;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)J * C2 * (K2 + 1)) return;
     const int j = (int)(t / ((int64_t)C2 * (K2 + 1)));
     const int e = (int)(t % ((int64_t)C2 * (K2 + 1)));
     const int co = e / (K2 + 1), k = e % (K2 + 1);   // k = channel * taps + tap, or K2 for db2
-    const int row = k == K2 ? K2 : (k % taps) * C1 + k / taps;
     float v = 0.0f;
-    for (int s = 0; s < S; ++s) v += part[(((int64_t)j * S + s) * (K2 + 1) + row) * C2 + co];
+    if (k == K2) {
+        for (int i = 0; i < nimg; ++i) v += db2part[((int64_t)j * B + i) * C2 + co];
+    } else {
+        const int row = (k % taps) * C1 + k / taps;
+        for (int s = 0; s < S; ++s) v += part[(((int64_t)j * S + s) * K2 + row) * C2 + co];
+    }
     float* d = k == K2 ? gb2 + (int64_t)j * C2 + co : gW2 + ((int64_t)j * C2 + co) * K2 + k;
     *d = accumulate ? *d + v : v;
 }
@@ -691,7 +687,7 @@ __global__ void conv2_wgrad_reduce_kernel(const float* __restrict__ part, int J,
 int conv2_splits(int J, int grid) { return grid / std::gcd(J, grid); }
 
 int64_t conv2_wgrad_partial_elems(const smc_ctx* c, const Shape& s) {
-    return (int64_t)c->J * conv2_splits(c->J, c->num_sms) * (s.K2 + 1) * s.C2;
+    return (int64_t)c->J * conv2_splits(c->J, c->num_sms) * s.K2 * s.C2;
 }
 
 // Work split of a launch with at most `grid_max` CTAs over J particles' T tiles.
@@ -768,7 +764,7 @@ cudaError_t conv2_wgrad(smc_ctx* c, const Shape& s, int nimg, int accumulate) {
     WgArgs a{};
     a.S = pl.S; a.k2 = s.k2; a.WP1 = s.WP1; a.K2 = s.K2;
     a.T = pl.T; a.units = pl.units; a.part = b.dW2P; a.err = c->err_dev;
-    const size_t smem = 128 + (size_t)kPlane + (size_t)kWgStages * kWgStage + 256;
+    const size_t smem = 128 + (size_t)kWgStages * kWgStage + 256;
     cudaError_t e = cudaFuncSetAttribute(conv2_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     conv2_wgrad_kernel<<<pl.grid, 192, smem, c->stream>>>(tmP, tmZ, a);
@@ -777,7 +773,8 @@ cudaError_t conv2_wgrad(smc_ctx* c, const Shape& s, int nimg, int accumulate) {
     if (e != cudaSuccess) return e;
     const int taps = s.k2 * s.k2;
     conv2_wgrad_reduce_kernel<<<blocks256((int64_t)c->J * s.C2 * (s.K2 + 1)), 256, 0, c->stream>>>(
-        b.dW2P, c->J, pl.S, s.C1, s.C2, taps, accumulate, c->grad + c->segs[c->layers[2].seg_w].off,
+        b.dW2P, b.db2P, c->J, pl.S, (int)c->chunk, nimg, s.C1, s.C2, taps, accumulate,
+        c->grad + c->segs[c->layers[2].seg_w].off,
         c->grad + c->segs[c->layers[2].seg_b].off);
     c->launches++;
     return cudaGetLastError();
