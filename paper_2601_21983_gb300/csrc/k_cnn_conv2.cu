@@ -276,17 +276,21 @@ constexpr int kEpiGroups = 2;     // its epilogue warp groups, one per TMEM accu
 // 128 grid rows q = r0 - 4 .. r0 + 123 of a tile (2 k2 MMAs, N = 16 k2), then
 // dP1[p][ci] = sum_kx E[p - kx][(kx, ci)] for p = r0 .. r0 + 123: row p - kx
 // is kx lanes back (a warp shuffle), or in the previous warp's last four rows,
-// published in shared memory first; pool-1 backward follows.
+// published in shared memory first; pool-1 backward follows.  A tile's outputs
+// are the dZ1 rows [4 r0, 4 r0 + 496) (four per pooled position, consecutive
+// across images) of particle j's 16 columns: each warp stages its rows in
+// shared memory and writes them with one TMA store.
 struct DgArgs {
-    int S, k2, WP1, R1, JC;
+    int S, k2, WP1;
     int64_t T, units, nvalid, rows_per_particle, p1_rows;
     int NW1;
     const __nv_bfloat16* W;   // [J][ky][(kx, ci) / 8][co / 8][8][8] (K-major per ky)
     const __nv_bfloat16* P1;
     const uint8_t* idx1;
-    __nv_bfloat16* Z1;        // dZ1 out: [B R1][J C1]
     int* err;
 };
+
+constexpr int kDgStageRows = 128;   // dZ1 rows staged per epilogue warp (4 per position)
 
 // What the epilogue needs of grid row p besides the accumulator: the pooled
 // conv-1 values (both planes) and the window argmaxes.
@@ -305,7 +309,11 @@ static __device__ __forceinline__ DgAux dg_aux(const DgArgs& a, int j, int64_t p
     return x;
 }
 
-__global__ void __launch_bounds__(320, 2) conv2_dgrad_kernel(const __grid_constant__ CUtensorMap tmD, const DgArgs a) {
+// tmO128 / tmO112: dZ1 [B R1][J C1] with boxes of 16 columns x 128 or 112 rows.
+__global__ void __launch_bounds__(320, 2) conv2_dgrad_kernel(const __grid_constant__ CUtensorMap tmD,
+                                                             const __grid_constant__ CUtensorMap tmO128,
+                                                             const __grid_constant__ CUtensorMap tmO112,
+                                                             const DgArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = align128(smem_raw);
     const int ncols = 16 * a.k2;                      // accumulator columns (kx, ci)
@@ -313,7 +321,8 @@ __global__ void __launch_bounds__(320, 2) conv2_dgrad_kernel(const __grid_consta
     uint8_t* wbuf = smem;
     uint8_t* stages = wbuf + a.k2 * wky;
     float* xbuf = (float*)(stages + kDgStages * 4 * kPlane);   // [group][2][warp][4 rows][4 kx][16]
-    uint64_t* full = (uint64_t*)(xbuf + kEpiGroups * 2 * 4 * 256);
+    uint8_t* obuf = (uint8_t*)(xbuf + kEpiGroups * 2 * 4 * 256);  // [epilogue warp][128 rows][32 bytes]
+    uint64_t* full = (uint64_t*)(obuf + 8 * kDgStageRows * 32);
     uint64_t* empty = full + kDgStages;
     uint64_t* tfull = empty + kDgStages;
     uint64_t* tempty = tfull + 2;
@@ -479,33 +488,51 @@ __global__ void __launch_bounds__(320, 2) conv2_dgrad_kernel(const __grid_consta
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty + grp);
-            const int64_t p = it.t * kOut - 4 + m;
-            if (m >= 4 && p < a.nvalid) {
-                const int img = (int)(p / a.NW1), w = (int)(p % a.NW1);
+            // pool-1 backward into this warp's staging rows (4 per position, lane-rotated
+            // 16-byte pieces so the eight lanes of each phase hit distinct banks)
+            uint8_t* ob = obuf + (warp - 2) * kDgStageRows * 32;
+            if (lane == 0) bulk_wait_read0();   // the previous tile's store has read the buffer
+            __syncwarp();
+            {
                 const __nv_bfloat16* pv = reinterpret_cast<const __nv_bfloat16*>(&cur.p0);
                 const __nv_bfloat16* pw = reinterpret_cast<const __nv_bfloat16*>(&cur.p1);
                 const uint8_t* bi = reinterpret_cast<const uint8_t*>(&cur.bi);
-                __align__(16) __nv_bfloat16 out[4][16];
+                float v[16];
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
                     const float h = __bfloat162float(c < 8 ? pv[c] : pw[c - 8]);
-                    const float v = acc[c] * (1.0f - h * h);
-#pragma unroll
-                    for (int d = 0; d < 4; ++d) out[d][c] = __float2bfloat16_rn(d == bi[c] ? v : 0.0f);
+                    v[c] = acc[c] * (1.0f - h * h);
                 }
+                // piece pc = 2 d + half: row d of this position, channels 8 half .. + 7
 #pragma unroll
-                for (int d = 0; d < 4; ++d) {
-                    uint4* dst = reinterpret_cast<uint4*>(a.Z1 + ((int64_t)img * a.R1 + 4 * w + d) * a.JC +
-                                                          (int64_t)it.j * 16);
-                    dst[0] = reinterpret_cast<const uint4*>(out[d])[0];
-                    dst[1] = reinterpret_cast<const uint4*>(out[d])[1];
+                for (int i = 0; i < 8; ++i) {
+                    const int pc = (i + lane) & 7, d = pc >> 1;
+                    const bool hi = pc & 1;
+                    __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const float x = hi ? v[8 + e] : v[e];
+                        const int b = hi ? bi[8 + e] : bi[e];
+                        o[e] = __float2bfloat16_rn(b == d ? x : 0.0f);
+                    }
+                    *reinterpret_cast<uint4*>(ob + lane * 128 + pc * 16) = *reinterpret_cast<const uint4*>(o);
                 }
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                // positions r0 - 4 + m, m = 32 wq + lane; warp 0's first four are not outputs
+                const int y = 4 * (int)(it.t * kOut) - 16 + 128 * wq;
+                if (wq == 0) tma_store_2d(&tmO112, ob + 16 * 32, it.j * 16, y + 16);
+                else tma_store_2d(&tmO128, ob, it.j * 16, y);
+                bulk_commit();
             }
             it = nx;
             have = hn;
             cur = nxt;
         }
     }
+    if (warp >= 2 && lane == 0) bulk_wait_all();   // this warp's output stores are complete
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
@@ -735,17 +762,22 @@ cudaError_t conv2_dgrad(smc_ctx* c, const Shape& s, int nimg) {
     CUtensorMap tm;
     if (!planes_map(&tm, b.dZ2c, b.dz_rows, b.dz_rows, 4 * (int64_t)c->J, kTile + shift_rows))
         return cudaErrorInvalidValue;
+    CUtensorMap to128, to112;
+    const uint64_t out_rows = (uint64_t)nimg * s.R1, JC = (uint64_t)c->J * s.C1;
+    if (!make_store_tmap_2d(&to128, b.Z1, JC, out_rows, JC * 2, 16, kDgStageRows) ||
+        !make_store_tmap_2d(&to112, b.Z1, JC, out_rows, JC * 2, 16, kDgStageRows - 16))
+        return cudaErrorInvalidValue;
     const Plan pl = plan(c, nimg, s, 2 * c->num_sms, kOut);
     DgArgs a{};
-    a.S = pl.S; a.k2 = s.k2; a.WP1 = s.WP1; a.R1 = s.R1; a.JC = c->J * s.C1; a.NW1 = s.NW1;
+    a.S = pl.S; a.k2 = s.k2; a.WP1 = s.WP1; a.NW1 = s.NW1;
     a.T = pl.T; a.units = pl.units; a.nvalid = (int64_t)nimg * s.NW1; a.rows_per_particle = b.p1_rows;
     a.p1_rows = b.p1_rows;
-    a.W = b.W2t; a.P1 = b.P1; a.idx1 = b.idx1; a.Z1 = b.Z1; a.err = c->err_dev;
+    a.W = b.W2t; a.P1 = b.P1; a.idx1 = b.idx1; a.err = c->err_dev;
     const size_t smem = 128 + (size_t)s.k2 * s.k2 * 1024 + (size_t)kDgStages * 4 * kPlane +
-                        (size_t)kEpiGroups * 2 * 4 * 256 * 4 + 256;
+                        (size_t)kEpiGroups * 2 * 4 * 256 * 4 + (size_t)8 * kDgStageRows * 32 + 256;
     cudaError_t e = cudaFuncSetAttribute(conv2_dgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    conv2_dgrad_kernel<<<pl.grid, 320, smem, c->stream>>>(tm, a);
+    conv2_dgrad_kernel<<<pl.grid, 320, smem, c->stream>>>(tm, to128, to112, a);
     c->launches++;
     return cudaGetLastError();
 }
