@@ -30,8 +30,6 @@
 #include "k_cnn.h"
 
 #include "k_grouped.h"
-#include "tc_ptx.cuh"
-#include "tmap.cuh"
 
 #include <algorithm>
 #include <math.h>

@@ -35,7 +35,7 @@
 #include "k_cnn.h"
 
 #include "tc_ptx.cuh"
-#include "tmap.cuh"
+#include "tmap_plain.cuh"
 
 #include <algorithm>
 #include <math.h>
