@@ -8,7 +8,11 @@ max-pool kinks: on these smooth images neighbouring conv outputs are often
 within BF16 rounding of each other, so the kernel's BF16 argmax and the
 oracle's FP64 argmax can pick different positions and route a window's
 gradient through a different input patch (as a ReLU mask flips at BF16
-rounding of 0 in the dense tests); those blocks are bounded at 5e-2."""
+rounding of 0 in the dense tests); those blocks are bounded at 5e-2.  The
+whole gradient's bound follows from the blocks' bounds: with e_b <= t_b for
+every block b, the norm-wise error of the whole is at most
+sqrt(sum_b t_b^2 |g_b|^2) / |g|, which is 2e-2 when the dense blocks carry the
+norm and approaches 5e-2 when the convolution blocks do (1-channel images)."""
 import numpy as np
 import pytest
 
@@ -25,28 +29,51 @@ TOL = 2e-2
 CNN2 = nn.Spec([("conv", 3, 16, 5), ("pool2",), ("conv", 16, 32, 5), ("pool2",), ("dense", 800, 10)], (3, 32, 32),
                nn.TANH)
 BLOCKS = [(16, 3, 5, 5), (16,), (32, 16, 5, 5), (32,), (10, 800), (10,)]
+# a second shape for the implicit conv-2 kernels: 1x28x28 images, a 12 x 12
+# pooled grid (tap shifts ky 12 + kx up to 52), 4 x 4 x 32 = 512 features
+CNN28 = nn.Spec([("conv", 1, 16, 5), ("pool2",), ("conv", 16, 32, 5), ("pool2",), ("dense", 512, 10)], (1, 28, 28),
+                nn.TANH)
+BLOCKS28 = [(16, 1, 5, 5), (16,), (32, 16, 5, 5), (32,), (10, 512), (10,)]
 
 
 def _per_particle_rel(a, b):
     return max(rel_err(a[j], b[j]) for j in range(a.shape[0]))
 
 
-def _check_eval(ctx, orc, J):
-    lp, g, la, lb = S.smc_eval(ctx, J, CNN2.n_params)
+BLOCK_TOL = [5e-2, 5e-2, 5e-2, 5e-2, TOL, TOL]   # conv W1, b1, W2, b2 (behind pooling), dense W, b
+
+
+def _whole_bound(rg, blocks):
+    """Per particle: sqrt(sum_b t_b^2 |g_b|^2) / |g| over the oracle's blocks."""
+    out = []
+    for j in range(rg.shape[0]):
+        off, acc = 0, 0.0
+        for shp, t in zip(blocks, BLOCK_TOL):
+            n = int(np.prod(shp))
+            acc += t * t * float(np.sum(rg[j, off:off + n] ** 2))
+            off += n
+        out.append(np.sqrt(acc / float(np.sum(rg[j] ** 2))))
+    return np.array(out)
+
+
+def _check_eval(ctx, orc, J, spec=CNN2, blocks=BLOCKS):
+    lp, g, la, lb = S.smc_eval(ctx, J, spec.n_params)
     rlp, rg, rla, rlb = oracle_eval(orc)
     scale = np.abs(rla) + np.abs(rlb)
     assert np.all(np.abs(la - rla) <= TOL * scale + 1e-6)
     assert np.all(np.abs(lb - rlb) <= TOL * scale + 1e-6)
     assert np.allclose(lp, rlp, rtol=TOL)
-    assert _per_particle_rel(g, rg) < TOL
     off, errs = 0, []
-    for shp in BLOCKS:
+    for shp in blocks:
         n = int(np.prod(shp))
         errs.append(_per_particle_rel(g[:, off:off + n], rg[:, off:off + n]))
         off += n
-    print("block errors", [f"{e:.2e}" for e in errs])
-    for shp, e, tol in zip(BLOCKS, errs, [5e-2, 5e-2, 5e-2, 5e-2, TOL, TOL]):
+    bound = np.maximum(_whole_bound(rg, blocks), TOL)
+    whole = np.array([rel_err(g[j], rg[j]) for j in range(J)])
+    print("block errors", [f"{e:.2e}" for e in errs], "whole", f"{whole.max():.2e}", "bound", f"{bound.min():.2e}")
+    for shp, e, tol in zip(blocks, errs, BLOCK_TOL):
         assert e < tol, (shp, e)
+    assert np.all(whole < bound), (whole, bound)
     return lp, g
 
 
@@ -66,6 +93,28 @@ def test_bf16_cnn_eval_parity(chunk):
         S.smc_anneal_next(ctx)
         orc.anneal_next()
         _check_eval(ctx, orc, J)
+    finally:
+        S.smc_destroy(ctx)
+
+
+def test_bf16_cnn_second_shape_parity():
+    """The same engine on 1x28x28 images (a 12 x 12 pooled grid instead of
+    14 x 14, so other tap shifts, window sizes and tile-to-image alignments in
+    the implicit conv-2 kernels; 512 features into the head), 5 particles,
+    chunks of 36 images (a ragged tail of 8), before and after one tempering
+    step."""
+    N, J = 80, 5
+    X, y = synthetic.smooth_field_images(N, seed=74, side=28, channels=1)
+    ctx, orc, _ = make_pair(CNN28, X, y, J, seed=74, precision=S.PREC_BF16, chunk=36)
+    try:
+        th0 = synthetic.particles(J, CNN28.n_params, 74, std=0.1)
+        S.smc_set_state(ctx, th0)
+        S.smc_set_schedule(ctx, S.make_schedule("linear", 40, 40, 10))
+        orc.set_schedule("linear", 40, 40, 10, th0)
+        _check_eval(ctx, orc, J, CNN28, BLOCKS28)
+        S.smc_anneal_next(ctx)
+        orc.anneal_next()
+        _check_eval(ctx, orc, J, CNN28, BLOCKS28)
     finally:
         S.smc_destroy(ctx)
 
