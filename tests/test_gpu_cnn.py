@@ -123,6 +123,24 @@ def test_bf16_cnn_second_shape_parity():
         S.smc_destroy(ctx)
 
 
+@pytest.mark.parametrize("J,N,chunk", [(1, 3, 2), (2, 1, 0), (7, 5, 1)])
+def test_bf16_cnn_tiny_edges(J, N, chunk):
+    """Edges of the engine's work split: one particle (J = 1: conv 1's N = 16
+    columns, one split unit per tile run), a single image (196 grid rows: two
+    128-row tiles, the second mostly past the data), chunks of one image, and
+    J = 7 (splits that do not divide the grid evenly)."""
+    X, y = synthetic.smooth_field_images(N, seed=76)
+    ctx, orc, _ = make_pair(CNN2, X, y, J, seed=76, precision=S.PREC_BF16, chunk=chunk)
+    try:
+        th0 = synthetic.particles(J, CNN2.n_params, 76, std=0.1)
+        S.smc_set_state(ctx, th0)
+        S.smc_set_schedule(ctx, S.make_schedule("constant", N, N, 10))
+        orc.set_schedule("constant", N, N, 10, th0)
+        _check_eval(ctx, orc, J)
+    finally:
+        S.smc_destroy(ctx)
+
+
 def test_bf16_cnn_sda_parity():
     """SDA (Sec. 3.1) on the CNN: both row regions, teacher-forced from the GPU's
     particles and weights each iteration; region sums, log pi and gradients
