@@ -13,14 +13,20 @@
 //                E[q][(kx, ci)] = sum_ky dZ2[q - ky WP1] W2_(ky, kx) (M = 128,
 //                N = 16 k2, K = C2: 2 k2 MMAs per tile), dP1[p] = sum_kx
 //                E[p - kx][kx] across lanes, then pool-1 backward
-//   weight grad  dW2_t = sum_p P1[p + s_t]^T dZ2[p], db2 = sum_p dZ2[p]:
-//                M = 128 rows = 16 consecutive shifts x 8 channels of one
+//   weight grad  dW2_t = sum_p P1[p + s_t]^T dZ2[p] with s_t = sa + 16 i:
+//                M = 128 rows = 16 consecutive shifts sa x 8 channels of one
 //                plane (MN-major A whose 8-row groups are 16 bytes apart, so
-//                group g reads the window g rows further on), N = C2 (MN-major
-//                B from the dZ2 planes), K = 16 grid rows; shifts 0..63 in four
-//                blocks per plane cover every tap (s <= 60); FP32 accumulators
-//                stay in TMEM over a particle's run of tiles (db2 comes from
-//                the pool-2 backward's per-image sums).
+//                group g reads the window g rows further on), N = 32 nsb =
+//                (i, C2) from nsb copies of the dZ2 planes loaded 16 i rows
+//                earlier (MN-major B), K = 16 grid rows: ONE MMA per channel
+//                plane and K step covers shifts 0 .. 16 nsb - 1 >= every tap;
+//                FP32 accumulators stay in TMEM over a particle's run of tiles
+//                (db2 comes from the pool-2 backward's per-image sums).  A
+//                copy shifted by 16 i sums dZ2 rows q over [start - 16 i,
+//                end - 16 i): the rows it skips at the end are a particle's
+//                last 16 i <= shift_max grid rows, outputs no valid
+//                convolution produces (zero in dZ2c), and the rows before 0
+//                are the zero margin.
 // Rows a valid convolution does not produce (x >= W2 or y >= H2 on the grid)
 // are computed by the forward and dropped by pooling; dZ2c holds zeros there,
 // so they add nothing to either gradient.
@@ -48,7 +54,7 @@ using namespace tcg;
 
 constexpr int kPlane = 3072;   // bytes of one 8-channel plane of a window (192 rows)
 constexpr int kTapB = 1024;    // one tap's C1 x C2 BF16 B operand
-constexpr int kFwdStages = 4, kDgStages = 3, kWgStages = 8;
+constexpr int kFwdStages = 4, kDgStages = 3, kWgStages = 5;
 constexpr int kZPlane = kTile * 16;   // one 8-channel plane of a tile's dZ2 rows
 enum { ERR_FWD = 0x411, ERR_DG = 0x412, ERR_WG = 0x413 };
 
@@ -543,13 +549,15 @@ __global__ void __launch_bounds__(320, 2) conv2_dgrad_kernel(const __grid_consta
 
 // ---------------------------------------------------------- weight gradient
 struct WgArgs {
-    int S, k2, WP1, K2;
+    int S, k2, WP1, K2, nsb;   // nsb: dZ2 copies (B-side shifts 0, 16, ..)
     int64_t T, units;
     float* part;   // [J][S][K2][32]: rows tap * 16 + input channel
     int* err;
 };
 
-constexpr int kWgStage = 2 * kPlane + 4 * kZPlane;   // P1 window (192 rows) + the tile's dZ2 rows
+constexpr int kWgPlaneP = (kTile + 16) * 16;                 // P1 window plane: 144 rows
+constexpr int kWgStage = 2 * kWgPlaneP + 4 * 4 * kZPlane;    // + up to four shifted copies of the dZ2 planes
+static_assert(kWgStages * kWgStage + 1024 <= 232448, "weight-gradient stages fit in shared memory");
 
 __global__ void __launch_bounds__(192, 1) conv2_wgrad_kernel(const __grid_constant__ CUtensorMap tmP,
                                                              const __grid_constant__ CUtensorMap tmZ, const WgArgs a) {
@@ -570,7 +578,7 @@ __global__ void __launch_bounds__(192, 1) conv2_wgrad_kernel(const __grid_consta
         *abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == 1) tmem_alloc(tslot, 256);   // 8 accumulators of 32 columns
+    if (warp == 1) tmem_alloc(tslot, 256);   // one N = 32 nsb <= 128 accumulator per input-channel plane
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -585,12 +593,14 @@ __global__ void __launch_bounds__(192, 1) conv2_wgrad_kernel(const __grid_consta
             bool ok = true;
             while (ok && it.next(a.units, a.S, a.T)) {
                 if (!mbar_wait(empty + stage, ph ^ 1, abort_flag)) { ok = false; break; }
-                mbar_expect_tx(full + stage, (uint32_t)kWgStage);
+                mbar_expect_tx(full + stage, (uint32_t)(2 * kWgPlaneP + a.nsb * 4 * kZPlane));
                 uint8_t* st = stages + stage * kWgStage;
                 const int y = (int)(it.t * kTile);
-                for (int cb = 0; cb < 2; ++cb) tma_load_3d(st + cb * kPlane, &tmP, 0, y, 2 * it.j + cb, full + stage);
-                for (int cb = 0; cb < 4; ++cb)
-                    tma_load_3d(st + 2 * kPlane + cb * kZPlane, &tmZ, 0, kDzMarg + y, 4 * it.j + cb, full + stage);
+                for (int cb = 0; cb < 2; ++cb) tma_load_3d(st + cb * kWgPlaneP, &tmP, 0, y, 2 * it.j + cb, full + stage);
+                for (int i = 0; i < a.nsb; ++i)
+                    for (int cb = 0; cb < 4; ++cb)
+                        tma_load_3d(st + 2 * kWgPlaneP + (i * 4 + cb) * kZPlane, &tmZ, 0, kDzMarg + y - 16 * i,
+                                    4 * it.j + cb, full + stage);
                 if (++stage == kWgStages) { stage = 0; ph ^= 1; }
             }
             if (!ok) role_abort(abort_flag, a.err, ERR_WG, true);
@@ -598,7 +608,7 @@ __global__ void __launch_bounds__(192, 1) conv2_wgrad_kernel(const __grid_consta
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t ID = idesc_bf16(128, 32) | (1u << 15) | (1u << 16);   // A and B MN-major
+            const uint32_t ID = idesc_bf16(128, 32 * a.nsb) | (1u << 15) | (1u << 16);   // A and B MN-major
             TileIter it;
             it.init();
             int stage = 0, units_seen = 0;
@@ -614,15 +624,16 @@ __global__ void __launch_bounds__(192, 1) conv2_wgrad_kernel(const __grid_consta
                 if (!mbar_wait(full + stage, ph, abort_flag)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t sp = su32(stages + stage * kWgStage);
-                const uint32_t sz = sp + 2 * kPlane;
+                const uint32_t sz = sp + 2 * kWgPlaneP;
 #pragma unroll 1
                 for (int ks = 0; ks < kTile / 16; ++ks) {
                     const uint32_t acc_on = (it.fresh && ks == 0) ? 0u : 1u;
+                    // B: N groups (copy i, output-channel plane) 2 KB apart
                     const uint64_t bd = sdesc_ns(sz + ks * 256, 128, kZPlane);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {   // plane q / 4, shifts 16 (q % 4) .. + 15
-                        const uint64_t ad = sdesc_ns(sp + (q >> 2) * kPlane + (16 * (q & 3) + 16 * ks) * 16, 128, 16);
-                        umma_bf16(tbase + (uint32_t)q * 32, ad, bd, ID, acc_on);
+                    for (int q = 0; q < 2; ++q) {   // input-channel plane q: shifts sa = 0 .. 15
+                        const uint64_t ad = sdesc_ns(sp + q * kWgPlaneP + 16 * ks * 16, 128, 16);
+                        umma_bf16(tbase + (uint32_t)q * 128, ad, bd, ID, acc_on);
                     }
                 }
                 umma_commit(empty + stage);
@@ -636,7 +647,7 @@ __global__ void __launch_bounds__(192, 1) conv2_wgrad_kernel(const __grid_consta
         __syncwarp();
     } else {
         const int wq = warp & 3;
-        const int m = wq * 32 + lane;   // accumulator row: shift block row g = m / 8, channel m % 8
+        const int m = wq * 32 + lane;   // accumulator row: shift sa = m / 8, channel m % 8
         uint32_t uph = 0;
         for (int64_t u = blockIdx.x; u < a.units; u += gridDim.x) {
             const int s = (int)(u % a.S), j = (int)(u / a.S);
@@ -650,7 +661,8 @@ __global__ void __launch_bounds__(192, 1) conv2_wgrad_kernel(const __grid_consta
                 uph ^= 1;
                 tc_fence_after();
             }
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < 8; ++q) {   // columns 32 q: plane q / 4, copy i = q % 4 (shift 16 i + sa)
+                if ((q & 3) >= a.nsb) continue;
                 uint32_t r[32];
                 __syncwarp();
                 if (!empty_unit) {
@@ -789,12 +801,15 @@ cudaError_t conv2_wgrad(smc_ctx* c, const Shape& s, int nimg, int accumulate) {
     const int64_t nvalid = (int64_t)nimg * s.NW1;
     CUtensorMap tmP, tmZ;
     // dZ2 rows past the chunk's images read as zeros (the extent ends there)
-    if (!planes_map(&tmP, b.P1, b.p1_rows, b.p1_rows, 2 * (int64_t)c->J, kPlane / 16) ||
+    if (!planes_map(&tmP, b.P1, b.p1_rows, b.p1_rows, 2 * (int64_t)c->J, kWgPlaneP / 16) ||
         !planes_map(&tmZ, b.dZ2c, kDzMarg + nvalid, b.dz_rows, 4 * (int64_t)c->J, kTile))
         return cudaErrorInvalidValue;
     const Plan pl = plan(c, nimg, s, c->num_sms, kTile);
     WgArgs a{};
     a.S = pl.S; a.k2 = s.k2; a.WP1 = s.WP1; a.K2 = s.K2;
+    // B-side shifts 0, 16, .., 16 (nsb - 1): enough for every tap, none past the
+    // trailing invalid rows (16 (nsb - 1) <= shift_max)
+    a.nsb = ((s.k2 - 1) * s.WP1 + (s.k2 - 1)) / 16 + 1;
     a.T = pl.T; a.units = pl.units; a.part = b.dW2P; a.err = c->err_dev;
     const size_t smem = 128 + (size_t)kWgStages * kWgStage + 256;
     cudaError_t e = cudaFuncSetAttribute(conv2_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
