@@ -243,42 +243,47 @@ __device__ __forceinline__ void store_box(const CUtensorMap* tm, int perm, const
 // Epilogues that stage their BF16 output tiles for TMA stores.
 __host__ __device__ constexpr bool staged_out(int epi) { return epi == EPI_BF16_ACT || epi == EPI_BF16_DACT; }
 
+// One of four values picked by a lane-dependent index without dynamic register
+// indexing.
+__device__ __forceinline__ float sel4(int x, float a, float b, float c, float d) {
+    return (x & 2) ? ((x & 1) ? d : c) : ((x & 1) ? b : a);
+}
+
 // EPI_BF16_POOL on one 32-column group: lanes 4w' .. 4w' + 3 of a warp hold the
 // four rows of pooling window w' (r: this lane's 32 FP32 accumulators, n8 of
-// its four 8-column pieces in use).  act is increasing and one bias is shared
-// by a column's four rows, so the window's maximum is taken on the
-// accumulators (a butterfly over the four lanes) and its index is the first
-// row that attains it; lane 4w' + q then finishes piece q alone: bias, act,
-// BF16, one 16-byte store into the piece's plane and 8 index bytes.
+// its four 8-column pieces in use), and lane 4w' + q finishes piece q.  act is
+// increasing and one bias is shared by a column's four rows, so the window's
+// maximum is taken on the accumulators: in round k = 1, 2, 3 the lane receives
+// row (q ^ k)'s eight values of its piece from lane 4w' + (q ^ k) (which sends
+// its own values of piece q ^ k ^ k = q), and keeps the maximum with the first
+// row attaining it.  Then bias, act, BF16, one 16-byte store into the piece's
+// plane and 8 index bytes.
 template <int ACT>
 __device__ __forceinline__ void pool_group(const GArgs& g, int b, int row0, int col0, int n8, const uint32_t* r) {
     const int lane = threadIdx.x & 31, d = lane & 3;
-    float mx[32];
-    uint32_t mask = 0;
+    float rv[32];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
-        const float own = c < 8 * n8 ? __uint_as_float(r[c]) : 0.0f;   // pieces past n8 were not loaded
-        float v = own;
-        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 1));
-        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 2));
-        mx[c] = v;
-        mask |= (own == v ? 1u : 0u) << c;
+    for (int c = 0; c < 32; ++c) rv[c] = c < 8 * n8 ? __uint_as_float(r[c]) : 0.0f;   // unloaded pieces: 0
+    float bv[8];
+    int bi8[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        bv[e] = sel4(d, rv[e], rv[8 + e], rv[16 + e], rv[24 + e]);
+        bi8[e] = d;
     }
-    uint32_t mk[4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) mk[e] = __shfl_sync(0xffffffffu, mask, (lane & ~3) + e);
+    for (int k = 1; k < 4; ++k) {
+        const int src = d ^ k;   // the row whose values arrive in this round
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const float send = sel4(src, rv[e], rv[8 + e], rv[16 + e], rv[24 + e]);
+            const float v = __shfl_xor_sync(0xffffffffu, send, k);
+            if (v > bv[e] || (v == bv[e] && src < bi8[e])) { bv[e] = v; bi8[e] = src; }
+        }
+    }
     const int win_row = row0 + (lane & ~3);   // first row of this lane's window
     const int col = col0 + 8 * d;
     if (d >= n8 || win_row >= g.M || col >= g.N) return;
-    float v8[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) v8[e] = mx[e];
-#pragma unroll
-    for (int q = 1; q < 4; ++q)
-        if (d == q) {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) v8[e] = mx[8 * q + e];
-        }
     const float* bp = g.bias + (int64_t)b * g.bias_bstride + col;
     const float4 b0 = *reinterpret_cast<const float4*>(bp);
     const float4 b1 = *reinterpret_cast<const float4*>(bp + 4);
@@ -287,10 +292,8 @@ __device__ __forceinline__ void pool_group(const GArgs& g, int b, int row0, int 
     __align__(8) uint8_t bi[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-        const int bit = 8 * d + e;
-        const int first = ((mk[0] >> bit) & 1u) ? 0 : ((mk[1] >> bit) & 1u) ? 1 : ((mk[2] >> bit) & 1u) ? 2 : 3;
-        best[e] = __float2bfloat16_rn(act_fwd<ACT>(v8[e] + bb[e]));
-        bi[e] = (uint8_t)first;
+        best[e] = __float2bfloat16_rn(act_fwd<ACT>(bv[e] + bb[e]));
+        bi[e] = (uint8_t)bi8[e];
     }
     const int64_t win = win_row >> 2;
     *reinterpret_cast<uint4*>(g.pool_out + ((int64_t)(col >> 3) * g.pool_rows + win) * 8) =
