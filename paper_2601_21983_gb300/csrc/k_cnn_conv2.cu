@@ -701,7 +701,8 @@ __global__ void __launch_bounds__(192, 1) conv2_wgrad_kernel(const __grid_consta
 
 // gW2 [J][C2][C1 taps] (+)= the sum over splits (in order) of the partials
 // [J][S][K2][C2] (rows tap * C1 + channel); gb2 [J][C2] (+)= the sum over the
-// chunk's images (in order) of the per-image partials db2part [J][B][C2].
+// chunk's images of the per-image partials db2part [J][B][C2] (eight
+// interleaved sums in a fixed order).
 __global__ void conv2_wgrad_reduce_kernel(const float* __restrict__ part, const float* __restrict__ db2part, int J,
                                           int S, int B, int nimg, int C1, int C2, int taps, int accumulate,
                                           float* __restrict__ gW2, float* __restrict__ gb2) {
@@ -713,7 +714,19 @@ __global__ void conv2_wgrad_reduce_kernel(const float* __restrict__ part, const 
     const int co = e / (K2 + 1), k = e % (K2 + 1);   // k = channel * taps + tap, or K2 for db2
     float v = 0.0f;
     if (k == K2) {
-        for (int i = 0; i < nimg; ++i) v += db2part[((int64_t)j * B + i) * C2 + co];
+        // eight interleaved partial sums (images i = r mod 8), combined in order
+        float p8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const float* src = db2part + (int64_t)j * B * C2 + co;
+        int i = 0;
+        for (; i + 8 <= nimg; i += 8) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) p8[q] += src[(int64_t)(i + q) * C2];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (i + q < nimg) p8[q] += src[(int64_t)(i + q) * C2];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v += p8[q];
     } else {
         const int row = (k % taps) * C1 + k / taps;
         for (int s = 0; s < S; ++s) v += part[(((int64_t)j * S + s) * K2 + row) * C2 + co];
