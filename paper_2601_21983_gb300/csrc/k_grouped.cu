@@ -253,7 +253,7 @@ __device__ __forceinline__ float sel4(int x, float a, float b, float c, float d)
 // four rows of pooling window w' (r: this lane's 32 FP32 accumulators, n8 of
 // its four 8-column pieces in use), and lane 4w' + q finishes piece q.  act is
 // increasing and one bias is shared by a column's four rows, so the window's
-// maximum is taken on the accumulators: in round k = 1, 2, 3 the lane receives
+// maximum is taken on the accumulators: in exchange step k = 1, 2, 3 the lane receives
 // row (q ^ k)'s eight values of its piece from lane 4w' + (q ^ k) (which sends
 // its own values of piece q ^ k ^ k = q), and keeps the maximum with the first
 // row attaining it.  Then bias, act, BF16, one 16-byte store into the piece's
@@ -273,7 +273,7 @@ __device__ __forceinline__ void pool_group(const GArgs& g, int b, int row0, int 
     }
 #pragma unroll
     for (int k = 1; k < 4; ++k) {
-        const int src = d ^ k;   // the row whose values arrive in this round
+        const int src = d ^ k;   // the row whose values arrive in this exchange step
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const float send = sel4(src, rv[e], rv[8 + e], rv[16 + e], rv[24 + e]);
