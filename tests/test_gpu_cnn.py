@@ -16,7 +16,16 @@ blocks are bounded at 5e-2.  The
 whole gradient's bound follows from the blocks' bounds: with e_b <= t_b for
 every block b, the norm-wise error of the whole is at most
 sqrt(sum_b t_b^2 |g_b|^2) / |g|, which is 2e-2 when the dense blocks carry the
-norm and approaches 5e-2 when the convolution blocks do (1-channel images)."""
+norm and approaches 5e-2 when the convolution blocks do (1-channel images).
+
+The engine rounds images and particles to BF16 on entry; about a third of
+the convolution blocks' error above is that rounding.  The evaluation check
+of the configuration's network therefore also runs on images and particles
+that are BF16 values already (the same arrays for both sides), and there
+every block, the convolution blocks included, is held to 2e-2 (measured
+1.2-1.6%).  With one input channel or a handful of images the cancellation
+alone leaves the convolution blocks at 2-3% even then, so those checks keep
+the bounds above."""
 import numpy as np
 import pytest
 
@@ -40,6 +49,13 @@ CNN28 = nn.Spec([("conv", 1, 16, 5), ("pool2",), ("conv", 16, 32, 5), ("pool2",)
 BLOCKS28 = [(16, 1, 5, 5), (16,), (32, 16, 5, 5), (32,), (10, 512), (10,)]
 
 
+def _bf16(a):
+    """a rounded to the nearest BF16 value (ties to even), kept in float32."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return u.view(np.float32)
+
+
 def _per_particle_rel(a, b):
     return max(rel_err(a[j], b[j]) for j in range(a.shape[0]))
 
@@ -60,7 +76,7 @@ def _whole_bound(rg, blocks):
     return np.array(out)
 
 
-def _check_eval(ctx, orc, J, spec=CNN2, blocks=BLOCKS):
+def _check_eval(ctx, orc, J, spec=CNN2, blocks=BLOCKS, exact_inputs=False):
     lp, g, la, lb = S.smc_eval(ctx, J, spec.n_params)
     rlp, rg, rla, rlb = oracle_eval(orc)
     scale = np.abs(rla) + np.abs(rlb)
@@ -72,31 +88,35 @@ def _check_eval(ctx, orc, J, spec=CNN2, blocks=BLOCKS):
         n = int(np.prod(shp))
         errs.append(_per_particle_rel(g[:, off:off + n], rg[:, off:off + n]))
         off += n
-    bound = np.maximum(_whole_bound(rg, blocks), TOL)
+    bound = np.full(J, TOL) if exact_inputs else np.maximum(_whole_bound(rg, blocks), TOL)
     whole = np.array([rel_err(g[j], rg[j]) for j in range(J)])
     print("block errors", [f"{e:.2e}" for e in errs], "whole", f"{whole.max():.2e}", "bound", f"{bound.min():.2e}")
-    for shp, e, tol in zip(blocks, errs, BLOCK_TOL):
+    for shp, e, tol in zip(blocks, errs, [TOL] * len(blocks) if exact_inputs else BLOCK_TOL):
         assert e < tol, (shp, e)
     assert np.all(whole < bound), (whole, bound)
     return lp, g
 
 
+@pytest.mark.parametrize("exact", [False, True])
 @pytest.mark.parametrize("chunk", [0, 40])
-def test_bf16_cnn_eval_parity(chunk):
+def test_bf16_cnn_eval_parity(chunk, exact):
     """log pi, region sums and the gradient of every parameter block at prior-
-    scale particles, whole subset and in chunks of 40 images (ragged tail)."""
+    scale particles, whole subset and in chunks of 40 images (ragged tail);
+    exact: images and particles that are BF16 values."""
     N, J = 96, 4
     X, y = synthetic.smooth_field_images(N, seed=71)
+    X = _bf16(X) if exact else X
     ctx, orc, _ = make_pair(CNN2, X, y, J, seed=71, precision=S.PREC_BF16, chunk=chunk)
     try:
         th0 = synthetic.particles(J, CNN2.n_params, 71, std=0.1)
+        th0 = _bf16(th0) if exact else th0
         S.smc_set_state(ctx, th0)
         S.smc_set_schedule(ctx, S.make_schedule("linear", 48, 48, 10))
         orc.set_schedule("linear", 48, 48, 10, th0)
-        _check_eval(ctx, orc, J)
+        _check_eval(ctx, orc, J, exact_inputs=exact)
         S.smc_anneal_next(ctx)
         orc.anneal_next()
-        _check_eval(ctx, orc, J)
+        _check_eval(ctx, orc, J, exact_inputs=exact)
     finally:
         S.smc_destroy(ctx)
 
