@@ -560,11 +560,13 @@ def run_eval_config(args):
                                  "flop_per_unit": flop, "precision": "fp32"}}), flush=True)
 
 
-def tta_compare(J, n, K, seeds, every=4, explore_iters=30):
+def tta_compare(J, n, K, seeds, every=4, explore_iters=15, explore_rounds=2):
     """Time to test accuracy, learned vs plain proposal (configuration c3).
 
     The proposal network is trained on exploratory trajectories of the same
-    setup with other seeds (100-102); then, for each seed, both proposals run
+    setup with other seeds (100, 101, ...: `explore_rounds` runs of
+    `explore_iters` iterations each, the network trained after each run on
+    everything collected so far); then, for each seed, both proposals run
     the same Linear-DA schedule (C = kappa = 1000, K iterations, HMC S = 3)
     from that seed.  The clock runs over the sampler iterations
     (GPU-synchronous; the test-set evaluations every `every` iterations are
@@ -592,7 +594,7 @@ def tta_compare(J, n, K, seeds, every=4, explore_iters=30):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     trainer = new_ctx(100)
-    for rnd, seed in enumerate([100, 101, 102]):
+    for rnd, seed in enumerate(range(100, 100 + explore_rounds)):
         ctx = trainer if rnd == 0 else new_ctx(seed)
         if rnd > 0:
             S.smc_learned_params(ctx, S.smc_learned_params(trainer))
@@ -659,7 +661,9 @@ def tta_compare(J, n, K, seeds, every=4, explore_iters=30):
     return {"metric": "time-to-test-acc, learned vs plain proposal", "unit": "s", "higher_is_better": False,
             "value": med("learned_s"), "plain_value": med("plain_s"), "speedup": med("speedup"),
             "speedup_with_training": med("speedup_with_training"), "train_seconds": train_s,
-            "train_rows": train_rows, "seeds": per_seed,
+            "train_rows": train_rows, "train_budget": {"rounds": explore_rounds, "explore_iters": explore_iters,
+                                                        "adam_epochs_per_round": 300},
+            "seeds": per_seed,
             "config": {"workload": f"c3: MLP {DIN}-{H}-{NCLS} ReLU, J={J}, {n} synthetic images, Linear DA "
                                    f"(C=kappa={MB}, K={K}), HMC S={S_LF}, h={STEP_H}, BF16, seeds {list(seeds)}",
                        "test_rows": 10000, "eval_every": every,
@@ -668,7 +672,7 @@ def tta_compare(J, n, K, seeds, every=4, explore_iters=30):
 
 def run_tta(args):
     print(json.dumps(tta_compare(args.J, args.n, args.tta_iters, list(range(args.tta_seeds)), args.tta_every,
-                                 args.tta_explore)), flush=True)
+                                 args.tta_explore, args.tta_rounds)), flush=True)
 
 
 def run_grid(args):
@@ -767,7 +771,8 @@ def main():
     ap.add_argument("--cnn-steps", type=int, default=3)
     ap.add_argument("--cnn-J", type=int, default=CNN_J, help="particles of the CNN section (profiling runs)")
     ap.add_argument("--cnn-n", type=int, default=CNN_N, help="images of the CNN section (profiling runs)")
-    ap.add_argument("--tta-explore", type=int, default=30)
+    ap.add_argument("--tta-explore", type=int, default=15, help="exploratory iterations per training run")
+    ap.add_argument("--tta-rounds", type=int, default=2, help="exploratory training runs (seeds 100, 101, ...)")
     ap.add_argument("--tta-every", type=int, default=4)
     if len(sys.argv) >= 6 and sys.argv[1] == "--oracle-worker":
         sec, j_s, m_s, seed = float(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]), int(sys.argv[5])
@@ -991,7 +996,7 @@ def main():
             line["cnn_config"] = run_cnn_config(args.cnn_steps, max(3, args.warmup), cpu=not args.no_cpu_baseline)
         if world == 1 and not args.no_tta:
             line["tta"] = tta_compare(args.J, args.n, args.tta_iters, list(range(args.tta_seeds)), args.tta_every,
-                                      args.tta_explore)
+                                      args.tta_explore, args.tta_rounds)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
