@@ -13,9 +13,22 @@ A model is a `Spec`: a list of layers
     ("dense", n_in, n_out)      z = a W^T + b,  W [n_out, n_in]
     ("conv", c_in, c_out, k)    valid k x k cross-correlation, stride 1, W [c_out, c_in, k, k]
     ("pool2",)                  2x2 max pool, stride 2 (first maximum wins ties)
-An activation follows every parametric layer except the last.  The parameter
+    ("bnorm", c)                per-channel scale and shift  z = gamma_c a + beta_c
+                                (W = gamma [c], b = beta [c]) on a [c, h, w] map or a
+                                [c] vector
+An activation follows every parametric layer except the last and except a
+layer whose successor is a "bnorm" layer (conv -> bnorm -> activation, the
+convolution-batchnorm blocks of Sec. 4's FashionMNIST network).  The parameter
 vector of one particle lists, layer by layer, W (row-major) then b.  A dense
 layer after a conv/pool layer reads the feature map flattened in (c, h, w) order.
+
+Reading of Sec. 4's batchnorm: batch normalisation in its inference form,
+with fixed statistics (mean 0, variance 1), so the layer is the per-channel
+affine map above and gamma, beta are parameters of the particle like any
+other.  Statistics taken over the evaluated rows would make each row's
+log-likelihood depend on the other rows of D_k, while eq. approx-grad scales a
+subset's sum of per-row terms by N / M_k as an estimate of the full-data sum,
+which needs each term to depend on its own row only.
 
 The Gaussian likelihood log N(y; z, s^2) with one linear layer is the
 linear-Gaussian model used to pin the sampler against a closed-form posterior.
@@ -56,11 +69,22 @@ class Spec:
             elif layer[0] == "pool2":
                 self.shapes.append([])
                 shp = (shp[0], shp[1] // 2, shp[2] // 2)
+            elif layer[0] == "bnorm":
+                assert shp[0] == layer[1], (shp, layer)
+                self.shapes.append([(layer[1],), (layer[1],)])
             else:
                 raise ValueError(layer)
         self.out_dim = int(np.prod(shp))
         self.n_params = sum(int(np.prod(s)) for ps in self.shapes for s in ps)
         self.last_param = max(i for i, l in enumerate(self.layers) if l[0] != "pool2")
+
+    def activation_of(self, li):
+        """Activation applied to layer li's output (parametric layers only)."""
+        if li == self.last_param:
+            return IDENTITY
+        if li + 1 < len(self.layers) and self.layers[li + 1][0] == "bnorm":
+            return IDENTITY
+        return self.activation
 
     def unpack(self, theta):
         """Views of (W, b) per layer into a flat parameter vector."""
@@ -144,13 +168,18 @@ def forward(spec: Spec, theta, X):
             a_in = a
             W, b = params[li]
             z = _conv(a_in, W, b)
+        elif layer[0] == "bnorm":
+            a_in = a
+            g, b = params[li]
+            shape = (1, -1) + (1,) * (a_in.ndim - 2)
+            z = g.reshape(shape) * a_in + b.reshape(shape)
         else:
             a_in = a
             z, idx = _pool(a_in)
             cache.append(("pool2", a_in.shape, idx))
             a = z
             continue
-        act = spec.activation if li != spec.last_param else IDENTITY
+        act = spec.activation_of(li)
         cache.append((layer[0], a_in, z, act))
         a = _act(act, z)
     return a.reshape(M, -1), cache
@@ -197,6 +226,10 @@ def loglik_grad(spec: Spec, theta, X, y, coef):
         if kind == "dense":
             grads[li] = (dzl.T @ a_in, dzl.sum(axis=0))
             da = dzl @ W
+        elif kind == "bnorm":
+            axes = (0,) + tuple(range(2, dzl.ndim))
+            grads[li] = ((dzl * a_in).sum(axis=axes), dzl.sum(axis=axes))
+            da = dzl * W.reshape((1, -1) + (1,) * (dzl.ndim - 2))
         else:
             da, dW, db = _conv_backward(a_in, W, dzl)
             grads[li] = (dW, db)

@@ -122,3 +122,108 @@ def test_gradient_zero_at_closed_form_mode():
     theta = np.concatenate([mu, [0.0]])          # bias fixed at 0: use the W-part only
     _, g = nn.loglik_grad(spec, theta, X, y, np.ones(30))
     assert np.allclose(g[:3] - mu, 0.0, atol=1e-10)
+
+
+# ---- per-channel batchnorm layer (Sec. 4's convolution-batchnorm blocks, in
+# their inference form: z = gamma_c a + beta_c)
+
+BN_SPEC = [("conv", 2, 3, 3), ("bnorm", 3), ("pool2",), ("conv", 3, 4, 2), ("bnorm", 4), ("dense", 4 * 2 * 2, 5),
+           ("bnorm", 5), ("dense", 5, 3)]
+
+
+def test_fd_batchnorm_cnn():
+    spec = nn.Spec(BN_SPEC, (2, 8, 8), nn.TANH)
+    rng = np.random.default_rng(11)
+    X, y = rng.uniform(size=(4, 2 * 8 * 8)), rng.integers(0, 3, 4)
+    _fd_check(spec, rng.normal(size=spec.n_params), X, y, rng.uniform(0.5, 2.0, 4))
+
+
+def _fold(spec_bn, theta):
+    """The same network without its bnorm layers: each bnorm folded into the
+    layer before it (W' = gamma W, b' = gamma b + beta, gamma per output channel)."""
+    P = spec_bn.unpack(theta)
+    layers, flat = [], []
+    for li, layer in enumerate(spec_bn.layers):
+        if layer[0] == "bnorm":
+            continue
+        if layer[0] == "pool2":
+            layers.append(layer)
+            continue
+        W, b = P[li]
+        if li + 1 < len(spec_bn.layers) and spec_bn.layers[li + 1][0] == "bnorm":
+            g, beta = P[li + 1]
+            W = W * g.reshape((-1,) + (1,) * (W.ndim - 1))
+            b = g * b + beta
+        layers.append(layer)
+        flat += [W.ravel(), b.ravel()]
+    return layers, np.concatenate(flat)
+
+
+def test_batchnorm_folds_into_the_layer_before():
+    # forward: a bnorm network equals the bnorm-free network with folded parameters
+    # (this pins where the activation goes: after the bnorm, not after the conv)
+    spec = nn.Spec(BN_SPEC, (2, 8, 8), nn.TANH)
+    rng = np.random.default_rng(12)
+    X, y = rng.uniform(size=(5, 2 * 8 * 8)), rng.integers(0, 3, 5)
+    theta = rng.normal(size=spec.n_params)
+    layers, theta_f = _fold(spec, theta)
+    spec_f = nn.Spec(layers, (2, 8, 8), nn.TANH)
+    z, _ = nn.forward(spec, theta, X)
+    zf, _ = nn.forward(spec_f, theta_f, X)
+    np.testing.assert_allclose(z, zf, rtol=1e-12, atol=1e-12)
+    # backward, by the chain rule through the fold: dL/dW = gamma dL/dW',
+    # dL/db = gamma dL/db', dL/dbeta = dL/db', dL/dgamma = <dL/dW', W> + dL/db' b
+    coef = rng.uniform(0.5, 2.0, 5)
+    _, g = nn.loglik_grad(spec, theta, X, y, coef)
+    _, gf = nn.loglik_grad(spec_f, theta_f, X, y, coef)
+    Gf = spec_f.unpack(gf)
+    P, G = spec.unpack(theta), spec.unpack(g)
+    fi = 0
+    for li, layer in enumerate(spec.layers):
+        if layer[0] in ("bnorm", "pool2"):
+            if layer[0] == "pool2":
+                fi += 1
+            continue
+        dWf, dbf = Gf[fi]
+        fi += 1
+        W, b = P[li]
+        if li + 1 < len(spec.layers) and spec.layers[li + 1][0] == "bnorm":
+            gam, _ = P[li + 1]
+            cshape = (-1,) + (1,) * (W.ndim - 1)
+            np.testing.assert_allclose(G[li][0], gam.reshape(cshape) * dWf, rtol=1e-10, atol=1e-12)
+            np.testing.assert_allclose(G[li][1], gam * dbf, rtol=1e-10, atol=1e-12)
+            np.testing.assert_allclose(G[li + 1][1], dbf, rtol=1e-10, atol=1e-12)
+            dgam = (dWf * W).reshape(W.shape[0], -1).sum(axis=1) + dbf * b
+            np.testing.assert_allclose(G[li + 1][0], dgam, rtol=1e-10, atol=1e-12)
+        else:
+            np.testing.assert_allclose(G[li][0], dWf, rtol=1e-10, atol=1e-12)
+            np.testing.assert_allclose(G[li][1], dbf, rtol=1e-10, atol=1e-12)
+
+
+def test_unit_batchnorm_is_the_network_without_it():
+    # gamma = 1, beta = 0: the layer is the identity and the activation moves past it
+    spec = nn.Spec(BN_SPEC, (2, 8, 8), nn.TANH)
+    layers = [l for l in BN_SPEC if l[0] != "bnorm"]
+    spec_f = nn.Spec(layers, (2, 8, 8), nn.TANH)
+    rng = np.random.default_rng(13)
+    theta_f = rng.normal(size=spec_f.n_params)
+    parts, k = [], 0
+    for li, layer in enumerate(BN_SPEC):
+        if layer[0] == "bnorm":
+            parts += [np.ones(layer[1]), np.zeros(layer[1])]
+        elif layer[0] != "pool2":
+            n = sum(int(np.prod(s)) for s in spec.shapes[li])
+            parts.append(theta_f[k:k + n])
+            k += n
+    theta = np.concatenate(parts)
+    X = rng.uniform(size=(3, 2 * 8 * 8))
+    np.testing.assert_array_equal(nn.forward(spec, theta, X)[0], nn.forward(spec_f, theta_f, X)[0])
+
+
+def test_fashion_cnn_parameter_count():
+    # Sec. 4's FashionMNIST network: two convolution-batchnorm-pool blocks, two dense
+    # layers, D = 96,658 (the layout is this build's reading: 3x3 kernels, 8 and 16
+    # channels, 232 hidden units)
+    spec = nn.Spec([("conv", 1, 8, 3), ("bnorm", 8), ("pool2",), ("conv", 8, 16, 3), ("bnorm", 16), ("pool2",),
+                    ("dense", 16 * 5 * 5, 232), ("dense", 232, 10)], (1, 28, 28), nn.TANH)
+    assert spec.n_params == 96658
