@@ -516,13 +516,19 @@ EVAL_CONFIGS = {
             "tanh", 128, 4096, 1024, 11.49e6, "smooth_field_images"),
     "mlp4": ([("dense", 784, 400), ("dense", 400, 400), ("dense", 400, 10)], (784,), "relu", 1024, 2048, 512,
              2.238e6, "template_images"),
+    # Sec. 4's FashionMNIST network with its batchnorm layers (D = 96,658): contractions
+    # 566,368 FLOP forward + 1,035,392 backward (the first layer has no data gradient)
+    "fashion_bn": ([("conv", 1, 8, 3), ("bnorm", 8), ("pool2",), ("conv", 8, 16, 3), ("bnorm", 16), ("pool2",),
+                    ("dense", 400, 232), ("dense", 232, 10)], (1, 28, 28), "tanh", 128, 4096, 1024, 1.60176e6,
+                   "template_images"),
 }
 
 
 def run_eval_config(args):
     """Gradient-evaluation throughput of the FP32 engine's other configurations:
-    the 3x32x32 CNN (conv5x5 3-16, pool, conv5x5 16-32, pool, fc 10; J = 128)
-    and the MLP 784-400-400-10 (J = 1024).  Each evaluation is log pi and its
+    the 3x32x32 CNN (conv5x5 3-16, pool, conv5x5 16-32, pool, fc 10; J = 128),
+    the MLP 784-400-400-10 (J = 1024) and Sec. 4's FashionMNIST network with
+    batchnorm (J = 128).  Each evaluation is log pi and its
     full gradient for every particle over the rows (smc_eval_device), timed
     with CUDA events after one warm-up evaluation."""
     import torch

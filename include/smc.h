@@ -53,7 +53,7 @@ typedef enum {
     SMC_EUNSUPPORTED = 7   /* valid request this library does not implement */
 } smc_status;
 
-enum { SMC_LAYER_DENSE = 0, SMC_LAYER_CONV = 1, SMC_LAYER_MAXPOOL2 = 2 };
+enum { SMC_LAYER_DENSE = 0, SMC_LAYER_CONV = 1, SMC_LAYER_MAXPOOL2 = 2, SMC_LAYER_BNORM = 3 };
 enum { SMC_ACT_TANH = 0, SMC_ACT_RELU = 1, SMC_ACT_IDENTITY = 2 };
 enum { SMC_LIK_CATEGORICAL = 0, SMC_LIK_GAUSSIAN = 1 };
 enum { SMC_PREC_FP32 = 0, SMC_PREC_BF16 = 1 };
@@ -73,9 +73,15 @@ enum { SMC_PROPOSAL_PLAIN = 0, SMC_PROPOSAL_LEARNED = 1, SMC_PROPOSAL_EXPLORE = 
 
 /* One layer.  DENSE: n_in -> n_out.  CONV: valid ksize x ksize cross-correlation,
  * stride 1, n_in = c_in channels -> n_out = c_out channels.  MAXPOOL2: 2x2 max
- * pool with stride 2 (n_in, n_out, ksize ignored).  An activation follows every
- * parametric layer except the last; the last layer's outputs are the logits
- * (categorical likelihood) or the mean (Gaussian likelihood, n_out = 1). */
+ * pool with stride 2 (n_in, n_out, ksize ignored).  BNORM: the batch
+ * normalisation of Sec. 4's convolution-batchnorm blocks in its inference form
+ * (fixed statistics): z = gamma_c a + beta_c per channel c of the input map (or
+ * per feature after a dense layer), n_in = n_out = that channel count, its W
+ * segment gamma [c] and its b segment beta [c]; FP32 engine only.  An
+ * activation follows every parametric layer except the last and except a layer
+ * followed by a BNORM layer (conv -> bnorm -> activation); the last layer
+ * (dense or conv) gives the logits (categorical likelihood) or the mean
+ * (Gaussian likelihood, n_out = 1). */
 typedef struct { int32_t kind, n_in, n_out, ksize; } smc_layer;
 
 typedef struct {

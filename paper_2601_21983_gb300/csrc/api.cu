@@ -296,7 +296,8 @@ smc_status smc_init(const smc_model* model, const smc_data* train, const smc_con
     int last_param = -1;
     for (int l = 0; l < model->n_layers; ++l)
         if (model->layers[l].kind != SMC_LAYER_MAXPOOL2) last_param = l;
-    if (last_param != model->n_layers - 1) return bad("the last layer must be dense or conv");
+    if (last_param != model->n_layers - 1 || model->layers[last_param].kind == SMC_LAYER_BNORM)
+        return bad("the last layer must be dense or conv");
     int64_t canon = 0, off = 0;
     for (int l = 0; l < model->n_layers; ++l) {
         const smc_layer& m = model->layers[l];
@@ -320,10 +321,21 @@ smc_status smc_init(const smc_model* model, const smc_data* train, const smc_con
         } else if (m.kind == SMC_LAYER_MAXPOOL2) {
             if (hh < 2 || ww < 2) return bad("pool input too small");
             L.out_c = cc; L.out_h = hh / 2; L.out_w = ww / 2;
+        } else if (m.kind == SMC_LAYER_BNORM) {
+            // Sec. 4's batchnorm in inference form: gamma [c] (W segment), beta [c] (b segment)
+            if (m.n_in != cc || m.n_out != cc) return bad("bnorm layer: n_in = n_out = input channels");
+            if (l == 0 || model->layers[l - 1].kind == SMC_LAYER_MAXPOOL2 ||
+                model->layers[l - 1].kind == SMC_LAYER_BNORM)
+                return bad("a bnorm layer follows a dense or conv layer");
+            L.out_c = cc; L.out_h = hh; L.out_w = ww;
+            wsz = cc;
+            bsz = cc;
         } else {
             return bad("unknown layer kind");
         }
-        L.act = (m.kind == SMC_LAYER_MAXPOOL2 || l == last_param) ? SMC_ACT_IDENTITY : model->activation;
+        const bool to_bnorm = l + 1 < model->n_layers && model->layers[l + 1].kind == SMC_LAYER_BNORM;
+        L.act = (m.kind == SMC_LAYER_MAXPOOL2 || l == last_param || to_bnorm) ? SMC_ACT_IDENTITY
+                                                                             : model->activation;
         if (wsz > 0) {
             L.seg_w = (int)c->segs.size();
             c->segs.push_back({wsz, off, canon});

@@ -516,6 +516,67 @@ __global__ void pool_bwd_kernel(const float* __restrict__ dout, const uint8_t* _
         }
 }
 
+// ------------------------------------------------------------- batchnorm
+// Sec. 4's batchnorm in inference form: a per-channel scale and shift with
+// fixed statistics.  Feature e of a row lies in channel (e / hw) % C, hw the
+// positions of the map (1 after a dense layer).  One thread per element of
+// particle blockIdx.y; per = rows x C x hw (below 2^31 per particle).
+// out(j,m,c,p) = act(gamma(j,c) in(j,m,c,p) + beta(j,c))
+__global__ void bnorm_fwd_kernel(const float* __restrict__ in, int64_t in_sj, const float* __restrict__ gamma,
+                                 const float* __restrict__ beta, int64_t g_sj, float* __restrict__ out,
+                                 int64_t out_sj, int per, int C, int hw, int act) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= per) return;
+    const int j = blockIdx.y;
+    const int ch = (e / hw) % C;
+    out[j * out_sj + e] = act_f(act, gamma[j * g_sj + ch] * in[j * in_sj + e] + beta[j * g_sj + ch]);
+}
+
+// dgamma(j,c) += sum_{m,p} dz(j,m,c,p) in(j,m,c,p),  dbeta(j,c) += sum_{m,p} dz(j,m,c,p);
+// one 256-thread block per (c, j), sums in a fixed order.
+__global__ void __launch_bounds__(256) bnorm_bwd_param_kernel(const float* __restrict__ dz, int64_t dz_sj,
+                                                              const float* __restrict__ in, int64_t in_sj,
+                                                              float* __restrict__ dgamma, float* __restrict__ dbeta,
+                                                              int64_t g_sj, int rows, int C, int hw) {
+    __shared__ float rg[256], rb[256];
+    const int j = blockIdx.y, ch = blockIdx.x;
+    float sg = 0.0f, sb = 0.0f;
+    const int64_t npos = (int64_t)rows * hw;
+    for (int64_t p = threadIdx.x; p < npos; p += blockDim.x) {
+        const int64_t m = p / hw, yx = p % hw;
+        const int64_t e = (m * C + ch) * hw + yx;
+        const float d = dz[j * dz_sj + e];
+        sg += d * in[j * in_sj + e];
+        sb += d;
+    }
+    rg[threadIdx.x] = sg;
+    rb[threadIdx.x] = sb;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) {
+            rg[threadIdx.x] += rg[threadIdx.x + st];
+            rb[threadIdx.x] += rb[threadIdx.x + st];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        dgamma[j * g_sj + ch] += rg[0];
+        dbeta[j * g_sj + ch] += rb[0];
+    }
+}
+
+// din(j,m,c,p) = dz(j,m,c,p) gamma(j,c) act'(T(j,m,c,p)), T the output of the
+// layer that feeds the batchnorm (its activation tact).
+__global__ void bnorm_bwd_data_kernel(const float* __restrict__ dz, int64_t dz_sj, const float* __restrict__ gamma,
+                                      int64_t g_sj, float* __restrict__ din, const float* __restrict__ T,
+                                      int64_t in_sj, int per, int C, int hw, int tact) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= per) return;
+    const int j = blockIdx.y;
+    const int ch = (e / hw) % C;
+    din[j * in_sj + e] = dz[j * dz_sj + e] * gamma[j * g_sj + ch] * act_grad_from_out(tact, T[j * in_sj + e]);
+}
+
 // ------------------------------------------------------------------- head
 // Per (j, m): ll(j, m) = log p(y | z) and delta(j, m, :) = c_g d ll / d z, with
 // c_g = coef_a for global rows g < rows_a, else coef_b.
@@ -639,6 +700,12 @@ static cudaError_t simt_forward(smc_ctx* c, const float* x, int rows) {
             SMC_LAUNCH(c, conv_fwd_kernel<<<nblk(tot), 256, 0, c->stream>>>(
                               in, in_sj, c->theta + c->segs[L.seg_w].off, c->theta + c->segs[L.seg_b].off, out,
                               ch * L.out_feat(), rows, J, s, L.act));
+        } else if (L.kind == SMC_LAYER_BNORM) {
+            const Segment& sg = c->segs[L.seg_w];
+            const int per = (int)((int64_t)rows * L.out_feat());
+            SMC_LAUNCH(c, bnorm_fwd_kernel<<<dim3(nblk(per), J), 256, 0, c->stream>>>(
+                              in, in_sj, c->theta + sg.off, c->theta + c->segs[L.seg_b].off, sg.size, out,
+                              ch * L.out_feat(), per, L.out_c, L.out_h * L.out_w, L.act));
         } else {
             const int per = (int)((int64_t)rows * L.out_feat());
             SMC_LAUNCH(c, pool_fwd_kernel<<<dim3(nblk(per), J), 256, 0, c->stream>>>(
@@ -726,6 +793,18 @@ smc_status simt_eval(smc_ctx* c) {
                     SMC_LAUNCH(c, conv_bwd_data_kernel<<<nblk(tot), 256, 0, c->stream>>>(
                                       dcur, ch * L.out_feat(), c->theta + sw.off, dnext, c->act[l - 1],
                                       ch * L.in_feat(), rows, J, s, ta));
+                }
+            } else if (L.kind == SMC_LAYER_BNORM) {
+                const Segment& sg = c->segs[L.seg_w];
+                const Segment& sb = c->segs[L.seg_b];
+                SMC_LAUNCH(c, bnorm_bwd_param_kernel<<<dim3(L.out_c, J), 256, 0, c->stream>>>(
+                                  dcur, ch * L.out_feat(), in, in_sj, c->grad + sg.off, c->grad + sb.off, sg.size,
+                                  rows, L.out_c, L.out_h * L.out_w));
+                if (l > 0) {
+                    const int per = (int)((int64_t)rows * L.in_feat());
+                    SMC_LAUNCH(c, bnorm_bwd_data_kernel<<<dim3(nblk(per), J), 256, 0, c->stream>>>(
+                                      dcur, ch * L.out_feat(), c->theta + sg.off, sg.size, dnext, c->act[l - 1],
+                                      ch * L.in_feat(), per, L.out_c, L.out_h * L.out_w, tact));
                 }
             } else {   // pool: scatter to the argmax, times act' of the producing layer
                 const int ta = (l > 0) ? c->layers[l - 1].act : SMC_ACT_IDENTITY;

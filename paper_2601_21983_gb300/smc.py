@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsmc.so")
 
 ABI_VERSION = 1
-LAYER_DENSE, LAYER_CONV, LAYER_MAXPOOL2 = 0, 1, 2
+LAYER_DENSE, LAYER_CONV, LAYER_MAXPOOL2, LAYER_BNORM = 0, 1, 2, 3
 ACT_TANH, ACT_RELU, ACT_IDENTITY = 0, 1, 2
 LIK_CATEGORICAL, LIK_GAUSSIAN = 0, 1
 PREC_FP32, PREC_BF16 = 0, 1
@@ -240,7 +240,7 @@ def _model_dims(model):
             shp = (l.n_out, 1, 1)
         elif l.kind == LAYER_CONV:
             shp = (l.n_out, shp[1] - l.ksize + 1, shp[2] - l.ksize + 1)
-        else:
+        elif l.kind == LAYER_MAXPOOL2:
             shp = (shp[0], shp[1] // 2, shp[2] // 2)
     return model.in_c * model.in_h * model.in_w, shp[0] * shp[1] * shp[2]
 
@@ -262,15 +262,20 @@ def _check(status, where, ctx=None):
 # -------------------------------------------------------------- structs
 def make_model(layers, in_shape, activation=ACT_TANH, likelihood=LIK_CATEGORICAL, prior_sigma=1.0,
                noise_sigma=1.0):
-    """layers: list of ("dense", n_in, n_out) / ("conv", c_in, c_out, k) / ("pool2",)."""
+    """layers: list of ("dense", n_in, n_out) / ("conv", c_in, c_out, k) / ("pool2",) /
+    ("bnorm", c)."""
     arr = (smc_layer * len(layers))()
     for i, l in enumerate(layers):
         if l[0] == "dense":
             arr[i] = smc_layer(LAYER_DENSE, l[1], l[2], 0)
         elif l[0] == "conv":
             arr[i] = smc_layer(LAYER_CONV, l[1], l[2], l[3])
-        else:
+        elif l[0] == "bnorm":
+            arr[i] = smc_layer(LAYER_BNORM, l[1], l[1], 0)
+        elif l[0] == "pool2":
             arr[i] = smc_layer(LAYER_MAXPOOL2, 0, 0, 0)
+        else:
+            raise ValueError(f"make_model: unknown layer {l!r}")
     shp = tuple(in_shape) + (1,) * (3 - len(in_shape))
     m = smc_model(ABI_VERSION, len(layers), arr, shp[0], shp[1], shp[2], activation, likelihood,
                   prior_sigma, noise_sigma)

@@ -132,6 +132,8 @@ def test_init_checks_data_against_the_model(lib):
       ("dense", 84, 10)], (1, 32, 32)),
     ([("conv", 3, 4, 3), ("pool2",), ("conv", 4, 3, 3), ("dense", 12, 5)], (3, 10, 10)),
     ([("conv", 2, 3, 3), ("pool2",)], (2, 9, 7)),
+    ([("conv", 1, 8, 3), ("bnorm", 8), ("pool2",), ("conv", 8, 16, 3), ("bnorm", 16), ("pool2",),
+      ("dense", 400, 232), ("dense", 232, 10)], (1, 28, 28)),
 ])
 def test_model_dims_follow_the_layer_shape_rules(layers, shape):
     """Input and output widths the binding derives from the C model struct
