@@ -77,7 +77,9 @@ enum { SMC_PROPOSAL_PLAIN = 0, SMC_PROPOSAL_LEARNED = 1, SMC_PROPOSAL_EXPLORE = 
  * normalisation of Sec. 4's convolution-batchnorm blocks in its inference form
  * (fixed statistics): z = gamma_c a + beta_c per channel c of the input map (or
  * per feature after a dense layer), n_in = n_out = that channel count, its W
- * segment gamma [c] and its b segment beta [c]; FP32 engine only.  An
+ * segment gamma [c] and its b segment beta [c]; it must follow a dense or conv
+ * layer (SMC_EINVAL otherwise) and runs on the FP32 engine only (a BF16
+ * context refuses the model with SMC_EUNSUPPORTED).  An
  * activation follows every parametric layer except the last and except a layer
  * followed by a BNORM layer (conv -> bnorm -> activation); the last layer
  * (dense or conv) gives the logits (categorical likelihood) or the mean
