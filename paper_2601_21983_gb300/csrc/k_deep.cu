@@ -63,8 +63,10 @@ template <int KT, int NW>
 struct HeadCfg {
     static constexpr int HP = 16 * KT;              // padded hidden width
     static constexpr int HS = HP + 8;               // tile row stride (elements): conflict-free fragments
-    static constexpr int FRAG = KT * 32 * 16;       // bytes of one fragment table
-    static constexpr int SMEM = 2 * FRAG + 16 * 4 + TILE * HS * 2 + TILE * DS * 2 + (2 * NW + NW * 16) * 8;
+    // the particle's last-layer weights as one BF16 tile [16 classes][HS], read by
+    // ldmatrix as the logits' B fragments and (transposed) as dH's
+    static constexpr int WT = 16 * HS * 2;
+    static constexpr int SMEM = WT + 16 * 4 + TILE * HS * 2 + TILE * DS * 2 + (2 * NW + NW * 16) * 8;
 };
 
 // Head and adjoint of the last layer for one particle (blockIdx.y) over one
@@ -85,26 +87,20 @@ __global__ void __launch_bounds__(32 * NW, NW == 4 ? 2 : 1) deep_head_kernel(
     constexpr int HP = F::HP, HS = F::HS, NT2 = 2 * KT, MH = (KT + NW - 1) / NW;
     constexpr int NT = 32 * NW;
     extern __shared__ __align__(16) uint8_t smraw[];
-    uint4* W2F = reinterpret_cast<uint4*>(smraw);                       // logits B fragments [KT][32]
-    uint4* W2TF = W2F + KT * 32;                                         // dH B fragments [KT][32]
-    float* bs = reinterpret_cast<float*>(W2TF + KT * 32);                // [16]
+    __nv_bfloat16* Ws = reinterpret_cast<__nv_bfloat16*>(smraw);        // W [16][HS], zero padded
+    float* bs = reinterpret_cast<float*>(smraw + F::WT);                 // [16]
     __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(bs + 16);       // [TILE][HS]
     __nv_bfloat16* Dl = As + TILE * HS;                                  // [TILE][DS]
     double* red = reinterpret_cast<double*>(Dl + TILE * DS);             // [NW][2] LL sums, [NW][16] db
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, g = lane >> 2, q4 = lane & 3;
     const int j = blockIdx.y, sl = blockIdx.x;
 
-    // ---- fragment tables of this particle's W [C][H] (zero padded), bias
+    // ---- this particle's W [C][H] as a BF16 tile [16][HS] (classes past C and
+    // hidden units past H zero), bias
     const float* Wj = W + (int64_t)j * C * H;
-    auto w = [&](int c, int k) { return (c < C && k < H) ? Wj[c * H + k] : 0.0f; };
-    for (int i = t; i < KT * 32; i += NT) {
-        const int kt = i / 32, ln = i % 32, gg = ln >> 2, qq = ln & 3;
-        const int k0 = 16 * kt + 2 * qq;
-        W2F[i] = make_uint4(pack2(w(gg, k0), w(gg, k0 + 1)), pack2(w(gg, k0 + 8), w(gg, k0 + 9)),
-                            pack2(w(8 + gg, k0), w(8 + gg, k0 + 1)), pack2(w(8 + gg, k0 + 8), w(8 + gg, k0 + 9)));
-        const int n0 = 8 * (2 * kt) + gg, n1 = n0 + 8, c0 = 2 * qq;
-        W2TF[i] = make_uint4(pack2(w(c0, n0), w(c0 + 1, n0)), pack2(w(c0 + 8, n0), w(c0 + 9, n0)),
-                             pack2(w(c0, n1), w(c0 + 1, n1)), pack2(w(c0 + 8, n1), w(c0 + 9, n1)));
+    for (int i = t; i < 16 * HP; i += NT) {
+        const int cl = i / HP, k = i % HP;
+        Ws[cl * HS + k] = __float2bfloat16_rn((cl < C && k < H) ? Wj[cl * H + k] : 0.0f);
     }
     if (t < 16) bs[t] = (t < C) ? bvec[(int64_t)j * C + t] : 0.0f;
     // pad columns [H, HP) of the tile stay zero for the whole kernel
@@ -151,11 +147,12 @@ __global__ void __launch_bounds__(32 * NW, NW == 4 ? 2 : 1) deep_head_kernel(
         if (rows_w) {
 #pragma unroll
         for (int kt = 0; kt < KT; ++kt) {
-            uint32_t af[4];
+            uint32_t af[4], bf[4];
             ldsm_x4(af, Hm + (lane & 15) * HS + 16 * kt + (lane >> 4) * 8);
-            const uint4 bf = W2F[kt * 32 + lane];
-            mma16816(cz[kt & 1][0], af, bf.x, bf.y);
-            mma16816(cz[kt & 1][1], af, bf.z, bf.w);
+            // B fragments of classes 0-7 (bf[0], bf[1]) and 8-15 (bf[2], bf[3]) over k 16 kt ..
+            ldsm_x4(bf, Ws + ((lane >> 4) * 8 + (lane & 7)) * HS + 16 * kt + ((lane >> 3) & 1) * 8);
+            mma16816(cz[kt & 1][0], af, bf[0], bf[1]);
+            mma16816(cz[kt & 1][1], af, bf[2], bf[3]);
         }
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
@@ -246,12 +243,15 @@ __global__ void __launch_bounds__(32 * NW, NW == 4 ? 2 : 1) deep_head_kernel(
         if (!rows_w) continue;
 #pragma unroll
         for (int n2 = 0; n2 < NT2; n2 += 2) {
-            const uint4 bt = W2TF[(n2 >> 1) * 32 + lane];
+            // B fragments (transposed W) of hidden units 8 n2 .. 8 n2 + 7 (bt[0], bt[1]) and
+            // 8 n2 + 8 .. 8 n2 + 15 (bt[2], bt[3]) over the 16 classes
+            uint32_t bt[4];
+            ldsm_x4_t(bt, Ws + (((lane >> 3) & 1) * 8 + (lane & 7)) * HS + 8 * n2 + (lane >> 4) * 8);
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const int n = n2 + u;
                 float d[4] = {0.f, 0.f, 0.f, 0.f};
-                mma16816(d, adl, u ? bt.z : bt.x, u ? bt.w : bt.y);
+                mma16816(d, adl, bt[2 * u], bt[2 * u + 1]);
                 uint32_t* pA = reinterpret_cast<uint32_t*>(Hm + g * HS + 8 * n + 2 * q4);
                 uint32_t* pB = reinterpret_cast<uint32_t*>(Hm + (g + 8) * HS + 8 * n + 2 * q4);
                 *pA = act_bwd2<ACT>(d[0], d[1], *pA);
