@@ -12,12 +12,15 @@
 //
 // Work unit: 256 rows x one particle pair on a 2-CTA cluster.  CTA r of the pair
 // stages the 128 rows of m-tile 2 q + r and the first-layer rows of particle
-// 2 p + r (a TMA box {64, HP, 1} of the [J][H][Din] weights; rows past H and
+// 2 p + r (a TMA box {64, NB, 1} of the [J][H][Din] weights; rows past H and
 // particles past J read as zeros), and the even CTA issues tcgen05.mma.cta_group::2
-// with M = 256, N = 2 HP: the B operand is split between the CTAs, so each SM
+// with M = 256, N = 2 NB: the B operand is split between the CTAs, so each SM
 // reads its own A rows and one particle's W1 rows per K step, and every CTA's
-// TMEM receives its 128 rows with particle 0 in columns [0, HP) and particle 1 in
-// [HP, 2 HP); HP = 16 KT keeps both blocks on 16-column boundaries.  The
+// TMEM receives its 128 rows with particle 0 in columns [0, NB) and particle 1 in
+// [NB, 2 NB).  NB is the hidden width rounded up to 8 rows (one swizzle atom of
+// the B tile; 104 for H = 97..104), so the MMA computes no more columns than
+// that; the head pads the hidden width further, to HP = 16 KT (the mma.sync K
+// step), with zero columns of its H tile.  The
 // accumulator is double-buffered in TMEM (columns 0 and 256).
 //
 // Roles (320 threads per CTA, one CTA per SM): warp 0 issues TMA (both CTAs'
@@ -77,11 +80,12 @@ enum { ERR_PRODUCER = 0x201, ERR_MMA = 0x202, ERR_EPILOGUE = 0x203 };
 
 template <int KT>
 struct FCfg {
-    static constexpr int HP = 16 * KT;      // padded hidden width per particle
-    static constexpr int N = 2 * HP;        // MMA N: two particles
+    static constexpr int HP = 16 * KT;      // padded hidden width per particle (head)
+    static constexpr int NB = KT == 7 ? 104 : HP;   // hidden rows per particle in the MMA (multiple of 8)
+    static constexpr int N = 2 * NB;        // MMA N: two particles
     static constexpr int HS = HP + 8;       // H tile row stride (elements)
     static constexpr int A_BYTES = BM * BK * 2;
-    static constexpr int B_BYTES = HP * BK * 2;     // this CTA's particle (half of the MMA's B)
+    static constexpr int B_BYTES = NB * BK * 2;     // this CTA's particle (half of the MMA's B)
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     // per-particle image, W2 in mma.sync B-fragment order (one 16-byte load per lane
     // gives two fragments): logits fragments [KT][32 lanes] | dH fragments
@@ -165,7 +169,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const __grid_constant__ CUtensorMap tmZ, const FusedArgs a) {
     using F = FCfg<KT>;
-    constexpr int HP = F::HP, HS = F::HS, NT2 = 2 * KT, STAGES = F::STAGES;
+    constexpr int HP = F::HP, NB = F::NB, HS = F::HS, NT2 = 2 * KT, STAGES = F::STAGES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int rank = (int)cluster_rank();   // 0: the CTA that issues the MMAs
@@ -355,11 +359,11 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                     if (lane == 0) bulk_wait_read0();
                     __syncwarp();
                     // ---- 1. accumulator -> bias + activation -> BF16 H tile (row = lane)
-                    const uint32_t tb = tbase + (uint32_t)acc * ACC_COLS + (uint32_t)(grp * HP) +
+                    const uint32_t tb = tbase + (uint32_t)acc * ACC_COLS + (uint32_t)(grp * NB) +
                                         ((uint32_t)(wq * 32) << 16);
 #pragma unroll
-                    for (int c0 = 0; c0 < HP; c0 += 32) {
-                        const int n8 = (HP - c0) >= 32 ? 4 : (HP - c0) / 8;
+                    for (int c0 = 0; c0 < NB; c0 += 32) {
+                        const int n8 = (NB - c0) >= 32 ? 4 : (NB - c0) / 8;
                         uint32_t r[32];
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
@@ -388,6 +392,11 @@ fused_fwd_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                             }
                         }
                     }
+                    // the head's padding columns [NB, HP) of this row are zero (the
+                    // previous unit's dZ1 staging overwrote them)
+#pragma unroll
+                    for (int z = NB; z < HP; z += 8)
+                        *reinterpret_cast<uint4*>(Hs + lane * HS + z) = make_uint4(0u, 0u, 0u, 0u);
                 }
                 // the accumulator buffer is free for the MMA warp (on the even CTA)
                 tc_fence_before();
@@ -615,7 +624,9 @@ __global__ void fused_image_kernel(const float* __restrict__ W2, const float* __
     for (int i = threadIdx.x; i < 16; i += blockDim.x) b2s[i] = (i < C) ? b2[(int64_t)j * C + i] : 0.0f;
 }
 
-static int kt_for(int H) { return (H > 96 && H <= 112) ? 7 : (H <= 48 ? 3 : 8); }
+// KT = 7 serves H = 97..104 (MMA rows NB = 104 per particle), KT = 3 H <= 48, KT = 8 the rest.
+static int kt_for(int H) { return (H > 96 && H <= FCfg<7>::NB) ? 7 : (H <= 48 ? 3 : 8); }
+static int nb_for(int kt) { return kt == 7 ? FCfg<7>::NB : (kt == 3 ? FCfg<3>::NB : FCfg<8>::NB); }
 
 template <int KT>
 static int img_bytes() { return FCfg<KT>::IMG_BYTES; }
@@ -750,7 +761,7 @@ cudaError_t launch_fused_images(smc_ctx* c) {
 cudaError_t launch_fused_fwd_head(smc_ctx* c, const __nv_bfloat16* x, int64_t g0, int64_t mc, int slot_base,
                                   int* nslots) {
     const Layer& L0 = c->layers[0];
-    const int H = (int)L0.out_feat(), kt = kt_for(H), HP = 16 * kt;
+    const int H = (int)L0.out_feat(), kt = kt_for(H), HP = 16 * kt, NB = nb_for(kt);
     FusedArgs a{};
     a.M = (int)mc;
     a.K = (int)c->in_feat;
@@ -777,7 +788,7 @@ cudaError_t launch_fused_fwd_head(smc_ctx* c, const __nv_bfloat16* x, int64_t g0
     CUtensorMap ta, tb, tz;
     const uint64_t din = (uint64_t)c->in_feat;
     if (!make_tmap(&ta, x, din, (uint64_t)mc, din * 2, BM)) return cudaErrorInvalidValue;
-    if (!make_tmap_3d(&tb, c->shadow, din, (uint64_t)H, (uint64_t)c->J, din * 2, din * 2 * (uint64_t)H, HP, 1))
+    if (!make_tmap_3d(&tb, c->shadow, din, (uint64_t)H, (uint64_t)c->J, din * 2, din * 2 * (uint64_t)H, NB, 1))
         return cudaErrorInvalidValue;
     // dZ1^T [J][H][ldz]: box {16 samples, HP hidden rows} per m-tile
     const uint64_t ldz = (uint64_t)c->chunk;
