@@ -350,19 +350,21 @@ static cudaError_t cnn_forward(smc_ctx* c, const Shape& s, const __nv_bfloat16* 
     auto& b = c->cnn;
     SMC_LAUNCH(c, im2col1_kernel<<<nimg, 256, (size_t)s.K1p * 4 + (size_t)s.C0 * s.H0 * s.W0 * 2, c->stream>>>(
                       x, c->in_feat, s, b.I1));
-    // conv 1 and pool 1: one GEMM over all particles' filters whose epilogue
-    // pools each window's four rows (only P1 and idx1 are written)
+    // conv 1 and pool 1: one GEMM over all particles' filters, computed
+    // transposed (rows = the J C1 output channels, columns = the chunk's
+    // positions, four consecutive per pooling window), whose epilogue pools each
+    // window inside one thread (only P1 and idx1 are written)
     {
-        const int64_t M = (int64_t)nimg * s.R1;
-        const GOperand A = op3(b.I1, 0, 0, 0, s.K1, M, 1, s.K1p, M * s.K1p);
+        const int64_t npos = (int64_t)nimg * s.R1;
         const GOperand W = op3(b.W1p, 0, 0, 0, s.K1, J * s.C1, 1, s.K1p, J * s.C1 * s.K1p);
+        const GOperand I = op3(b.I1, 0, 0, 0, s.K1, npos, 1, s.K1p, npos * s.K1p);
         GArgs g{};
-        g.M = (int)M; g.N = (int)(J * s.C1); g.K = s.K1; g.batch = 1; g.epi = gk::EPI_BF16_POOL;
+        g.M = (int)(J * s.C1); g.N = (int)npos; g.K = s.K1; g.batch = 1; g.epi = gk::EPI_BF16_POOL;
         g.bias = c->theta + c->segs[c->layers[0].seg_b].off;
         g.pool_out = b.P1; g.pool_idx = b.idx1; g.pool_rows = b.p1_rows; g.pool_ch = s.C1;
         g.aug_col = -1; g.err = c->err_dev;
         fam_begin(c, F_FWD_GEMM);
-        cudaError_t e = grouped_gemm(A, W, nullptr, g, SMC_ACT_TANH, 104, c->stream, c->num_sms);
+        cudaError_t e = grouped_gemm(W, I, nullptr, g, SMC_ACT_TANH, 128, c->stream, c->num_sms);
         c->launches++;
         fam_end(c, F_FWD_GEMM);
         if (e != cudaSuccess) return e;

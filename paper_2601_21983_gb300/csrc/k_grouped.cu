@@ -34,11 +34,13 @@
 //   EPI_BF16_ACT  BF16 act(acc + bias[b][n]) (a forward layer);
 //   EPI_BF16_DACT BF16 acc * act'(aux) with aux the stored activation at the
 //                 same position (dZ of a hidden layer, act' from its output);
-//   EPI_BF16_POOL four consecutive rows (one 2x2 pooling window) reduced to
-//                 their maximum and its index by warp shuffles, then BF16
-//                 act(max + bias); only the pooled values (8-column planes)
-//                 and the argmaxes are stored (a convolution layer followed
-//                 by max pooling, rows ordered window by window).
+//   EPI_BF16_POOL a convolution layer followed by 2x2 max pooling, computed
+//                 transposed (rows = output channels, columns = input
+//                 positions ordered window by window), so each thread holds
+//                 its channel's four values of a window: their maximum and
+//                 its index are taken on the accumulators, then BF16
+//                 act(max + bias); only the pooled values (8-channel planes)
+//                 and the argmaxes are stored.
 // The BF16 epilogues stage each warp's 32 rows x 32 (or, at the end of a
 // half, 8) columns in shared memory and write them with TMA bulk-tensor
 // stores: a warp's thread-per-row registers would otherwise scatter every
@@ -243,63 +245,34 @@ __device__ __forceinline__ void store_box(const CUtensorMap* tm, int perm, const
 // Epilogues that stage their BF16 output tiles for TMA stores.
 __host__ __device__ constexpr bool staged_out(int epi) { return epi == EPI_BF16_ACT || epi == EPI_BF16_DACT; }
 
-// One of four values picked by a lane-dependent index without dynamic register
-// indexing.
-__device__ __forceinline__ float sel4(int x, float a, float b, float c, float d) {
-    return (x & 2) ? ((x & 1) ? d : c) : ((x & 1) ? b : a);
-}
-
-// EPI_BF16_POOL on one 32-column group: lanes 4w' .. 4w' + 3 of a warp hold the
-// four rows of pooling window w' (r: this lane's 32 FP32 accumulators, n8 of
-// its four 8-column pieces in use), and lane 4w' + q finishes piece q.  act is
-// increasing and one bias is shared by a column's four rows, so the window's
-// maximum is taken on the accumulators: in exchange step k = 1, 2, 3 the lane receives
-// row (q ^ k)'s eight values of its piece from lane 4w' + (q ^ k) (which sends
-// its own values of piece q ^ k ^ k = q), and keeps the maximum with the first
-// row attaining it.  Then bias, act, BF16, one 16-byte store into the piece's
-// plane and 8 index bytes.
+// EPI_BF16_POOL on one 32-column group of this lane's row (output channel m):
+// columns col0 .. col0 + 8 n8 - 1 are 2 n8 pooling windows of four positions
+// (col0 a multiple of 32, the columns of a window consecutive).  The window's
+// maximum and the first position attaining it are taken on the accumulators
+// (act is increasing and the bias is the channel's), then BF16 act(max + bias)
+// goes to the channel's plane and the index to its argmax row.
 template <int ACT>
-__device__ __forceinline__ void pool_group(const GArgs& g, int b, int row0, int col0, int n8, const uint32_t* r) {
-    const int lane = threadIdx.x & 31, d = lane & 3;
-    float rv[32];
+__device__ __forceinline__ void pool_group(const GArgs& g, int b, int m, int col0, int n8, const uint32_t* r) {
+    if (m >= g.M) return;
+    const float bias = g.bias[(int64_t)b * g.bias_bstride + m];
+    __nv_bfloat16* po = g.pool_out + (int64_t)(m >> 3) * g.pool_rows * 8 + (m & 7);
+    uint8_t* pi = g.pool_idx + (int64_t)(m / g.pool_ch) * g.pool_rows * g.pool_ch + m % g.pool_ch;
 #pragma unroll
-    for (int c = 0; c < 32; ++c) rv[c] = c < 8 * n8 ? __uint_as_float(r[c]) : 0.0f;   // unloaded pieces: 0
-    float bv[8];
-    int bi8[8];
+    for (int w = 0; w < 8; ++w) {
+        const int col = col0 + 4 * w;
+        if (w < 2 * n8 && col < g.N) {
+            float best = __uint_as_float(r[4 * w]);
+            int bi = 0;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        bv[e] = sel4(d, rv[e], rv[8 + e], rv[16 + e], rv[24 + e]);
-        bi8[e] = d;
-    }
-#pragma unroll
-    for (int k = 1; k < 4; ++k) {
-        const int src = d ^ k;   // the row whose values arrive in this exchange step
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const float send = sel4(src, rv[e], rv[8 + e], rv[16 + e], rv[24 + e]);
-            const float v = __shfl_xor_sync(0xffffffffu, send, k);
-            if (v > bv[e] || (v == bv[e] && src < bi8[e])) { bv[e] = v; bi8[e] = src; }
+            for (int k = 1; k < 4; ++k) {
+                const float v = __uint_as_float(r[4 * w + k]);
+                if (v > best) { best = v; bi = k; }
+            }
+            const int64_t win = col >> 2;
+            po[win * 8] = __float2bfloat16_rn(act_fwd<ACT>(best + bias));
+            pi[win * g.pool_ch] = (uint8_t)bi;
         }
     }
-    const int win_row = row0 + (lane & ~3);   // first row of this lane's window
-    const int col = col0 + 8 * d;
-    if (d >= n8 || win_row >= g.M || col >= g.N) return;
-    const float* bp = g.bias + (int64_t)b * g.bias_bstride + col;
-    const float4 b0 = *reinterpret_cast<const float4*>(bp);
-    const float4 b1 = *reinterpret_cast<const float4*>(bp + 4);
-    const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-    __align__(16) __nv_bfloat16 best[8];
-    __align__(8) uint8_t bi[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        best[e] = __float2bfloat16_rn(act_fwd<ACT>(bv[e] + bb[e]));
-        bi[e] = (uint8_t)bi8[e];
-    }
-    const int64_t win = win_row >> 2;
-    *reinterpret_cast<uint4*>(g.pool_out + ((int64_t)(col >> 3) * g.pool_rows + win) * 8) =
-        *reinterpret_cast<const uint4*>(best);
-    *reinterpret_cast<uint2*>(g.pool_idx + ((int64_t)(col / g.pool_ch) * g.pool_rows + win) * g.pool_ch +
-                              col % g.pool_ch) = *reinterpret_cast<const uint2*>(bi);
 }
 
 template <int NHALF, bool AMN, bool BMN, int EPI, int ACT>
@@ -490,7 +463,7 @@ grouped_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                 }
                 tmem_ld_wait();
                 if (POOL) {
-                    pool_group<ACT>(g, b, row0, tn * 2 * NHALF + c0, n8, r);
+                    pool_group<ACT>(g, b, row, tn * 2 * NHALF + c0, n8, r);
                     continue;
                 }
                 if (!BF16OUT) {
@@ -674,16 +647,18 @@ cudaError_t grouped_gemm(const gk::GOperand& A, const gk::GOperand& B, const gk:
         if (nhalf == 48) return launch_t<48, true, true, EPI_F32, SMC_ACT_IDENTITY>(A, B, O, g, s, num_sms);
         return cudaErrorInvalidValue;
     }
+    if (g.epi == EPI_BF16_POOL) {
+        // rows: output channels (M a multiple of 8, whole planes); columns: input
+        // positions, four per pooling window
+        if (nhalf != 128 || A.mn_major || B.mn_major || g.batch != 1 || g.M % 8 != 0 || g.N % 4 != 0 ||
+            g.pool_ch % 8 != 0 || g.M % g.pool_ch != 0 || g.pool_out == nullptr || g.pool_idx == nullptr)
+            return cudaErrorInvalidValue;
+        if (act == SMC_ACT_RELU) return launch_t<128, false, false, EPI_BF16_POOL, SMC_ACT_RELU>(A, B, O, g, s, num_sms);
+        if (act == SMC_ACT_TANH) return launch_t<128, false, false, EPI_BF16_POOL, SMC_ACT_TANH>(A, B, O, g, s, num_sms);
+        return launch_t<128, false, false, EPI_BF16_POOL, SMC_ACT_IDENTITY>(A, B, O, g, s, num_sms);
+    }
     // the BF16 epilogues follow a K-major A (rows of a layer), N a multiple of 8
     if (A.mn_major || (nhalf != 104 && nhalf != 16) || (g.N % 8 != 0)) return cudaErrorInvalidValue;
-    if (g.epi == EPI_BF16_POOL) {
-        if (nhalf != 104 || B.mn_major || g.batch != 1 || g.M % 4 != 0 || g.pool_ch % 8 != 0 ||
-            g.pool_out == nullptr || g.pool_idx == nullptr)
-            return cudaErrorInvalidValue;
-        if (act == SMC_ACT_RELU) return launch_t<104, false, false, EPI_BF16_POOL, SMC_ACT_RELU>(A, B, O, g, s, num_sms);
-        if (act == SMC_ACT_TANH) return launch_t<104, false, false, EPI_BF16_POOL, SMC_ACT_TANH>(A, B, O, g, s, num_sms);
-        return launch_t<104, false, false, EPI_BF16_POOL, SMC_ACT_IDENTITY>(A, B, O, g, s, num_sms);
-    }
     if (O == nullptr) return cudaErrorInvalidValue;
     if (nhalf == 16 && B.mn_major) return cudaErrorInvalidValue;
     auto run = [&](auto epi_tag, auto act_tag) -> cudaError_t {

@@ -39,10 +39,11 @@ struct GArgs {
     float* aug_out;              // EPI_F32: column aug_col goes to aug_out[b aug_bstride + m];
     int aug_col;                 //          columns past it are dropped (-1: none)
     int64_t aug_bstride;
-    __nv_bfloat16* pool_out;     // EPI_BF16_POOL: the 2x2 max of rows 4w .. 4w + 3 of column n at
-                                 //   pool_out[((n / 8) pool_rows + w) 8 + n % 8] (8-channel planes)
+    __nv_bfloat16* pool_out;     // EPI_BF16_POOL: the 2x2 max of columns 4w .. 4w + 3 of row m
+                                 //   (channel m) at pool_out[((m / 8) pool_rows + w) 8 + m % 8]
+                                 //   (8-channel planes)
     uint8_t* pool_idx;           //   and its argmax (0..3, first maximum) at
-                                 //   pool_idx[((n / pool_ch) pool_rows + w) pool_ch + n % pool_ch]
+                                 //   pool_idx[((m / pool_ch) pool_rows + w) pool_ch + m % pool_ch]
     int64_t pool_rows;
     int pool_ch;                 //   columns per batch of planes (a multiple of 8)
     int* err;                    // device error flag (timeouts)
@@ -59,11 +60,12 @@ struct GArgs {
 // EPI_F32, or 16 / 48 with both operands MN-major (the narrow weight
 // gradients of convolution layers); 104 (two accumulators, so one tile's
 // epilogue overlaps the next tile's MMAs) or 16 (a 32-channel convolution,
-// K-major operands) for the BF16 epilogues.  act selects the activation of
+// K-major operands) for the BF16 epilogues; 128 for EPI_BF16_POOL (K-major
+// operands, 64 pooling windows per 256-column tile).  act selects the activation of
 // the BF16 epilogues.
 // O: the BF16 epilogues' output as a 3-D array (inner = N columns, outer =
 // M rows, batch), written by TMA stores; NULL for EPI_F32 (out / ldo /
-// out_bstride of GArgs) and for EPI_BF16_POOL (nhalf 104, one batch: the
+// out_bstride of GArgs) and for EPI_BF16_POOL (nhalf 128, one batch: the
 // activations are pooled in the epilogue and only the pooled planes and the
 // argmaxes are written).
 cudaError_t grouped_gemm(const gk::GOperand& A, const gk::GOperand& B, const gk::GOperand* O, const gk::GArgs& g,
