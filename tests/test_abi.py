@@ -61,3 +61,35 @@ def test_struct_sizes_match_header_layout():
     assert C.sizeof(smc.smc_step_stats) == 56
     assert C.sizeof(smc.smc_step_params) == 32
     assert C.sizeof(smc.smc_schedule) == 56
+
+
+def _header_constants():
+    """NAME = value pairs of the header's enums and #defines (comments removed)."""
+    txt = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    vals = {n: int(v) for n, v in re.findall(r"\b(SMC_[A-Z0-9_]+)\s*=\s*(\d+)", txt)}
+    vals.update({n: int(v) for n, v in re.findall(r"#define\s+(SMC_[A-Z0-9_]+)\s+(\d+)", txt)})
+    return vals
+
+
+def test_binding_constants_match_the_header():
+    """Every enum value the binding passes to the library (layer kinds,
+    activations, likelihoods, precisions, resamplers, schedule kinds,
+    proposals) equals the header's."""
+    from paper_2601_21983_gb300 import smc
+    h = _header_constants()
+    pairs = {
+        "LAYER_DENSE": "SMC_LAYER_DENSE", "LAYER_CONV": "SMC_LAYER_CONV", "LAYER_MAXPOOL2": "SMC_LAYER_MAXPOOL2",
+        "LAYER_BNORM": "SMC_LAYER_BNORM", "ACT_TANH": "SMC_ACT_TANH", "ACT_RELU": "SMC_ACT_RELU",
+        "ACT_IDENTITY": "SMC_ACT_IDENTITY", "LIK_CATEGORICAL": "SMC_LIK_CATEGORICAL",
+        "LIK_GAUSSIAN": "SMC_LIK_GAUSSIAN", "PREC_FP32": "SMC_PREC_FP32", "PREC_BF16": "SMC_PREC_BF16",
+        "RESAMPLE_SYSTEMATIC": "SMC_RESAMPLE_SYSTEMATIC", "RESAMPLE_MULTINOMIAL": "SMC_RESAMPLE_MULTINOMIAL",
+        "PROPOSAL_PLAIN": "SMC_PROPOSAL_PLAIN", "PROPOSAL_LEARNED": "SMC_PROPOSAL_LEARNED",
+        "PROPOSAL_EXPLORE": "SMC_PROPOSAL_EXPLORE", "LEARNED_NUM_PARAMS": "SMC_LEARNED_NUM_PARAMS",
+    }
+    for py, c in pairs.items():
+        assert getattr(smc, py) == h[c], (py, c)
+    sched = {"constant": "SMC_SCHED_CONSTANT", "fb": "SMC_SCHED_FB", "ctr": "SMC_SCHED_CTR",
+             "linear": "SMC_SCHED_LINEAR", "automated": "SMC_SCHED_AUTOMATED", "sda": "SMC_SCHED_SDA",
+             "constant_fresh": "SMC_SCHED_CONSTANT_FRESH", "ctr_fresh": "SMC_SCHED_CTR_FRESH"}
+    for name, c in sched.items():
+        assert smc.SCHED[name] == h[c], name
