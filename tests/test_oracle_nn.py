@@ -227,3 +227,32 @@ def test_fashion_cnn_parameter_count():
     spec = nn.Spec([("conv", 1, 8, 3), ("bnorm", 8), ("pool2",), ("conv", 8, 16, 3), ("bnorm", 16), ("pool2",),
                     ("dense", 16 * 5 * 5, 232), ("dense", 232, 10)], (1, 28, 28), nn.TANH)
     assert spec.n_params == 96658
+
+
+def test_fd_fashion_cnn_sampled_coordinates():
+    # the 96,658-parameter network itself: central differences on coordinates drawn
+    # from every parameter block (both batchnorm scales and shifts included)
+    spec = nn.Spec([("conv", 1, 8, 3), ("bnorm", 8), ("pool2",), ("conv", 8, 16, 3), ("bnorm", 16), ("pool2",),
+                    ("dense", 16 * 5 * 5, 232), ("dense", 232, 10)], (1, 28, 28), nn.TANH)
+    rng = np.random.default_rng(14)
+    X, y = rng.uniform(size=(3, 784)), rng.integers(0, 10, 3)
+    theta = 0.3 * rng.normal(size=spec.n_params)
+    _, g = nn.loglik_grad(spec, theta, X, y, np.ones(3))
+
+    def f(t):
+        z, _ = nn.forward(spec, t, X)
+        return float(np.sum(nn.per_sample_loglik(spec, z, y)))
+
+    off = 0
+    for shapes in spec.shapes:
+        for s in shapes:
+            n = int(np.prod(s))
+            for i in rng.choice(n, min(n, 2), replace=False):
+                k = off + int(i)
+                tp, tm = theta.copy(), theta.copy()
+                tp[k] += 1e-6
+                tm[k] -= 1e-6
+                fd = (f(tp) - f(tm)) / 2e-6
+                assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(fd)) + 1e-7, (k, fd, g[k])
+            off += n
+    assert off == spec.n_params
